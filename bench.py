@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the sliced tensor-network contraction on GB300.
+
+Workload: the 30-qubit 5x6 grid random circuit (14 cycles of the
+sqrt(X)/sqrt(Y)/sqrt(W) + fSim family, seed 2) with the last 6 qubits open
+(64 amplitudes), greedy contraction tree, lifetime-based slicing to at most
+2^27-element intermediates (Algorithms 1 and 2, seed 7). A step is one
+tnc_contract call over a batch of consecutive slices: every pairwise
+contraction of those slices plus the FP64 slice sum. Inputs (leaves) are
+resident in HBM when the timed region starts; every step streams 1 GiB
+intermediates, far larger than the 129 MB L2, so no flush is needed.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (rank 0 only; other ranks exit without work).
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sliced contraction complex TFLOPS & s/1024 slices, split-TC vs FP32 at rel err≤1e-4"
+UNIT = "TFLOPS (complex, effective 8*M*N*K per node)"
+WORKLOAD = dict(rows=5, cols=6, cycles=14, seed=2, n_open=6, target_log2=27, sa_seed=7)
+MODES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x2": 3}
+# FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def workload_name():
+    w = WORKLOAD
+    return ("rqc-%dx%d-%dcyc-seed%d-open%d-t%d" %
+            (w["rows"], w["cols"], w["cycles"], w["seed"], w["n_open"], w["target_log2"]))
+
+
+def build_network():
+    from tnc_inputs import circuit_to_network, grid_rqc
+    w = WORKLOAD
+    c = grid_rqc(w["rows"], w["cols"], w["cycles"], w["seed"], n_open=w["n_open"])
+    return c, circuit_to_network(c).as_complex64()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_traffic(kind_name):
+    """DRAM bytes per launch from the committed ncu summary, valid only while
+    the kernel source is unchanged (hash recorded beside the figure)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kind_name)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes_per_unit"] if h == rec["source_sha"] else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def node_flops(stats, batch):
+    """Effective complex flops (8*M*N*K per node) of one tnc_contract call over `batch` slices."""
+    tot = 0
+    for mb, nb, kb, per_slice, kind in stats["nodes"]:
+        tot += 8 * (1 << (mb + nb + kb)) * (batch if per_slice else 1)
+    return tot
+
+
+def run_oracle_sample(ref_net, path, S, budget_s=20.0):
+    """Time the FP64 oracle on one slice's largest contractions (the nodes that
+    carry 99.99% of the flops), at most ~budget_s seconds."""
+    import threading
+    from oracle import tn
+    log = []
+    t0 = time.perf_counter()
+    tn.contract_slice(ref_net, path, S, 0, log=log)
+    dt = time.perf_counter() - t0
+    return sum(log), dt
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+        return int(n)
+    except Exception:
+        return os.cpu_count()
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import planner
+    c, ref_net = build_network()
+    path = planner.greedy_path(ref_net.indices, ref_net.dims)
+    tree = planner.Tree(ref_net.indices, ref_net.dims, ref_net.open_ids, path)
+    S = planner.find_slices(tree, WORKLOAD["target_log2"], WORKLOAD["sa_seed"])
+    from oracle import tn
+    times, macs = [], 0
+    for i in range(args.warmup + args.steps):
+        log = []
+        t0 = time.perf_counter()
+        tn.contract_slice(ref_net, path, S, i % (1 << len(S)), log=log)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            macs += sum(log)
+    T = sum(times)
+    tflops = 8 * macs / T / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": tflops, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "s_per_1024_slices": T / args.steps * 1024,
+        "config": {"workload": workload_name(), "slices_per_step": 1, "n_slices": 1 << len(S),
+                   "mode": "oracle-fp64"},
+        "cpu_baseline": {"value": tflops, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                         "sample": "one full slice (all pairwise contractions) per step, NumPy complex128"},
+        "e2e": {"value": tflops, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tnc", choices=["tnc", "reference"])
+    ap.add_argument("--mode", default="fp32", choices=sorted(MODES))
+    ap.add_argument("--slices-per-step", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2205_00393_gb300 import Network
+
+    c, ref_net = build_network()
+    net = Network.from_tn(ref_net)
+    path = net.greedy_path()
+    net.set_path(path)
+    S = net.find_slices(WORKLOAD["target_log2"], WORKLOAD["sa_seed"])
+    net.set_slices(S)
+    n_slices = net.n_slices
+    B = args.slices_per_step
+    mode = MODES[args.mode]
+    ws = torch.empty(net.workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    net.set_workspace(ws)
+    stats = net.stats()
+    stream = torch.cuda.current_stream()
+    out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
+
+    def slice_range(step):
+        lo = ((step * world + rank) * B) % n_slices
+        return lo, min(lo + B, n_slices)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        lo, hi = slice_range(i)
+        net.contract(lo, hi, mode, out=out)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    net.set_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flops = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for i in range(args.steps):
+            lo, hi = slice_range(args.warmup + i)
+            net.contract(lo, hi, mode, out=out)
+            flops += node_flops(stats, hi - lo)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    T = ev0.elapsed_time(ev1) / 1e3
+    recs, n_launches = net.last_timings()
+    net.set_timing(False)
+    n_sl_done = sum(slice_range(args.warmup + i)[1] - slice_range(args.warmup + i)[0]
+                    for i in range(args.steps))
+    if world > 1:
+        t = torch.tensor([T], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+        f = torch.tensor([flops, n_sl_done], device="cuda", dtype=torch.float64)
+        dist.all_reduce(f)
+        flops, n_sl_tot = float(f[0].item()), int(f[1].item())
+    else:
+        n_sl_tot = n_sl_done
+    value = flops / T / 1e12
+
+    # ---- dominant kernel roofline (per-launch CUDA events over the timed region)
+    by_kind = {}
+    for r in recs:
+        k = r["kind"]
+        d = by_kind.setdefault(k, {"ms": 0.0, "flops": 0.0, "launches": 0})
+        d["ms"] += r["ms"]
+        d["launches"] += 1
+        d["flops"] += 8.0 * (1 << r["mnk_log2"]) * r["batch"]
+    kind_names = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", -1: "k_slice_sum_f32"}
+    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    d = by_kind[dom]
+    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    peaks, peak_src = load_peaks()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(kind_names[dom]),
+                "kernel": kind_names[dom], "launches": d["launches"],
+                "share_of_timed_kernel_time": d["ms"] / sum(v["ms"] for v in by_kind.values()),
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz"}
+
+    # ---- end to end through the public API with host buffers
+    leaf_bytes = net.leaf_bytes()
+    packed = np.concatenate([np.asarray(t, dtype=np.complex64).reshape(-1) for t in ref_net.tensors])
+    host_in = torch.from_numpy(packed.view(np.float32).copy()).pin_memory()
+    host_out = torch.empty(net.n_out, dtype=torch.complex128).pin_memory()
+    e2e_steps = max(2, min(args.steps, 4))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        lo, hi = slice_range(i)
+        net.upload_leaves(host_in.data_ptr(), stream)
+        net.contract(lo, hi, mode, out=out)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    Te = time.perf_counter() - t0
+    e2e_flops = sum(node_flops(stats, slice_range(i)[1] - slice_range(i)[0]) for i in range(e2e_steps))
+    if world > 1:
+        t = torch.tensor([Te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        Te = float(t.item())
+        e2e_flops *= world
+    e2e = {"value": e2e_flops / Te / 1e12, "unit": UNIT, "h2d_bytes_per_step": leaf_bytes,
+           "d2h_bytes_per_step": net.n_out * 16}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64-fp32" if args.mode == "fp32" else args.mode,
+        "data": "synthetic",
+        "s_per_1024_slices": T / n_sl_tot * 1024 * world if world > 1 else T / n_sl_tot * 1024,
+        "config": {"workload": workload_name(), "mode": args.mode, "slices_per_step": B,
+                   "n_slices": n_slices, "sliced": len(S), "eq3_overhead": stats["overhead"],
+                   "l2": "working set > L2 (1 GiB intermediates), no flush",
+                   "parallelism": "slices sharded over ranks" if world > 1 else "1 GPU"},
+        "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launches,
+        "kernel_time_ms": {kind_names[k]: v["ms"] for k, v in by_kind.items()},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import planner
+        path_py = [tuple(p) for p in path]
+        macs, dt = run_oracle_sample(ref_net, path_py, S)
+        line["cpu_baseline"] = {"value": 8 * macs / dt / 1e12, "unit": UNIT, "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": "one full slice of the workload (NumPy complex128 tensordot per node), %.1f s" % dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

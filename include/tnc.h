@@ -1,0 +1,171 @@
+/*
+ * tnc.h - C ABI of libtnc: sliced tensor-network contraction on GB300 (sm_103a).
+ *
+ * The library computes amplitudes of a tensor network (Sec. 2.1.1 of Liu et
+ * al., "Lifetime-based Optimization for Simulating Quantum Circuits on a New
+ * Sunway Supercomputer"): tensors are vertices, indices are edges, every index
+ * joins at most two tensors, an index joining one tensor only is open and
+ * survives into the result. A contraction tree fixes the order of pairwise
+ * contractions; slicing fixes a set S of closed indices of dimension 2, giving
+ * 2^|S| independent sub-contractions whose results are summed (Sec. 2.1.1,
+ * Fig. 2). The host-side planner implements the paper's lifetime-based slice
+ * finder (Algorithm 1) and simulated-annealing refiner (Algorithms 2-4).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a tnc_status and never throws. On failure a message is
+ *    available from tnc_last_error() (thread-local, valid until the next call
+ *    on the same thread).
+ *  - Complex numbers are interleaved (re, im). Host tensor data is complex64
+ *    (2 floats per element), row-major over the tensor's index list: the last
+ *    listed index varies fastest.
+ *  - Index ids are integers in [0, n_indices); dimensions are powers of two.
+ *  - The library copies every host input it is given; the caller keeps
+ *    ownership of its buffers. Device buffers passed in (outputs, workspace)
+ *    are owned by the caller and must stay valid until the stream work that
+ *    uses them completes.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). All device
+ *    work of a call is enqueued on it; calls return before it completes.
+ *  - A network object is not thread-safe; use one per thread.
+ */
+#ifndef TNC_H
+#define TNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tnc_net* tnc_net_t;
+
+typedef enum {
+    TNC_OK = 0,
+    TNC_E_INVALID = 1, /* malformed input: message says which argument   */
+    TNC_E_OOM = 2,     /* device or host allocation failed               */
+    TNC_E_CUDA = 3,    /* a CUDA runtime call failed                     */
+    TNC_E_TIMEOUT = 4, /* a bounded device-side wait gave up             */
+    TNC_E_STATE = 5    /* call out of order (e.g. contract before path)  */
+} tnc_status;
+
+/* Arithmetic used by the pairwise contractions. The slice sum and the final
+ * amplitude reduction are always accumulated in FP64. */
+typedef enum {
+    TNC_FP32 = 0,        /* complex64 on FP32 CUDA cores (4 real FMAs per complex MAC)     */
+    TNC_SPLIT_TF32 = 1,  /* x = hi + lo in TF32, 3 products, tcgen05 kind::tf32, FP32 accum */
+    TNC_SPLIT_BF16 = 2,  /* x = x0 + x1 + x2 in BF16, 6 products, tcgen05 kind::f16, FP32   */
+    TNC_SPLIT_BF16X2 = 3 /* x = x0 + x1 in BF16, 3 products (cheaper, lower accuracy)       */
+} tnc_mode;
+
+/* Build a network (Sec. 2.1.1: G = (V, E, w)).
+ *  n_tensors       number of tensors (leaves), >= 1
+ *  ranks[i]        number of indices of tensor i (0 allowed: a scalar)
+ *  index_ids[i]    ranks[i] index ids of tensor i, in row-major order of its data
+ *  n_indices       number of index ids; index_dims[e] = w(e), a power of two
+ *  data_c64[i]     host pointer to 2 * prod(dims) floats of tensor i (copied)
+ *  open_ids        the n_open indices that belong to exactly one tensor, in the
+ *                  order of the result tensor (first = most significant)
+ *  out             receives the handle; free it with tnc_destroy
+ * Errors: TNC_E_INVALID if an index joins more than two tensors, repeats within
+ * a tensor, has a non-power-of-two dimension, if an index on one tensor only is
+ * not listed in open_ids (or vice versa), or if a tensor exceeds 2^31 elements.
+ * No device memory is touched until the first contraction. */
+tnc_status tnc_create_network(int n_tensors, const int* ranks,
+                              const int64_t* const* index_ids, int64_t n_indices,
+                              const int64_t* index_dims, const float* const* data_c64,
+                              int n_open, const int64_t* open_ids, tnc_net_t* out);
+
+/* Replace the data of leaf `tensor` (same shape) from host memory; used for
+ * gate-parameter updates. The host copy is updated at once; the device copy on
+ * the next contraction. */
+tnc_status tnc_set_tensor_data(tnc_net_t net, int tensor, const float* data_c64);
+
+/* Bytes of all leaves packed back to back in leaf order (complex64). */
+tnc_status tnc_leaf_bytes(tnc_net_t net, size_t* bytes);
+
+/* Copy all leaves, packed as tnc_leaf_bytes describes, from host memory
+ * (pinned memory lets the copy overlap) to the device copy, enqueued on
+ * `stream`. The host buffer must stay valid until the copy completes. */
+tnc_status tnc_upload_leaves(tnc_net_t net, const float* packed_c64, void* stream);
+
+/* Greedy contraction path in SSA form (leaves 0..n-1, step i creates n+i):
+ * rank-1/rank-2 tensors are first absorbed into their largest-rank neighbour
+ * (the simplification of Sec. 2.1.2), then the connected pair minimising
+ * size(out) - size(a) - size(b) is contracted (ties: smaller ids), then
+ * disconnected remainders are joined in ascending id order.
+ * pairs_out receives 2 * (n_tensors - 1) ints; pair entries are (smaller, larger). */
+tnc_status tnc_greedy_path(tnc_net_t net, int* pairs_out);
+
+/* Set the contraction tree B (Sec. 2.1.1, Fig. 1) as an SSA path of
+ * n_steps = n_tensors - 1 pairs. Errors: TNC_E_INVALID if the pairs do not
+ * form a binary tree over all leaves or an intermediate exceeds 2^120 elements.
+ * Clears any slicing set. A contraction additionally requires every
+ * intermediate to keep at most 2^36 elements once the sliced indices are
+ * fixed (TNC_E_INVALID from tnc_contract otherwise). */
+tnc_status tnc_set_path(tnc_net_t net, int n_steps, const int* pairs);
+
+/* Lifetime-based in-place slicing (Sec. 4): Algorithm 1 (slice finder on the
+ * stem) then Algorithm 2 (simulated-annealing refiner, with Algorithms 3/4),
+ * minimising the Eq. 3 cost under the constraint that every tree tensor keeps
+ * at most 2^target_log2 elements. T0, Tf, alpha: starting temperature, final
+ * temperature and cooling factor (defaults 1.0, 1e-4, 0.9 if <= 0).
+ * Writes up to `cap` sliced index ids to out_ids in insertion order and their
+ * number to *n_out. Errors: TNC_E_INVALID if the target is infeasible (a tree
+ * tensor has more than target_log2 bits of open indices) or cap is too small;
+ * TNC_E_STATE before tnc_set_path. Does not change the network's slicing set. */
+tnc_status tnc_find_slices(tnc_net_t net, int target_log2, uint64_t seed,
+                           double T0, double Tf, double alpha,
+                           int64_t* out_ids, int* n_out, int cap);
+
+/* Set the slicing set S (Sec. 2.1.1): n closed indices of dimension 2.
+ * Slice s in [0, 2^n) assigns bit j of s to the j-th smallest id of S.
+ * Errors: TNC_E_INVALID for an open index, a dimension other than 2, a
+ * repeated id or n > 62; TNC_E_STATE before tnc_set_path. */
+tnc_status tnc_set_slices(tnc_net_t net, int n, const int64_t* ids);
+
+/* Device workspace needed to contract `max_batch` slices at once with the
+ * current path and slicing set (max_batch >= 1). */
+tnc_status tnc_workspace_bytes(tnc_net_t net, int64_t max_batch, size_t* bytes);
+
+/* Give the library caller-owned device workspace (e.g. from PyTorch's
+ * allocator). Contractions then batch as many slices as fit. If none is set,
+ * the library allocates (and owns) the workspace for batch 1 itself. */
+tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes);
+
+/* Sum over slices s in [slice_lo, slice_hi) of the sliced contraction
+ * (Sec. 2.1.1; the per-slice results are accumulated, the paper's final
+ * allReduce becomes an on-device FP64 reduction in a fixed order).
+ *  out_c128  device pointer, 2 * 2^(sum of log2 dims of open indices) doubles,
+ *            overwritten with the result in open_ids order.
+ * Errors: TNC_E_STATE before tnc_set_path; TNC_E_INVALID if the range is not
+ * within [0, 2^|S|] or mode is unknown; TNC_E_CUDA / TNC_E_OOM from the device. */
+tnc_status tnc_contract(tnc_net_t net, int64_t slice_lo, int64_t slice_hi, int mode,
+                        double* out_c128, void* stream);
+
+/* JSON statistics of the current plan: Eq. 1 cost, Eq. 3 cost, Eq. 2
+ * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace. */
+tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
+
+/* Per-launch timing: when enabled, every kernel launch of tnc_contract is
+ * bracketed by CUDA events recorded on the contraction's stream. Each call
+ * clears the records and the launch counter, which then accumulate over all
+ * following contractions. */
+tnc_status tnc_set_timing(tnc_net_t net, int enable);
+
+/* Launch records since the last tnc_set_timing (waits for their events): per timed
+ * launch the node's tensor id, kernel kind (0 GEMM, 1 FP64 root reduction,
+ * 2 GEMM root + FP64 slice sum, -1 leaf slice sum), slice batch, log2(M*N*K)
+ * and milliseconds; any output array may be NULL. *n_out receives the number
+ * of records (TNC_E_INVALID if it exceeds cap); *n_launches (may be NULL) the
+ * number of kernels launched since then (counted with timing on or off). */
+tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, int64_t* mnk_log2,
+                            float* ms, int cap, int* n_out, int64_t* n_launches);
+
+const char* tnc_last_error(void);
+void tnc_destroy(tnc_net_t net);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNC_H */

@@ -1,0 +1,226 @@
+"""ctypes binding of libtnc (include/tnc.h). Argument marshalling only.
+
+Every contraction step runs in the library's CUDA kernels; this module only
+converts Python/NumPy/PyTorch objects to the C ABI's plain pointers and sizes.
+The library is loaded from this package directory (built in-tree by
+``paper_2205_00393_gb300/build.py``); a missing library is an error.
+"""
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+FP32, SPLIT_TF32, SPLIT_BF16, SPLIT_BF16X2 = 0, 1, 2, 3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+class TNCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libtnc status %d: %s" % (status, msg))
+        self.status = status
+
+
+def lib_path():
+    return os.path.join(_HERE, "libtnc.so")
+
+
+def load_library():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError("libtnc.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_2205_00393_gb300.build)")
+    try:  # share the CUDA runtime already loaded by PyTorch, if any
+        import torch  # noqa: F401
+    except ImportError:
+        pass
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    c_i64p = P(ctypes.c_int64)
+    sigs = {
+        "tnc_create_network": [ctypes.c_int, P(ctypes.c_int), P(c_i64p), ctypes.c_int64, c_i64p,
+                               P(P(ctypes.c_float)), ctypes.c_int, c_i64p, P(ctypes.c_void_p)],
+        "tnc_set_tensor_data": [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_float)],
+        "tnc_leaf_bytes": [ctypes.c_void_p, P(ctypes.c_size_t)],
+        "tnc_upload_leaves": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+        "tnc_greedy_path": [ctypes.c_void_p, P(ctypes.c_int)],
+        "tnc_set_path": [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int)],
+        "tnc_find_slices": [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_double, c_i64p, P(ctypes.c_int), ctypes.c_int],
+        "tnc_set_slices": [ctypes.c_void_p, ctypes.c_int, c_i64p],
+        "tnc_workspace_bytes": [ctypes.c_void_p, ctypes.c_int64, P(ctypes.c_size_t)],
+        "tnc_set_workspace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+        "tnc_contract": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                         ctypes.c_void_p, ctypes.c_void_p],
+        "tnc_stats": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
+        "tnc_set_timing": [ctypes.c_void_p, ctypes.c_int],
+        "tnc_last_timings": [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                             c_i64p, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int), c_i64p],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.tnc_last_error.argtypes = []
+    lib.tnc_last_error.restype = ctypes.c_char_p
+    lib.tnc_destroy.argtypes = [ctypes.c_void_p]
+    lib.tnc_destroy.restype = None
+    _LIB = lib
+    return lib
+
+
+def _check(lib, st):
+    if st != 0:
+        raise TNCError(st, lib.tnc_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Network:
+    """A tensor network held by libtnc (Sec. 2.1.1: tensors = vertices,
+    indices = edges). ``tensors`` are complex arrays (rounded to complex64),
+    ``indices`` the index ids per tensor, ``dims`` the dimension per id and
+    ``open_ids`` the order of the result tensor."""
+
+    def __init__(self, tensors, indices, dims, open_ids):
+        self._lib = load_library()
+        self.n_tensors = len(tensors)
+        self.dims = np.asarray(dims, dtype=np.int64)
+        self.open_ids = tuple(int(e) for e in open_ids)
+        self._keep = []
+        ranks = (ctypes.c_int * self.n_tensors)(*[len(ix) for ix in indices])
+        idx_arrays = [np.ascontiguousarray(np.asarray(ix, dtype=np.int64)) for ix in indices]
+        data = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64)) for t in tensors]
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        FP = ctypes.POINTER(ctypes.c_float)
+        idx_ptrs = (I64P * self.n_tensors)(*[a.ctypes.data_as(I64P) for a in idx_arrays])
+        data_ptrs = (FP * self.n_tensors)(*[d.ctypes.data_as(FP) for d in data])
+        op = np.asarray(self.open_ids, dtype=np.int64)
+        h = ctypes.c_void_p()
+        st = self._lib.tnc_create_network(self.n_tensors, ranks, idx_ptrs, len(self.dims),
+                                          self.dims.ctypes.data_as(I64P), data_ptrs, len(op),
+                                          op.ctypes.data_as(I64P) if len(op) else None,
+                                          ctypes.byref(h))
+        _check(self._lib, st)
+        self._h = h
+        self.n_out = int(np.prod([self.dims[e] for e in self.open_ids])) if self.open_ids else 1
+        self.sliced = []
+        self._ws = None
+
+    @classmethod
+    def from_tn(cls, tn):
+        return cls(tn.tensors, tn.indices, tn.dims, tn.open_ids)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.tnc_destroy(h)
+            self._h = None
+
+    def greedy_path(self):
+        n = max(self.n_tensors - 1, 0)
+        buf = (ctypes.c_int * max(2 * n, 1))()
+        _check(self._lib, self._lib.tnc_greedy_path(self._h, buf))
+        return [(buf[2 * i], buf[2 * i + 1]) for i in range(n)]
+
+    def set_path(self, pairs):
+        flat = np.asarray(pairs, dtype=np.int32).reshape(-1)
+        arr = (ctypes.c_int * max(len(flat), 1))(*flat.tolist())
+        _check(self._lib, self._lib.tnc_set_path(self._h, len(flat) // 2, arr))
+        self.sliced = []
+
+    def find_slices(self, target_log2, seed, T0=1.0, Tf=1e-4, alpha=0.9, cap=4096):
+        out = (ctypes.c_int64 * cap)()
+        n = ctypes.c_int()
+        _check(self._lib, self._lib.tnc_find_slices(self._h, int(target_log2), int(seed) & (2**64 - 1),
+                                                    T0, Tf, alpha, out, ctypes.byref(n), cap))
+        return [int(out[i]) for i in range(n.value)]
+
+    def set_slices(self, ids):
+        ids = [int(e) for e in ids]
+        arr = (ctypes.c_int64 * max(len(ids), 1))(*ids)
+        _check(self._lib, self._lib.tnc_set_slices(self._h, len(ids), arr))
+        self.sliced = ids
+
+    @property
+    def n_slices(self):
+        return 1 << len(self.sliced)
+
+    def set_tensor_data(self, i, data):
+        d = np.ascontiguousarray(np.asarray(data, dtype=np.complex64))
+        _check(self._lib, self._lib.tnc_set_tensor_data(self._h, int(i),
+                                                         d.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def leaf_bytes(self):
+        n = ctypes.c_size_t()
+        _check(self._lib, self._lib.tnc_leaf_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def upload_leaves(self, packed_host_ptr, stream=None):
+        _check(self._lib, self._lib.tnc_upload_leaves(self._h, ctypes.c_void_p(packed_host_ptr),
+                                                       _stream_ptr(stream)))
+
+    def workspace_bytes(self, batch=1):
+        n = ctypes.c_size_t()
+        _check(self._lib, self._lib.tnc_workspace_bytes(self._h, int(batch), ctypes.byref(n)))
+        return n.value
+
+    def set_workspace(self, tensor):
+        """Hand a caller-owned (PyTorch) device buffer to the library as workspace."""
+        if tensor is None:
+            _check(self._lib, self._lib.tnc_set_workspace(self._h, None, 0))
+        else:
+            _check(self._lib, self._lib.tnc_set_workspace(self._h, ctypes.c_void_p(tensor.data_ptr()),
+                                                           tensor.numel() * tensor.element_size()))
+        self._ws = tensor
+
+    def contract(self, lo=0, hi=None, mode=FP32, out=None, stream=None):
+        """Sum over slices [lo, hi) of the sliced contraction, as a complex128
+        CUDA tensor of 2^n_open elements in open_ids order."""
+        import torch
+        if hi is None:
+            hi = self.n_slices
+        if out is None:
+            out = torch.empty(self.n_out, dtype=torch.complex128, device="cuda")
+        st = self._lib.tnc_contract(self._h, int(lo), int(hi), int(mode), ctypes.c_void_p(out.data_ptr()),
+                                    _stream_ptr(stream))
+        _check(self._lib, st)
+        return out
+
+    def set_timing(self, enable):
+        _check(self._lib, self._lib.tnc_set_timing(self._h, 1 if enable else 0))
+
+    def last_timings(self, cap=1 << 16):
+        """Per-launch records of the last contraction: list of dicts with node,
+        kind, batch, mnk_log2 and ms; plus the number of kernels launched."""
+        node = (ctypes.c_int * cap)()
+        kind = (ctypes.c_int * cap)()
+        batch = (ctypes.c_int * cap)()
+        mnk = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_float * cap)()
+        n = ctypes.c_int()
+        nl = ctypes.c_int64()
+        _check(self._lib, self._lib.tnc_last_timings(self._h, node, kind, batch, mnk, ms, cap,
+                                                      ctypes.byref(n), ctypes.byref(nl)))
+        recs = [dict(node=node[i], kind=kind[i], batch=batch[i], mnk_log2=mnk[i], ms=ms[i])
+                for i in range(n.value)]
+        return recs, nl.value
+
+    def stats(self):
+        cap = 1 << 22
+        buf = ctypes.create_string_buffer(cap)
+        _check(self._lib, self._lib.tnc_stats(self._h, buf, cap))
+        return json.loads(buf.value.decode())

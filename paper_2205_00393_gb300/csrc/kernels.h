@@ -1,0 +1,75 @@
+// Internal interface between the host executor (tnc_api.cpp) and the CUDA
+// kernels. Not part of the public C ABI.
+//
+// Tensors are complex64 arrays whose dimensions are all 2 internally: an index
+// of dimension 2^d is split into d binary modes (most significant first), so a
+// row-major tensor over indices is a row-major tensor over binary modes and
+// every permutation is a permutation of address bits. A pairwise contraction
+// (Sec. 2.1.1, TTGT form of Sec. 5.3.1: A's free modes first, contracted
+// modes last; B's contracted modes first) is then
+//     C[m, n] = sum_k A(m, k) B(k, n),   M = 2^mb, N = 2^nb, K = 2^kb,
+// with A(m, k) = A_base[sum_j bit_j(m) am[j] + sum_j bit_j(k) ak[j]] (and
+// likewise for B): the permutation is a per-bit stride table applied during
+// the operand load, never a separate pass. The output is row-major [m][n].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tnc {
+
+constexpr int kMaxBits = 40;      // binary modes per operand side
+constexpr int kMaxSliceBits = 16; // sliced modes of one leaf
+
+// One operand of a launch covering `batch` consecutive slices s = slice0 + z.
+// Element address for slice z: ptr + z * batch_stride + slice_offset(s) + ...
+// where slice_offset(s) = sum_j ((s >> sl_bit[j]) & 1) * sl_stride[j] fixes the
+// sliced modes of a leaf (Sec. 2.1.1: a sliced index takes one value per task).
+struct Operand {
+    const float2* ptr;
+    int64_t batch_stride;
+    int n_sl;
+    int sl_bit[kMaxSliceBits];
+    int64_t sl_stride[kMaxSliceBits];
+};
+
+struct GemmParams {
+    Operand A, B;
+    float2* C;
+    int64_t c_batch_stride;
+    int mb, nb, kb;
+    int64_t am[kMaxBits], ak[kMaxBits], bk[kMaxBits], bn[kMaxBits];
+    int64_t slice0;
+};
+
+// Final contraction whose output has R = 2^(mb+nb) <= 64 elements: FP64
+// partial sums over chunks of K (Sec. 2.1.1: results of all subtasks are
+// accumulated; the reduction runs in FP64 in a fixed order).
+struct RootParams {
+    GemmParams g;
+    int chunks;       // K is split into `chunks` equal parts (power of two)
+};
+
+// Accumulate an FP32 tensor of R = 2^obits elements per slice into the FP64
+// result: out[r] += sum_z src_z[ sum_j bit_j(r) ostride[j] ] (r in result order).
+struct SumParams {
+    Operand src;
+    int obits;
+    int64_t ostride[kMaxBits];
+    int64_t slice0;
+};
+
+// Result-order permutation for accumulating FP64 partials laid out in the
+// root's own order.
+struct PermParams {
+    int obits;
+    int64_t ostride[kMaxBits];
+};
+
+cudaError_t launch_gemm_f32(const GemmParams& p, int batch, cudaStream_t s);
+cudaError_t launch_root_partials(const RootParams& p, int batch, double2* partials, cudaStream_t s);
+cudaError_t launch_accumulate_partials(const double2* partials, int count, const PermParams& pp,
+                                       double2* out, cudaStream_t s);
+cudaError_t launch_slice_sum_f32(const SumParams& p, int batch, double2* out, cudaStream_t s);
+
+}  // namespace tnc

@@ -1,0 +1,762 @@
+// C ABI of libtnc (declared in include/tnc.h) and the host-side executor.
+//
+// Execution of tnc_contract over slices [lo, hi) (Sec. 2.1.1: slicing turns
+// the contraction into 2^|S| independent subtasks whose results are summed):
+//  1. Contraction nodes whose subtree holds no sliced index give the same
+//     tensor in every slice (Sec. 3.1: only tensors on a sliced index's
+//     lifetime change); they run once per call, batch 1.
+//  2. The remaining nodes run for a batch of consecutive slices per launch
+//     (grid z = slice within the batch), in SSA order.
+//  3. The root contraction reduces in FP64 and is accumulated into the
+//     caller's complex128 result in a fixed order.
+// Intermediates live in one workspace arena whose offsets are planned on the
+// host by a first-fit simulation of the tensors' lifetimes.
+#include "tnc.h"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <set>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "planner.hpp"
+
+namespace {
+
+thread_local std::string g_err;
+
+tnc_status fail(tnc_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return fail(_e == cudaErrorMemoryAllocation ? TNC_E_OOM : TNC_E_CUDA,        \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));             \
+    } while (0)
+
+constexpr int64_t kAlign = 256;
+
+int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Kernel chosen for a contraction node.
+enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2 };
+
+struct NodePlan {
+    int v = 0;            // tensor id produced
+    int A = 0, B = 0;     // operand tensor ids
+    int mb = 0, nb = 0, kb = 0;
+    std::vector<int64_t> am, ak, bk, bn;
+    bool per_slice = true;
+    bool is_root = false;
+    int kind = K_GEMM_F32;
+    int chunks = 1;       // root reduction chunks
+};
+
+struct Plan {
+    bool valid = false;
+    std::vector<int> slice_bit_of_mode;                     // by mode, -1 if not sliced
+    std::vector<std::vector<int>> layout;                   // effective modes per tensor
+    std::vector<std::vector<std::pair<int, int64_t>>> str;  // (mode, stride) per tensor
+    std::vector<std::vector<std::pair<int, int64_t>>> sl;   // leaves: (slice bit, stride)
+    std::vector<char> per_slice;
+    std::vector<NodePlan> nodes;                            // SSA order
+    std::vector<int64_t> out_stride;                        // result-order bit j -> root offset
+    int obits = 0;
+};
+
+struct Arena {
+    std::vector<int64_t> off;      // byte offset per tensor (-1 = none)
+    int64_t root_scratch_off = -1; // FP64 partials or FP32 per-slice root
+    int64_t peak = 0;
+};
+
+int64_t stride_of(const std::vector<std::pair<int, int64_t>>& s, int mode) {
+    for (auto& p : s)
+        if (p.first == mode) return p.second;
+    return -1;
+}
+
+}  // namespace
+
+struct tnc_net {
+    // network
+    int n_leaves = 0;
+    std::vector<std::vector<int64_t>> leaf_idx;
+    std::vector<int> logd;          // by index id (0 for ids not present)
+    std::vector<char> present;
+    std::vector<int64_t> open_ids;
+    std::vector<int> mode_base;     // first binary mode of an index id
+    std::vector<int64_t> leaf_off;  // element offsets in the packed leaf buffer
+    std::vector<int64_t> leaf_elems;
+    std::vector<float> host_leaves; // packed complex64
+    int64_t total_leaf_elems = 0;
+    // device
+    float2* d_leaves = nullptr;
+    bool dev_dirty = true;
+    // path and slices
+    std::vector<tnc::Pair> path;
+    std::unique_ptr<tnc::Tree> tree;
+    std::vector<int64_t> S;         // as given
+    std::vector<int64_t> S_sorted;
+    Plan plan;
+    // workspace
+    void* ws_user = nullptr;
+    size_t ws_user_bytes = 0;
+    void* ws_own = nullptr;
+    size_t ws_own_bytes = 0;
+    int64_t last_batch = 0;
+    // per-launch timing (tnc_set_timing) and launch accounting
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct TimedLaunch { int node; int kind; int batch; size_t ev; };
+    std::vector<TimedLaunch> timed;
+    int64_t launches = 0;
+
+    ~tnc_net() {
+        if (d_leaves) cudaFree(d_leaves);
+        if (ws_own) cudaFree(ws_own);
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+// ------------------------------------------------------------- planning ----
+
+void build_plan(tnc_net* net) {
+    Plan& P = net->plan;
+    P = Plan();
+    const tnc::Tree& T = *net->tree;
+    const int nt = T.n_tensors();
+    int total_modes = net->mode_base.empty() ? 0 : net->mode_base.back();
+    P.slice_bit_of_mode.assign(total_modes, -1);
+    for (size_t j = 0; j < net->S_sorted.size(); ++j)
+        P.slice_bit_of_mode[net->mode_base[net->S_sorted[j]]] = (int)j;
+    P.layout.resize(nt);
+    P.str.resize(nt);
+    P.sl.resize(nt);
+    P.per_slice.assign(nt, 0);
+    auto modes_of = [&](int64_t e) {
+        std::vector<int> m;
+        for (int b = 0; b < net->logd[e]; ++b) m.push_back(net->mode_base[e] + b);
+        return m;
+    };
+    for (int v = 0; v < net->n_leaves; ++v) {
+        std::vector<int> full;
+        for (int64_t e : net->leaf_idx[v])
+            for (int m : modes_of(e)) full.push_back(m);
+        const int L = (int)full.size();
+        for (int p = 0; p < L; ++p) {
+            int64_t st = 1ll << (L - 1 - p);
+            int sb = P.slice_bit_of_mode[full[p]];
+            if (sb >= 0) {
+                P.sl[v].emplace_back(sb, st);
+                P.per_slice[v] = 1;
+            } else {
+                P.layout[v].push_back(full[p]);
+                P.str[v].emplace_back(full[p], st);
+            }
+        }
+        if ((int)P.sl[v].size() > tnc::kMaxSliceBits)
+            throw tnc::PlanError("leaf " + std::to_string(v) + " has more than 16 sliced modes");
+    }
+    for (size_t i = 0; i < T.children.size(); ++i) {
+        const int v = net->n_leaves + (int)i;
+        int c0 = T.children[i].first, c1 = T.children[i].second;
+        std::set<int> s0(P.layout[c0].begin(), P.layout[c0].end());
+        std::set<int> s1(P.layout[c1].begin(), P.layout[c1].end());
+        std::vector<int> f0, f1;
+        for (int m : P.layout[c0])
+            if (!s1.count(m)) f0.push_back(m);
+        for (int m : P.layout[c1])
+            if (!s0.count(m)) f1.push_back(m);
+        NodePlan np;
+        np.v = v;
+        np.A = c0;
+        np.B = c1;
+        if (f1.size() > f0.size()) {
+            std::swap(np.A, np.B);
+            std::swap(f0, f1);
+        }
+        const std::set<int>& sB = (np.B == c1) ? s1 : s0;
+        std::vector<int> kmodes;
+        for (int m : P.layout[np.A])
+            if (sB.count(m)) kmodes.push_back(m);
+        np.mb = (int)f0.size();
+        np.nb = (int)f1.size();
+        np.kb = (int)kmodes.size();
+        if (np.mb > tnc::kMaxBits || np.nb > tnc::kMaxBits || np.kb > tnc::kMaxBits)
+            throw tnc::PlanError("contraction node " + std::to_string(i) + " exceeds 40 modes per side");
+        for (int j = 0; j < np.mb; ++j) np.am.push_back(stride_of(P.str[np.A], f0[np.mb - 1 - j]));
+        for (int j = 0; j < np.kb; ++j) {
+            np.ak.push_back(stride_of(P.str[np.A], kmodes[np.kb - 1 - j]));
+            np.bk.push_back(stride_of(P.str[np.B], kmodes[np.kb - 1 - j]));
+        }
+        for (int j = 0; j < np.nb; ++j) np.bn.push_back(stride_of(P.str[np.B], f1[np.nb - 1 - j]));
+        std::vector<int> out(f0);
+        out.insert(out.end(), f1.begin(), f1.end());
+        const int L = (int)out.size();
+        if (L > 36)
+            throw tnc::PlanError("intermediate " + std::to_string(v) + " keeps 2^" + std::to_string(L) +
+                                 " elements after slicing; slice more indices");
+        for (int p = 0; p < L; ++p) P.str[v].emplace_back(out[p], 1ll << (L - 1 - p));
+        P.layout[v] = out;
+        P.per_slice[v] = P.per_slice[c0] || P.per_slice[c1];
+        np.is_root = (v == T.root);
+        np.per_slice = P.per_slice[v] || np.is_root;
+        if (np.is_root) {
+            if (np.mb + np.nb <= 6) {
+                np.kind = K_ROOT_F64;
+                int64_t K = 1ll << np.kb;
+                int64_t ch = K / 1024;
+                if (ch < 1) ch = 1;
+                if (ch > 1024) ch = 1024;
+                np.chunks = (int)ch;
+            } else {
+                np.kind = K_GEMM_ROOT_SUM;
+            }
+        } else {
+            np.kind = K_GEMM_F32;
+        }
+        P.nodes.push_back(np);
+    }
+    // result order: open_ids, each expanded MSB first; bit j counts from the last mode
+    const int root = T.root;
+    std::vector<int> omodes;
+    for (int64_t e : net->open_ids)
+        for (int m : modes_of(e)) omodes.push_back(m);
+    P.obits = (int)omodes.size();
+    if (P.obits > tnc::kMaxBits) throw tnc::PlanError("more than 40 open modes");
+    for (int j = 0; j < P.obits; ++j) {
+        int64_t st = stride_of(P.str[root], omodes[P.obits - 1 - j]);
+        if (st < 0) throw tnc::PlanError("open mode missing from the result");
+        P.out_stride.push_back(st);
+    }
+    P.valid = true;
+}
+
+int64_t tensor_bytes(const Plan& P, int v) { return (int64_t)8 << P.layout[v].size(); }
+
+// First-fit simulation of the workspace for a batch of `nb` slices.
+Arena plan_arena(const tnc_net* net, int64_t nb) {
+    const Plan& P = net->plan;
+    const tnc::Tree& T = *net->tree;
+    Arena ar;
+    ar.off.assign(T.n_tensors(), -1);
+    std::map<int64_t, int64_t> used;  // off -> len
+    int64_t top = 0;
+    auto alloc = [&](int64_t len) {
+        len = align_up(len);
+        int64_t prev_end = 0;
+        for (auto& kv : used) {
+            if (kv.first - prev_end >= len) break;
+            prev_end = kv.first + kv.second;
+        }
+        int64_t off = prev_end;
+        used[off] = len;
+        top = std::max(top, off + len);
+        return off;
+    };
+    auto release = [&](int64_t off) { used.erase(off); };
+    // phase 1: invariant nodes
+    for (const NodePlan& np : P.nodes) {
+        if (np.per_slice) continue;
+        ar.off[np.v] = alloc(tensor_bytes(P, np.v));
+        for (int c : {np.A, np.B})
+            if (c >= net->n_leaves) release(ar.off[c]);
+    }
+    // phase 2: one batch of per-slice nodes
+    for (const NodePlan& np : P.nodes) {
+        if (!np.per_slice) continue;
+        if (np.is_root) {
+            int64_t bytes = np.kind == K_ROOT_F64
+                                ? nb * np.chunks * (int64_t)16 << (np.mb + np.nb)
+                                : nb * tensor_bytes(P, np.v);
+            ar.root_scratch_off = alloc(bytes);
+        } else {
+            ar.off[np.v] = alloc(nb * tensor_bytes(P, np.v));
+        }
+        for (int c : {np.A, np.B})
+            if (c >= net->n_leaves && P.per_slice[c]) release(ar.off[c]);
+    }
+    ar.peak = top;
+    return ar;
+}
+
+tnc::Operand operand(const tnc_net* net, const Arena& ar, char* ws, int v, int64_t nb) {
+    const Plan& P = net->plan;
+    tnc::Operand op{};
+    if (v < net->n_leaves) {
+        op.ptr = net->d_leaves + net->leaf_off[v];
+        op.batch_stride = 0;
+        op.n_sl = (int)P.sl[v].size();
+        for (int j = 0; j < op.n_sl; ++j) {
+            op.sl_bit[j] = P.sl[v][j].first;
+            op.sl_stride[j] = P.sl[v][j].second;
+        }
+    } else {
+        op.ptr = reinterpret_cast<const float2*>(ws + ar.off[v]);
+        op.batch_stride = P.per_slice[v] ? (tensor_bytes(P, v) / 8) : 0;
+        op.n_sl = 0;
+    }
+    (void)nb;
+    return op;
+}
+
+tnc::GemmParams gemm_params(const tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int64_t nb) {
+    tnc::GemmParams g{};
+    g.A = operand(net, ar, ws, np.A, nb);
+    g.B = operand(net, ar, ws, np.B, nb);
+    g.mb = np.mb;
+    g.nb = np.nb;
+    g.kb = np.kb;
+    for (int j = 0; j < np.mb; ++j) g.am[j] = np.am[j];
+    for (int j = 0; j < np.kb; ++j) {
+        g.ak[j] = np.ak[j];
+        g.bk[j] = np.bk[j];
+    }
+    for (int j = 0; j < np.nb; ++j) g.bn[j] = np.bn[j];
+    return g;
+}
+
+tnc_status ensure_plan(tnc_net* net) {
+    if (!net->tree) return fail(TNC_E_STATE, "no contraction path set (call tnc_set_path)");
+    if (!net->plan.valid) {
+        try {
+            build_plan(net);
+        } catch (const std::exception& e) {
+            return fail(TNC_E_INVALID, e.what());
+        }
+    }
+    return TNC_OK;
+}
+
+tnc_status ensure_leaves(tnc_net* net, cudaStream_t st) {
+    if (!net->d_leaves) {
+        CUDA_TRY(cudaMalloc(&net->d_leaves, std::max<int64_t>(8, net->total_leaf_elems * 8)));
+        net->dev_dirty = true;
+    }
+    if (net->dev_dirty) {
+        CUDA_TRY(cudaMemcpyAsync(net->d_leaves, net->host_leaves.data(), net->total_leaf_elems * 8,
+                                 cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));  // pageable source: keep the host copy stable
+        net->dev_dirty = false;
+    }
+    return TNC_OK;
+}
+
+// Event pair around one launch when timing is on; returns the pool slot.
+cudaError_t timed_begin(tnc_net* net, int node, int kind, int batch, cudaStream_t s) {
+    net->launches += 1;
+    if (!net->timing) return cudaSuccess;
+    size_t slot = net->timed.size() * 2;
+    while (net->ev_pool.size() < slot + 2) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        net->ev_pool.push_back(e);
+    }
+    net->timed.push_back({node, kind, batch, slot});
+    return cudaEventRecord(net->ev_pool[slot], s);
+}
+
+cudaError_t timed_end(tnc_net* net, cudaStream_t s) {
+    if (!net->timing) return cudaSuccess;
+    return cudaEventRecord(net->ev_pool[net->timed.back().ev + 1], s);
+}
+
+int64_t pick_batch(const tnc_net* net, int64_t want, size_t budget) {
+    int64_t lo = 1, hi = std::max<int64_t>(1, std::min<int64_t>(want, 65535));
+    if ((size_t)plan_arena(net, 1).peak > budget) return 0;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if ((size_t)plan_arena(net, mid).peak <= budget) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char* tnc_last_error(void) { return g_err.c_str(); }
+
+tnc_status tnc_create_network(int n_tensors, const int* ranks, const int64_t* const* index_ids,
+                              int64_t n_indices, const int64_t* index_dims, const float* const* data_c64,
+                              int n_open, const int64_t* open_ids, tnc_net_t* out) {
+    if (!out) return fail(TNC_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n_tensors < 1) return fail(TNC_E_INVALID, "n_tensors must be >= 1");
+    if (n_indices < 0 || n_indices > (1ll << 30)) return fail(TNC_E_INVALID, "n_indices out of range");
+    if (!ranks || !index_ids || !data_c64 || (n_indices > 0 && !index_dims))
+        return fail(TNC_E_INVALID, "NULL argument");
+    std::unique_ptr<tnc_net> net(new tnc_net());
+    net->n_leaves = n_tensors;
+    net->logd.assign(n_indices, 0);
+    net->present.assign(n_indices, 0);
+    for (int64_t e = 0; e < n_indices; ++e) {
+        int64_t d = index_dims[e];
+        if (d < 1 || (d & (d - 1))) return fail(TNC_E_INVALID, "index " + std::to_string(e) + " has a dimension that is not a power of two");
+        net->logd[e] = 63 - __builtin_clzll((unsigned long long)d);
+    }
+    std::vector<int> count(n_indices, 0);
+    for (int i = 0; i < n_tensors; ++i) {
+        if (ranks[i] < 0) return fail(TNC_E_INVALID, "negative rank");
+        if (ranks[i] > 0 && !index_ids[i]) return fail(TNC_E_INVALID, "NULL index list");
+        std::vector<int64_t> idx(index_ids[i], index_ids[i] + ranks[i]);
+        std::set<int64_t> seen;
+        int bits = 0;
+        for (int64_t e : idx) {
+            if (e < 0 || e >= n_indices) return fail(TNC_E_INVALID, "index id out of range in tensor " + std::to_string(i));
+            if (!seen.insert(e).second) return fail(TNC_E_INVALID, "index repeated within tensor " + std::to_string(i));
+            count[e] += 1;
+            net->present[e] = 1;
+            bits += net->logd[e];
+        }
+        if (bits > 31) return fail(TNC_E_INVALID, "tensor " + std::to_string(i) + " exceeds 2^31 elements");
+        net->leaf_idx.push_back(idx);
+        net->leaf_off.push_back(net->total_leaf_elems);
+        net->leaf_elems.push_back(1ll << bits);
+        net->total_leaf_elems += 1ll << bits;
+    }
+    for (int64_t e = 0; e < n_indices; ++e)
+        if (count[e] > 2) return fail(TNC_E_INVALID, "index " + std::to_string(e) + " joins more than two tensors");
+    std::set<int64_t> open_set;
+    if (n_open < 0 || (n_open > 0 && !open_ids)) return fail(TNC_E_INVALID, "bad open index list");
+    for (int j = 0; j < n_open; ++j) {
+        int64_t e = open_ids[j];
+        if (e < 0 || e >= n_indices || count[e] != 1) return fail(TNC_E_INVALID, "open index " + std::to_string(e) + " must belong to exactly one tensor");
+        if (!open_set.insert(e).second) return fail(TNC_E_INVALID, "open index repeated");
+        net->open_ids.push_back(e);
+    }
+    for (int64_t e = 0; e < n_indices; ++e)
+        if (count[e] == 1 && !open_set.count(e)) return fail(TNC_E_INVALID, "index " + std::to_string(e) + " belongs to one tensor but is not open");
+    net->mode_base.assign(n_indices + 1, 0);
+    for (int64_t e = 0; e < n_indices; ++e) net->mode_base[e + 1] = net->mode_base[e] + net->logd[e];
+    net->host_leaves.resize(net->total_leaf_elems * 2);
+    for (int i = 0; i < n_tensors; ++i) {
+        if (!data_c64[i]) return fail(TNC_E_INVALID, "NULL tensor data");
+        std::memcpy(net->host_leaves.data() + 2 * net->leaf_off[i], data_c64[i], net->leaf_elems[i] * 8);
+    }
+    *out = net.release();
+    return TNC_OK;
+}
+
+tnc_status tnc_set_tensor_data(tnc_net_t net, int tensor, const float* data_c64) {
+    if (!net || !data_c64) return fail(TNC_E_INVALID, "NULL argument");
+    if (tensor < 0 || tensor >= net->n_leaves) return fail(TNC_E_INVALID, "tensor out of range");
+    std::memcpy(net->host_leaves.data() + 2 * net->leaf_off[tensor], data_c64, net->leaf_elems[tensor] * 8);
+    net->dev_dirty = true;
+    return TNC_OK;
+}
+
+tnc_status tnc_leaf_bytes(tnc_net_t net, size_t* bytes) {
+    if (!net || !bytes) return fail(TNC_E_INVALID, "NULL argument");
+    *bytes = (size_t)net->total_leaf_elems * 8;
+    return TNC_OK;
+}
+
+tnc_status tnc_upload_leaves(tnc_net_t net, const float* packed, void* stream) {
+    if (!net || !packed) return fail(TNC_E_INVALID, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!net->d_leaves) CUDA_TRY(cudaMalloc(&net->d_leaves, std::max<int64_t>(8, net->total_leaf_elems * 8)));
+    std::memcpy(net->host_leaves.data(), packed, net->total_leaf_elems * 8);
+    CUDA_TRY(cudaMemcpyAsync(net->d_leaves, packed, net->total_leaf_elems * 8, cudaMemcpyHostToDevice, st));
+    net->dev_dirty = false;
+    return TNC_OK;
+}
+
+tnc_status tnc_greedy_path(tnc_net_t net, int* pairs_out) {
+    if (!net || (!pairs_out && net->n_leaves > 1)) return fail(TNC_E_INVALID, "NULL argument");
+    try {
+        auto p = tnc::greedy_path(net->leaf_idx, net->logd);
+        for (size_t i = 0; i < p.size(); ++i) {
+            pairs_out[2 * i] = p[i].first;
+            pairs_out[2 * i + 1] = p[i].second;
+        }
+    } catch (const std::exception& e) {
+        return fail(TNC_E_INVALID, e.what());
+    }
+    return TNC_OK;
+}
+
+tnc_status tnc_set_path(tnc_net_t net, int n_steps, const int* pairs) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (n_steps != net->n_leaves - 1) return fail(TNC_E_INVALID, "path must have n_tensors - 1 steps");
+    if (n_steps > 0 && !pairs) return fail(TNC_E_INVALID, "NULL pairs");
+    std::vector<tnc::Pair> path;
+    for (int i = 0; i < n_steps; ++i) path.emplace_back(pairs[2 * i], pairs[2 * i + 1]);
+    try {
+        auto tree = std::make_unique<tnc::Tree>(net->leaf_idx, net->logd, net->open_ids, path);
+        for (int v = 0; v < tree->n_tensors(); ++v)
+            if (tree->size_log(v) > 120) return fail(TNC_E_INVALID, "an intermediate tensor exceeds 2^120 elements");
+        net->tree = std::move(tree);
+    } catch (const std::exception& e) {
+        return fail(TNC_E_INVALID, e.what());
+    }
+    net->path = path;
+    net->S.clear();
+    net->S_sorted.clear();
+    net->plan.valid = false;
+    return TNC_OK;
+}
+
+tnc_status tnc_find_slices(tnc_net_t net, int target_log2, uint64_t seed, double T0, double Tf, double alpha,
+                           int64_t* out_ids, int* n_out, int cap) {
+    if (!net || !n_out) return fail(TNC_E_INVALID, "NULL argument");
+    if (!net->tree) return fail(TNC_E_STATE, "no contraction path set (call tnc_set_path)");
+    if (T0 <= 0) T0 = 1.0;
+    if (Tf <= 0) Tf = 1e-4;
+    if (alpha <= 0 || alpha >= 1) alpha = 0.9;
+    try {
+        auto S1 = tnc::slice_finder(*net->tree, target_log2);
+        auto S = tnc::slice_refiner(*net->tree, target_log2, S1, seed, T0, Tf, alpha);
+        *n_out = (int)S.size();
+        if ((int)S.size() > cap || (!out_ids && !S.empty()))
+            return fail(TNC_E_INVALID, "out_ids capacity too small: need " + std::to_string(S.size()));
+        for (size_t i = 0; i < S.size(); ++i) out_ids[i] = S[i];
+    } catch (const std::exception& e) {
+        return fail(TNC_E_INVALID, e.what());
+    }
+    return TNC_OK;
+}
+
+tnc_status tnc_set_slices(tnc_net_t net, int n, const int64_t* ids) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (!net->tree) return fail(TNC_E_STATE, "no contraction path set (call tnc_set_path)");
+    if (n < 0 || n > 62 || (n > 0 && !ids)) return fail(TNC_E_INVALID, "bad slice count");
+    std::set<int64_t> seen;
+    for (int j = 0; j < n; ++j) {
+        int64_t e = ids[j];
+        if (e < 0 || e >= (int64_t)net->logd.size() || !net->present[e]) return fail(TNC_E_INVALID, "sliced index " + std::to_string(e) + " not in the network");
+        if (net->tree->is_open[e]) return fail(TNC_E_INVALID, "sliced index " + std::to_string(e) + " is open");
+        if (net->logd[e] != 1) return fail(TNC_E_INVALID, "sliced index " + std::to_string(e) + " must have dimension 2");
+        if (!seen.insert(e).second) return fail(TNC_E_INVALID, "sliced index repeated");
+    }
+    net->S.assign(ids, ids + n);
+    net->S_sorted.assign(seen.begin(), seen.end());
+    net->plan.valid = false;
+    return TNC_OK;
+}
+
+tnc_status tnc_workspace_bytes(tnc_net_t net, int64_t max_batch, size_t* bytes) {
+    if (!net || !bytes || max_batch < 1) return fail(TNC_E_INVALID, "bad argument");
+    tnc_status st = ensure_plan(net);
+    if (st != TNC_OK) return st;
+    *bytes = (size_t)plan_arena(net, max_batch).peak;
+    return TNC_OK;
+}
+
+tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (((uintptr_t)dev_ptr) % kAlign) return fail(TNC_E_INVALID, "workspace must be 256-byte aligned");
+    net->ws_user = dev_ptr;
+    net->ws_user_bytes = dev_ptr ? bytes : 0;
+    return TNC_OK;
+}
+
+tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double* out_c128, void* stream) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (!out_c128) return fail(TNC_E_INVALID, "NULL output");
+    if (mode != TNC_FP32 && mode != TNC_SPLIT_TF32 && mode != TNC_SPLIT_BF16 && mode != TNC_SPLIT_BF16X2)
+        return fail(TNC_E_INVALID, "unknown mode");
+    if (mode != TNC_FP32) return fail(TNC_E_INVALID, "split tensor-core modes are not available in this build");
+    tnc_status st = ensure_plan(net);
+    if (st != TNC_OK) return st;
+    const int64_t n_slices = 1ll << net->S_sorted.size();
+    if (lo < 0 || hi < lo || hi > n_slices) return fail(TNC_E_INVALID, "slice range outside [0, 2^|S|]");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Plan& P = net->plan;
+    const int64_t R = 1ll << P.obits;
+    CUDA_TRY(cudaMemsetAsync(out_c128, 0, R * 16, s));
+    if (hi == lo) return TNC_OK;
+    if ((st = ensure_leaves(net, s)) != TNC_OK) return st;
+
+    // workspace and batch
+    char* ws = nullptr;
+    int64_t nb = 0;
+    const int64_t want = hi - lo;
+    if (net->ws_user) {
+        nb = pick_batch(net, want, net->ws_user_bytes);
+        if (nb < 1) return fail(TNC_E_OOM, "workspace too small for one slice");
+        ws = (char*)net->ws_user;
+    } else {
+        size_t one = (size_t)plan_arena(net, 1).peak;
+        size_t budget = std::max<size_t>(one, (size_t)1 << 30);
+        nb = pick_batch(net, std::min<int64_t>(want, 1024), budget);
+        size_t need = (size_t)plan_arena(net, nb).peak;
+        if (net->ws_own_bytes < need) {
+            if (net->ws_own) CUDA_TRY(cudaFree(net->ws_own));
+            net->ws_own = nullptr;
+            net->ws_own_bytes = 0;
+            CUDA_TRY(cudaMalloc(&net->ws_own, std::max<size_t>(need, kAlign)));
+            net->ws_own_bytes = need;
+        }
+        ws = (char*)net->ws_own;
+    }
+    net->last_batch = nb;
+    const Arena ar = plan_arena(net, nb);
+
+    // invariant nodes once
+    for (const NodePlan& np : P.nodes) {
+        if (np.per_slice) continue;
+        tnc::GemmParams g = gemm_params(net, ar, ws, np, 1);
+        g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
+        g.c_batch_stride = 0;
+        g.slice0 = 0;
+        CUDA_TRY(timed_begin(net, np.v, np.kind, 1, s));
+        CUDA_TRY(tnc::launch_gemm_f32(g, 1, s));
+        CUDA_TRY(timed_end(net, s));
+    }
+    tnc::PermParams pp{};
+    pp.obits = P.obits;
+    for (int j = 0; j < P.obits; ++j) pp.ostride[j] = P.out_stride[j];
+    double2* out = reinterpret_cast<double2*>(out_c128);
+
+    for (int64_t s0 = lo; s0 < hi; s0 += nb) {
+        const int b = (int)std::min<int64_t>(nb, hi - s0);
+        if (P.nodes.empty()) {  // a single leaf: the result is the leaf itself
+            tnc::SumParams sp{};
+            sp.src = operand(net, ar, ws, 0, b);
+            sp.obits = P.obits;
+            for (int j = 0; j < P.obits; ++j) sp.ostride[j] = P.out_stride[j];
+            sp.slice0 = s0;
+            CUDA_TRY(timed_begin(net, 0, -1, b, s));
+            CUDA_TRY(tnc::launch_slice_sum_f32(sp, b, out, s));
+            CUDA_TRY(timed_end(net, s));
+            continue;
+        }
+        for (const NodePlan& np : P.nodes) {
+            if (!np.per_slice) continue;
+            tnc::GemmParams g = gemm_params(net, ar, ws, np, b);
+            g.slice0 = s0;
+            CUDA_TRY(timed_begin(net, np.v, np.kind, b, s));
+            if (!np.is_root) {
+                g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
+                g.c_batch_stride = tensor_bytes(P, np.v) / 8;
+                CUDA_TRY(tnc::launch_gemm_f32(g, b, s));
+            } else if (np.kind == K_ROOT_F64) {
+                tnc::RootParams rp{};
+                rp.g = g;
+                rp.chunks = np.chunks;
+                double2* partials = reinterpret_cast<double2*>(ws + ar.root_scratch_off);
+                CUDA_TRY(tnc::launch_root_partials(rp, b, partials, s));
+                net->launches += 1;
+                CUDA_TRY(tnc::launch_accumulate_partials(partials, b * np.chunks, pp, out, s));
+            } else {
+                float2* rootbuf = reinterpret_cast<float2*>(ws + ar.root_scratch_off);
+                g.C = rootbuf;
+                g.c_batch_stride = tensor_bytes(P, np.v) / 8;
+                CUDA_TRY(tnc::launch_gemm_f32(g, b, s));
+                net->launches += 1;
+                tnc::SumParams sp{};
+                sp.src.ptr = rootbuf;
+                sp.src.batch_stride = g.c_batch_stride;
+                sp.src.n_sl = 0;
+                sp.obits = P.obits;
+                for (int j = 0; j < P.obits; ++j) sp.ostride[j] = P.out_stride[j];
+                sp.slice0 = s0;
+                CUDA_TRY(tnc::launch_slice_sum_f32(sp, b, out, s));
+            }
+            CUDA_TRY(timed_end(net, s));
+        }
+    }
+    return TNC_OK;
+}
+
+tnc_status tnc_set_timing(tnc_net_t net, int enable) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    net->timing = enable != 0;
+    net->timed.clear();
+    net->launches = 0;
+    return TNC_OK;
+}
+
+tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, int64_t* mnk_log2,
+                            float* ms, int cap, int* n_out, int64_t* n_launches) {
+    if (!net || !n_out) return fail(TNC_E_INVALID, "NULL argument");
+    if (n_launches) *n_launches = net->launches;
+    *n_out = (int)net->timed.size();
+    if ((int)net->timed.size() > cap) return fail(TNC_E_INVALID, "capacity too small");
+    for (size_t i = 0; i < net->timed.size(); ++i) {
+        const auto& t = net->timed[i];
+        float v = 0.f;
+        CUDA_TRY(cudaEventSynchronize(net->ev_pool[t.ev + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&v, net->ev_pool[t.ev], net->ev_pool[t.ev + 1]));
+        if (node) node[i] = t.node;
+        if (kind) kind[i] = t.kind;
+        if (batch) batch[i] = t.batch;
+        if (ms) ms[i] = v;
+        if (mnk_log2) {
+            int64_t x = 0;
+            if (t.node >= net->n_leaves) {
+                const NodePlan& np = net->plan.nodes[t.node - net->n_leaves];
+                x = np.mb + np.nb + np.kb;
+            }
+            mnk_log2[i] = x;
+        }
+    }
+    return TNC_OK;
+}
+
+tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
+    if (!net || !json) return fail(TNC_E_INVALID, "NULL argument");
+    if (!net->tree) return fail(TNC_E_STATE, "no contraction path set (call tnc_set_path)");
+    const tnc::Tree& T = *net->tree;
+    std::ostringstream o;
+    tnc::Wide e1 = T.eq1(), e3 = T.eq3(net->S);
+    o << "{\"n_leaves\":" << net->n_leaves << ",\"n_nodes\":" << T.children.size();
+    o << ",\"eq1\":\"" << e1.to_string() << "\",\"eq3\":\"" << e3.to_string() << "\"";
+    o << ",\"overhead\":" << (e3.to_double() / e1.to_double());
+    o << ",\"sliced\":[";
+    for (size_t i = 0; i < net->S.size(); ++i) o << (i ? "," : "") << net->S[i];
+    o << "]";
+    std::vector<char> sl(T.logd.size(), 0);
+    for (int64_t e : net->S) sl[e] = 1;
+    int w = 0;
+    for (int v = 0; v < T.n_tensors(); ++v) w = std::max(w, T.dim(v, sl));
+    o << ",\"max_log2_size\":" << w;
+    std::string perr;
+    if (!net->plan.valid) {
+        try {
+            build_plan(net);
+        } catch (const std::exception& e) {
+            perr = e.what();
+        }
+    }
+    if (net->plan.valid) {
+        o << ",\"workspace_batch1\":" << plan_arena(net, 1).peak;
+        o << ",\"last_batch\":" << net->last_batch;
+        o << ",\"nodes\":[";
+        bool first = true;
+        for (const NodePlan& np : net->plan.nodes) {
+            o << (first ? "" : ",") << "[" << np.mb << "," << np.nb << "," << np.kb << ","
+              << (np.per_slice ? 1 : 0) << "," << np.kind << "]";
+            first = false;
+        }
+        o << "]";
+    } else {
+        o << ",\"plan_error\":\"" << perr << "\"";
+    }
+    o << "}";
+    std::string s = o.str();
+    if (s.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small: need " + std::to_string(s.size() + 1));
+    std::memcpy(json, s.c_str(), s.size() + 1);
+    return TNC_OK;
+}
+
+void tnc_destroy(tnc_net_t net) { delete net; }
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+"""CPU-side tests of libtnc: the library loads and exports every entry point
+of include/tnc.h, validates its inputs, and its host planner matches the
+oracle's planning twin bit for bit (greedy paths, slicing sets in insertion
+order, Eq. 1/Eq. 3 costs). No GPU call is made here."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tnc_inputs import circuit_to_network, grid_rqc, lattice_53q_rqc
+from oracle import planner
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:tnc_status|const char\*|void)\s+(tnc_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_exports_every_declared_symbol(libtnc):
+    names = _declared()
+    assert {"tnc_create_network", "tnc_set_path", "tnc_set_slices", "tnc_contract"} <= names
+    for n in sorted(names):
+        assert hasattr(libtnc, n), n
+
+
+def _net(c):
+    from paper_2205_00393_gb300 import Network
+    tn = circuit_to_network(c)
+    return tn, Network.from_tn(tn)
+
+
+def test_validation_errors(libtnc):
+    from paper_2205_00393_gb300 import Network, TNCError
+    t = np.ones((2, 2), dtype=np.complex64)
+    # index on three tensors
+    with pytest.raises(TNCError):
+        Network([t, t, t], [(0, 1), (0, 2), (0, 3)], [2, 2, 2, 2], [1, 2, 3])
+    # non power of two
+    with pytest.raises(TNCError):
+        Network([np.ones((3,), np.complex64)], [(0,)], [3], [0])
+    # dangling index not declared open
+    with pytest.raises(TNCError):
+        Network([t], [(0, 1)], [2, 2], [0])
+    # repeated index within a tensor
+    with pytest.raises(TNCError):
+        Network([t], [(0, 0)], [2], [])
+    n = Network([t, t], [(0, 1), (1, 2)], [2, 2, 2], [0, 2])
+    with pytest.raises(TNCError) as e:
+        n.set_slices([1])
+    assert e.value.status == 5  # TNC_E_STATE before a path
+    with pytest.raises(TNCError):
+        n.set_path([(0, 0)])
+    n.set_path([(0, 1)])
+    with pytest.raises(TNCError):
+        n.set_slices([0])  # open
+    n.set_slices([1])
+    assert n.n_slices == 2
+
+
+CASES = [(3, 4, 8, 1, 0), (3, 3, 6, 2, 3), (2, 4, 8, 2, 0), (5, 6, 14, 2, 6), (4, 5, 12, 7, 2)]
+
+
+@pytest.mark.parametrize("rows,cols,cyc,seed,n_open", CASES)
+def test_greedy_path_twin(libtnc, rows, cols, cyc, seed, n_open):
+    c = grid_rqc(rows, cols, cyc, seed, n_open=n_open)
+    tn, net = _net(c)
+    assert net.greedy_path() == planner.greedy_path(tn.indices, tn.dims)
+
+
+def test_greedy_path_twin_53q(libtnc):
+    c = lattice_53q_rqc(12, 3)
+    tn, net = _net(c)
+    assert net.greedy_path() == planner.greedy_path(tn.indices, tn.dims)
+
+
+@pytest.mark.parametrize("rows,cols,cyc,seed,n_open,t,sa_seed", [
+    (3, 4, 8, 1, 0, 8, 7), (3, 4, 8, 1, 0, 6, 3), (3, 3, 6, 2, 3, 5, 1),
+    (5, 6, 14, 2, 6, 27, 7), (5, 6, 14, 2, 6, 24, 99), (4, 5, 12, 7, 2, 16, 5),
+])
+def test_slicer_twin(libtnc, rows, cols, cyc, seed, n_open, t, sa_seed):
+    c = grid_rqc(rows, cols, cyc, seed, n_open=n_open)
+    tn, net = _net(c)
+    path = planner.greedy_path(tn.indices, tn.dims)
+    net.set_path(path)
+    tree = planner.Tree(tn.indices, tn.dims, tn.open_ids, path)
+    S_py = planner.find_slices(tree, t, sa_seed)
+    S_c = net.find_slices(t, sa_seed)
+    assert S_c == S_py
+    net.set_slices(S_c)
+    st = net.stats()
+    assert int(st["eq1"]) == tree.eq1()
+    assert int(st["eq3"]) == tree.eq3(S_py)
+    assert st["max_log2_size"] <= max(tree.size_log(v) for v in range(tree.n_tensors))
+
+
+def test_slicer_twin_random_small_trees(libtnc):
+    rng = np.random.default_rng(123)
+    for trial in range(30):
+        rows, cols = int(rng.integers(2, 4)), int(rng.integers(2, 5))
+        c = grid_rqc(rows, cols, int(rng.integers(4, 10)), int(rng.integers(0, 10**6)),
+                     n_open=int(rng.integers(0, 3)))
+        tn, net = _net(c)
+        path = planner.greedy_path(tn.indices, tn.dims)
+        net.set_path(path)
+        tree = planner.Tree(tn.indices, tn.dims, tn.open_ids, path)
+        W = max(tree.size_log(v) for v in range(tree.n_tensors))
+        t = max(W - int(rng.integers(1, 4)), 4 + len(tn.open_ids))
+        seed = int(rng.integers(0, 2**63))
+        try:
+            S_py = planner.find_slices(tree, t, seed)
+        except planner.Infeasible:
+            from paper_2205_00393_gb300 import TNCError
+            with pytest.raises(TNCError):
+                net.find_slices(t, seed)
+            continue
+        assert net.find_slices(t, seed) == S_py
+
+
+def test_eq3_wide_costs(libtnc):
+    """53-qubit tree: Eq. 1 and Eq. 3 exceed 2^90; the exact wide-integer cost matches Python."""
+    c = lattice_53q_rqc(20, 3)
+    tn, net = _net(c)
+    path = planner.greedy_path(tn.indices, tn.dims)
+    net.set_path(path)
+    tree = planner.Tree(tn.indices, tn.dims, tn.open_ids, path)
+    S1 = planner.slice_finder(tree, 30)[:60]  # at most 62 sliced indices are accepted
+    net.set_slices(S1)
+    st = net.stats()
+    assert int(st["eq3"]) == tree.eq3(S1) and tree.eq3(S1) > 2 ** 100
+    assert int(st["eq1"]) == tree.eq1()
