@@ -161,6 +161,36 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable);
 tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, int64_t* mnk_log2,
                             float* ms, int cap, int* n_out, int64_t* n_launches);
 
+/* Capacity, in complex doubles, of the static scratch of tnc_reduce_pair_noalloc. */
+#define TNC_NOALLOC_MAX_PARTIALS 65536
+
+/* Allocation-free final contraction. The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory, e.g. a host
+ * program whose device memory is entirely owned by another allocator (a
+ * framework pool, a fixed per-process budget), or a latency-critical caller
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * Computes out[m*N + n] = sum_k A[m*K + k] * B[k*N + n] with A row-major
+ * M x K and B row-major K x N (complex64, interleaved, device pointers), M =
+ * 2^m_log2, N = 2^n_log2, K = 2^k_log2, M*N <= 64, K <= 2^31. The products are
+ * summed in FP64, per chunk of K and then over the chunks in a fixed order -
+ * the same kernels as the final reduction of tnc_contract - and out_c128
+ * (device, 2*M*N doubles) is overwritten.
+ *
+ * No memory is allocated or freed, by this library or by any library it
+ * calls: the partial sums live in one static device array of
+ * TNC_NOALLOC_MAX_PARTIALS complex doubles (1 MiB) that every GPU loading
+ * libtnc holds until the process exits. The first call on a device looks up
+ * that array's device address (with the device current) and caches it; make
+ * that first call before any stream capture. Every call on a device shares
+ * the array, so calls whose work overlaps on the GPU (e.g. on two streams)
+ * race; serialise them. Partial sums are fully rewritten by each call before
+ * they are read. Errors: TNC_E_INVALID for NULL pointers or sizes beyond the
+ * limits above (the number of partial sums, min(max(K/1024,1),1024) * M * N,
+ * must fit the array); TNC_E_CUDA if the lookup or a launch fails. */
+tnc_status tnc_reduce_pair_noalloc(const float* a_c64, const float* b_c64, int m_log2, int n_log2,
+                                   int k_log2, double* out_c128, void* stream);
+
 const char* tnc_last_error(void);
 void tnc_destroy(tnc_net_t net);
 

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace tnc {
@@ -65,6 +66,9 @@ struct PermParams {
     int obits;
     int64_t ostride[kMaxBits];
 };
+
+// Message returned by tnc_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 cudaError_t launch_gemm_f32(const GemmParams& p, int batch, cudaStream_t s);
 cudaError_t launch_root_partials(const RootParams& p, int batch, double2* partials, cudaStream_t s);

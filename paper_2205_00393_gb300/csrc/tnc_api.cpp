@@ -87,6 +87,8 @@ int64_t stride_of(const std::vector<std::pair<int, int64_t>>& s, int mode) {
 
 }  // namespace
 
+void tnc::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct tnc_net {
     // network
     int n_leaves = 0;
