@@ -39,9 +39,25 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
 }
 
 // C[m][n] = sum_k A(m,k) B(k,n), one 64x64 tile per CTA, 4x4 complex per thread.
+// Shared-memory stages are double buffered: the gather of tile t+1 goes to
+// registers while tile t is multiplied, then to the other stage (one barrier
+// per tile). Accumulation is two-level: each group of GROUP_TILES k-tiles is
+// summed in a fresh partial, and the partials are added to the result with
+// Kahan compensation, so the FP32 rounding error grows with sqrt(64) per
+// group instead of sqrt(K).
+constexpr int PAD = 2;           // keeps 16-byte alignment of fragment rows
+constexpr int GROUP_TILES = 4;   // 64 k-terms per partial sum
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+    float y = x - comp;
+    float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
 __global__ void __launch_bounds__(NT) k_gemm_f32(const __grid_constant__ GemmParams p) {
-    __shared__ float2 As[BK][BM + 1];
-    __shared__ float2 Bs[BK][BN + 1];
+    __shared__ __align__(16) float2 As[2][BK][BM + PAD];
+    __shared__ __align__(16) float2 Bs[2][BK][BN + PAD];
     __shared__ int64_t rowA[BM], colB[BN], klA[BK], klB[BK];
 
     const int tid = threadIdx.x;
@@ -68,62 +84,98 @@ __global__ void __launch_bounds__(NT) k_gemm_f32(const __grid_constant__ GemmPar
     // load mapping: walk the operand's unit-stride mode with consecutive threads
     const bool a_kfast = p.kb > 0 && p.ak[0] == 1;
     const bool b_nfast = p.nb > 0 && p.bn[0] == 1;
-
-    const int tx = tid & 15, ty = tid >> 4;
-    float2 acc[4][4];
+    int la_k[4], la_m[4], lb_k[4], lb_n[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 4; ++i) {
+        int e = tid + i * NT;
+        if (a_kfast) { la_k[i] = e % BK; la_m[i] = e / BK; }
+        else { la_m[i] = e % BM; la_k[i] = e / BM; }
+        if (b_nfast) { lb_n[i] = e % BN; lb_k[i] = e / BN; }
+        else { lb_k[i] = e % BK; lb_n[i] = e / BK; }
+    }
     __syncthreads();
 
-    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    float2 ra[4], rb[4];
+    auto gather = [&](int64_t k0) {
         const int64_t khA = bits_offset(k0, p.ak, p.kb, LOG_BK);
         const int64_t khB = bits_offset(k0, p.bk, p.kb, LOG_BK);
 #pragma unroll
-        for (int i = 0; i < (BM * BK) / NT; ++i) {
-            int e = tid + i * NT;
-            int kk, mm;
-            if (a_kfast) { kk = e % BK; mm = e / BK; }
-            else { mm = e % BM; kk = e / BM; }
-            float2 v = make_float2(0.f, 0.f);
-            if (m0 + mm < M && k0 + kk < K) v = A[rowA[mm] + khA + klA[kk]];
-            As[kk][mm] = v;
+        for (int i = 0; i < 4; ++i) {
+            ra[i] = make_float2(0.f, 0.f);
+            if (m0 + la_m[i] < M && k0 + la_k[i] < K) ra[i] = A[rowA[la_m[i]] + khA + klA[la_k[i]]];
+            rb[i] = make_float2(0.f, 0.f);
+            if (n0 + lb_n[i] < N && k0 + lb_k[i] < K) rb[i] = B[colB[lb_n[i]] + khB + klB[lb_k[i]]];
         }
+    };
+    auto stage_store = [&](int st) {
 #pragma unroll
-        for (int i = 0; i < (BN * BK) / NT; ++i) {
-            int e = tid + i * NT;
-            int kk, nn;
-            if (b_nfast) { nn = e % BN; kk = e / BN; }
-            else { kk = e % BK; nn = e / BK; }
-            float2 v = make_float2(0.f, 0.f);
-            if (n0 + nn < N && k0 + kk < K) v = B[colB[nn] + khB + klB[kk]];
-            Bs[kk][nn] = v;
+        for (int i = 0; i < 4; ++i) {
+            As[st][la_k[i]][la_m[i]] = ra[i];
+            Bs[st][lb_k[i]][lb_n[i]] = rb[i];
         }
-        __syncthreads();
+    };
+
+    const int tx = tid & 15, ty = tid >> 4;
+    float2 acc[4][4], cmp[4][4], part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            acc[i][j] = make_float2(0.f, 0.f);
+            cmp[i][j] = make_float2(0.f, 0.f);
+            part[i][j] = make_float2(0.f, 0.f);
+        }
+
+    const int64_t ntiles = (K + BK - 1) / BK;
+    gather(0);
+    stage_store(0);
+    __syncthreads();
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int st = (int)(t & 1);
+        if (t + 1 < ntiles) gather((t + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            float2 a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            float4 a01 = *reinterpret_cast<const float4*>(&As[st][kk][4 * ty]);
+            float4 a23 = *reinterpret_cast<const float4*>(&As[st][kk][4 * ty + 2]);
+            float4 b01 = *reinterpret_cast<const float4*>(&Bs[st][kk][4 * tx]);
+            float4 b23 = *reinterpret_cast<const float4*>(&Bs[st][kk][4 * tx + 2]);
+            float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
+                           make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
+            float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
+                           make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) cmac(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < 4; ++j) cmac(part[i][j], a[i], b[j]);
         }
+        if ((t + 1) % GROUP_TILES == 0 || t + 1 == ntiles) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    kahan_add(acc[i][j].x, cmp[i][j].x, part[i][j].x);
+                    kahan_add(acc[i][j].y, cmp[i][j].y, part[i][j].y);
+                    part[i][j] = make_float2(0.f, 0.f);
+                }
+        }
+        if (t + 1 < ntiles) stage_store(st ^ 1);
         __syncthreads();
     }
     float2* C = p.C + z * p.c_batch_stride;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        int64_t m = m0 + ty + 16 * i;
+        int64_t m = m0 + 4 * ty + i;
         if (m >= M) continue;
+        if (n0 + 4 * tx + 3 < N) {
+            float4* dst = reinterpret_cast<float4*>(C + m * N + n0 + 4 * tx);
+            dst[0] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+            dst[1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int64_t n = n0 + tx + 16 * j;
-            if (n < N) C[m * N + n] = acc[i][j];
+            for (int j = 0; j < 4; ++j) {
+                int64_t n = n0 + 4 * tx + j;
+                if (n < N) C[m * N + n] = acc[i][j];
+            }
         }
     }
 }
