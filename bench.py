@@ -285,7 +285,8 @@ def main():
         d["ms"] += r["ms"]
         d["launches"] += 1
         d["flops"] += 8.0 * (1 << r["mnk_log2"]) * r["batch"]
-    kind_names = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", -1: "k_slice_sum_f32"}
+    kind_names = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
+                  4: "k_split_operand", -1: "k_slice_sum_f32"}
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     d = by_kind[dom]
     achieved = d["flops"] / (d["ms"] / 1e3) / 1e12

@@ -142,6 +142,12 @@ tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes);
 tnc_status tnc_contract(tnc_net_t net, int64_t slice_lo, int64_t slice_hi, int mode,
                         double* out_c128, void* stream);
 
+/* Wait for `stream` and report device-side failures of the last
+ * contraction: TNC_E_TIMEOUT if a bounded wait inside a tensor-core kernel
+ * gave up (the kernel then drained its copies, freed its tensor memory and
+ * returned; the result is invalid but the context stays usable). */
+tnc_status tnc_check_device(tnc_net_t net, void* stream);
+
 /* JSON statistics of the current plan: Eq. 1 cost, Eq. 3 cost, Eq. 2
  * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace. */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
@@ -153,8 +159,9 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 tnc_status tnc_set_timing(tnc_net_t net, int enable);
 
 /* Launch records since the last tnc_set_timing (waits for their events): per timed
- * launch the node's tensor id, kernel kind (0 GEMM, 1 FP64 root reduction,
- * 2 GEMM root + FP64 slice sum, -1 leaf slice sum), slice batch, log2(M*N*K)
+ * launch the node's tensor id, kernel kind (0 FP32 GEMM, 1 FP64 root reduction,
+ * 2 GEMM root + FP64 slice sum, 3 tensor-core GEMM, 4 operand split,
+ * -1 leaf slice sum), slice batch, log2(M*N*K)
  * and milliseconds; any output array may be NULL. *n_out receives the number
  * of records (TNC_E_INVALID if it exceeds cap); *n_launches (may be NULL) the
  * number of kernels launched since then (counted with timing on or off). */

@@ -60,6 +60,7 @@ def load_library():
                          ctypes.c_void_p, ctypes.c_void_p],
         "tnc_stats": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
         "tnc_set_timing": [ctypes.c_void_p, ctypes.c_int],
+        "tnc_check_device": [ctypes.c_void_p, ctypes.c_void_p],
         "tnc_last_timings": [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                              c_i64p, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int), c_i64p],
     }
@@ -199,6 +200,10 @@ class Network:
                                     _stream_ptr(stream))
         _check(self._lib, st)
         return out
+
+    def check_device(self, stream=None):
+        """Wait for the stream; raise TNCError if a device-side wait gave up."""
+        _check(self._lib, self._lib.tnc_check_device(self._h, _stream_ptr(stream)))
 
     def set_timing(self, enable):
         _check(self._lib, self._lib.tnc_set_timing(self._h, 1 if enable else 0))

@@ -70,7 +70,7 @@ def build_library(force=False, verbose=False, extra=()):
                 sys.stderr.write(err)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + [ARCH, "-cudart", "shared", "-lcuda"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + [ARCH, "-cudart", "shared"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (res.stdout, res.stderr))

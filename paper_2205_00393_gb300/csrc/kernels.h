@@ -67,6 +67,32 @@ struct PermParams {
     int64_t ostride[kMaxBits];
 };
 
+// Operand split for the tensor-core path: the logical matrix X[R][K]
+// (R = M for A, N for B) with X(r, k) = src[r strides + k strides] is
+// written as K-major planes [batch][3 * parts][R][K] (Re, Im, Re+Im, each
+// split into parts).
+struct SplitParams {
+    Operand src;
+    int rb, kb;
+    int64_t rs[kMaxBits], ks[kMaxBits];
+    int64_t slice0;
+    void* dst;
+};
+
+struct TcGemmParams {
+    int mb, nb, kb;
+    float2* C;
+    int64_t c_batch_stride;
+    int* err;   // device error word (4 = a bounded wait gave up)
+};
+
+int tc_plane_count(int mode);
+int tc_elem_bytes(int mode);
+int tc_min_kb(int mode);
+cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s);
+cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
+                            int batch, cudaStream_t s);
+
 // Message returned by tnc_last_error() on this thread.
 void set_last_error(const std::string& msg);
 

@@ -1,0 +1,539 @@
+// Split-precision complex GEMM on the 5th-generation tensor cores (tcgen05).
+//
+// A pairwise contraction C[m,n] = sum_k A(m,k) B(k,n) (Sec. 2.1.1, in the
+// TTGT arrangement of Sec. 5.3.1) runs in two kernels:
+//
+//  1. k_split_operand: the permute-fused operand load. It gathers the FP32
+//     complex operand through its per-bit stride table (the permutation and
+//     the slice fixing), stages a 32x64 tile in shared memory so that both the
+//     gather and the writes are coalesced, and writes, for each of the three
+//     real matrices of the 3M complex product (Re, Im, Re+Im), the split
+//     parts as K-major planes:  BF16: x = x0 + x1 + x2 (three parts),
+//     TF32: x = x0 + x1 (two parts).
+//  2. k_cgemm_tc: a warp-specialised tcgen05 GEMM on 128x128 output tiles.
+//     One warp issues TMA loads (128-byte swizzle, the three or two parts of
+//     one real matrix per box) into a shared-memory ring guarded by mbarriers;
+//     one thread issues tcgen05.mma (kind::f16 or kind::tf32, FP32
+//     accumulation) for every part pair (i, j) with i + j <= 2 (BF16) or
+//     i + j <= 1 (TF32) into one of three TMEM accumulators
+//     T1 = Re A Re B, T2 = Im A Im B, T3 = (Re+Im)A (Re+Im)B; eight epilogue
+//     warps move each K-chunk's T1..T3 into FP32 registers and finally write
+//     C = (T1 - T2) + i (T3 - T1 - T2).
+//
+// Every mbarrier wait is bounded; a wait that gives up records an error code
+// in the caller's error word, the CTA drains its own copies in flight, frees
+// its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "kernels.h"
+
+namespace tnc {
+
+namespace {
+
+constexpr int TM = 128, TN = 128;
+constexpr int PART_TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes (one swizzle row each)
+constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr int kErrTimeout = 4;
+
+template <int KIND> struct Cfg;
+template <> struct Cfg<0> {  // BF16 parts, kind::f16
+    static constexpr int PARTS = 3, NPAIRS = 6, STAGES = 2, ELEM = 2, BK = 64;
+};
+template <> struct Cfg<1> {  // TF32 parts, kind::tf32
+    static constexpr int PARTS = 2, NPAIRS = 3, STAGES = 3, ELEM = 4, BK = 32;
+};
+template <> struct Cfg<2> {  // two BF16 parts, kind::f16 (cheaper, ~16-bit accurate)
+    static constexpr int PARTS = 2, NPAIRS = 3, STAGES = 3, ELEM = 2, BK = 64;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false if it gave up or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // version
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (KIND != 1) {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <int KIND>
+__host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4) | ((KIND == 1 ? 2u : 1u) << 7) | ((KIND == 1 ? 2u : 1u) << 10) |
+           ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+// Part pairs, smallest magnitudes first.
+__constant__ int kPairsBF16[6][2] = {{1, 1}, {0, 2}, {2, 0}, {0, 1}, {1, 0}, {0, 0}};
+__constant__ int kPairs2[3][2] = {{0, 1}, {1, 0}, {0, 0}};
+
+// K is processed in chunks of KC_ELEMS. Within a chunk the three real
+// products run one after the other (product-major), each accumulating in its
+// own TMEM columns; when a product's chunk is complete the epilogue warps move
+// it into FP32 registers (Cr += T1 - T2, Ci += T3 - T1 - T2) while the tensor
+// cores work on the next product. The tensor core's accumulation into TMEM
+// does not round to nearest, so its error grows linearly with the number of
+// accumulated MMAs; short chunks bound that growth and the register sums
+// across chunks round to nearest.
+constexpr int KC_ELEMS = 256;
+constexpr int EPI_WARPS = 8;   // warps 0-7: epilogue (warp w: TMEM lanes 32*(w%4), columns 64*(w/4))
+constexpr int PRODUCER_WARP = 8, MMA_WARP = 9, NTHREADS = 320;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_cgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ TcGemmParams p) {
+    using C_ = Cfg<KIND>;
+    constexpr int STAGE_A = C_::PARTS * PART_TILE_BYTES;
+    constexpr int STAGE_BYTES = 2 * STAGE_A;
+    extern __shared__ __align__(1024) uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t full_bar[C_::STAGES], empty_bar[C_::STAGES], tfull[3], tfree[3], drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+    const int64_t N = 1ll << p.nb, K = 1ll << p.kb;
+    const int64_t tiles_n = N / TN;
+    const int m0 = (int)((blockIdx.x / tiles_n) * TM);
+    const int n0 = (int)((blockIdx.x % tiles_n) * TN);
+    const int z = blockIdx.z;
+    const int nkb = (int)(K / C_::BK);
+    const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;  // k-blocks per chunk
+    const int nchunks = nkb / kpc;
+    const int n_it = nchunks * 3 * kpc;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C_::STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int t = 0; t < 3; ++t) {
+            mbar_init(smem_u32(&tfull[t]), 1);
+            mbar_init(smem_u32(&tfree[t]), EPI_WARPS);
+        }
+        mbar_init(smem_u32(&drain_bar), 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    volatile int* abort_flag = &abort_sh;
+
+    if (warp == PRODUCER_WARP && lane == 0) {
+        // ---------------- TMA producer: stages in (chunk, product, k-block) order
+        int issued = 0;
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % C_::STAGES;
+            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag)) {
+                abort_sh = 1;
+                atomicExch(p.err, kErrTimeout);
+                break;
+            }
+            const int c = it / (3 * kpc), r = it % (3 * kpc);
+            const int t = r / kpc, kb = c * kpc + r % kpc;
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t fb = smem_u32(&full_bar[s]);
+            mbar_expect_tx(fb, STAGE_BYTES);
+            tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, z, fb);
+            tma_load_4d(sa + STAGE_A, &tmB, kb * C_::BK, n0, t * C_::PARTS, z, fb);
+            issued = it + 1;
+        }
+        if (*abort_flag) {
+            // drain: wait (bounded) for every load that may still be in flight
+            int first = issued - C_::STAGES < 0 ? 0 : issued - C_::STAGES;
+            for (int it = first; it < issued; ++it) {
+                const int s = it % C_::STAGES;
+                const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+                for (uint32_t i = 0; i < kSpinLimit && !mbar_try(smem_u32(&full_bar[s]), ph); ++i) {
+                }
+            }
+        }
+    } else if (warp == MMA_WARP && lane == 0) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = instr_desc<KIND>();
+        bool any = false;
+        for (int it = 0; it < n_it && !*abort_flag; ++it) {
+            const int s = it % C_::STAGES;
+            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+            const int c = it / (3 * kpc), r = it % (3 * kpc);
+            const int t = r / kpc, kbi = r % kpc;
+            if (kbi == 0 && c > 0 &&
+                !mbar_wait(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag)) {
+                abort_sh = 1;
+                atomicExch(p.err, kErrTimeout);
+                break;
+            }
+            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag)) {
+                abort_sh = 1;
+                atomicExch(p.err, kErrTimeout);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t sb = sa + STAGE_A;
+            const uint32_t d = tmem + (uint32_t)(t * TN);
+#pragma unroll
+            for (int q = 0; q < C_::NPAIRS; ++q) {
+                const int pa = KIND == 0 ? kPairsBF16[q][0] : kPairs2[q][0];
+                const int pb = KIND == 0 ? kPairsBF16[q][1] : kPairs2[q][1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {  // 4 MMAs of 32 bytes of K per 128-byte row
+                    const uint64_t ad = smem_desc(sa + pa * PART_TILE_BYTES + j * 32);
+                    const uint64_t bd = smem_desc(sb + pb * PART_TILE_BYTES + j * 32);
+                    mma<KIND>(d, ad, bd, idesc, (kbi > 0 || q > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            any = true;
+            mma_commit(smem_u32(&empty_bar[s]));
+            if (kbi == kpc - 1) mma_commit(smem_u32(&tfull[t]));
+        }
+        if (*abort_flag && any) {
+            mma_commit(smem_u32(&drain_bar));
+            for (uint32_t i = 0; i < kSpinLimit && !mbar_try(smem_u32(&drain_bar), 0); ++i) {
+            }
+        }
+    } else if (warp < EPI_WARPS) {
+        // ---------------- epilogue: chunk partials TMEM -> FP32 registers -> C
+        const int g = warp & 3, h = warp >> 2;
+        float cr[64], ci[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            cr[j] = 0.f;
+            ci[j] = 0.f;
+        }
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                int w = 0;
+                if (lane == 0) w = mbar_wait(smem_u32(&tfull[t]), (uint32_t)c & 1u, abort_flag) ? 1 : 0;
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(t * TN + 64 * h + 32 * half), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = 32 * half + j;
+                        if (t == 0) {
+                            cr[col] += v[j];
+                            ci[col] -= v[j];
+                        } else if (t == 1) {
+                            cr[col] -= v[j];
+                            ci[col] -= v[j];
+                        } else {
+                            ci[col] += v[j];
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tfree[t]));
+            }
+        }
+        if (!ok) {
+            if (lane == 0 && !abort_sh) {
+                abort_sh = 1;
+                atomicExch(p.err, kErrTimeout);
+            }
+        } else {
+            const int row = 32 * g + lane;
+            float4* dst = reinterpret_cast<float4*>(p.C + (int64_t)z * p.c_batch_stride +
+                                                    (int64_t)(m0 + row) * N + n0 + 64 * h);
+#pragma unroll
+            for (int j = 0; j < 64; j += 2) dst[j / 2] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+// ------------------------------------------------------------ operand split
+
+__device__ __forceinline__ int64_t slice_offset(const Operand& op, int64_t s) {
+    int64_t off = 0;
+    for (int j = 0; j < op.n_sl; ++j) off += ((s >> op.sl_bit[j]) & 1) * op.sl_stride[j];
+    return off;
+}
+
+__device__ __forceinline__ int64_t bits_offset(int64_t x, const int64_t* str, int nbits, int from) {
+    int64_t off = 0;
+    for (int j = from; j < nbits; ++j)
+        if ((x >> j) & 1) off += str[j];
+    return off;
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+constexpr int SR = 32, SK = 64;  // split tile: 32 rows x 64 k
+
+// planes: out[((z * (3*PARTS) + q) * R + r) * K + k], q = t * PARTS + part
+template <int KIND>
+__global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ SplitParams p) {
+    using C_ = Cfg<KIND>;
+    __shared__ float2 tile[SR][SK + 1];
+    __shared__ int64_t roff[SR], koff[SK];
+    const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
+    const int64_t tiles_k = K / SK;
+    const int64_t r0 = (blockIdx.x / tiles_k) * SR, k0 = (blockIdx.x % tiles_k) * SK;
+    const int z = blockIdx.z;
+    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, p.slice0 + z);
+    const int tid = threadIdx.x;
+    if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
+    else if (tid < SR + SK) koff[tid - SR] = bits_offset(k0 + tid - SR, p.ks, p.kb, 0);
+    __syncthreads();
+    const bool kfast = p.kb > 0 && p.ks[0] == 1;
+#pragma unroll
+    for (int i = 0; i < (SR * SK) / 256; ++i) {
+        int e = tid + i * 256;
+        int rr, kk;
+        if (kfast) { kk = e % SK; rr = e / SK; }
+        else { rr = e % SR; kk = e / SR; }
+        tile[rr][kk] = src[roff[rr] + koff[kk]];
+    }
+    __syncthreads();
+    constexpr int Q = 3 * C_::PARTS;
+    const int64_t plane = R * K;
+    uint8_t* out = reinterpret_cast<uint8_t*>(p.dst) + (int64_t)z * Q * plane * C_::ELEM;
+#pragma unroll
+    for (int i = 0; i < (SR * SK / 2) / 256; ++i) {
+        int e = tid + i * 256;
+        int kp = e % (SK / 2), rr = e / (SK / 2);
+        float2 x0 = tile[rr][2 * kp], x1 = tile[rr][2 * kp + 1];
+        float v0[3] = {x0.x, x0.y, x0.x + x0.y};
+        float v1[3] = {x1.x, x1.y, x1.x + x1.y};
+        const int64_t idx = (r0 + rr) * K + k0 + 2 * kp;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if constexpr (KIND != 1) {
+                float a = v0[t], b = v1[t];
+#pragma unroll
+                for (int q = 0; q < C_::PARTS; ++q) {
+                    __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+                    __nv_bfloat162 pr;
+                    pr.x = ha;
+                    pr.y = hb;
+                    reinterpret_cast<__nv_bfloat162*>(out + ((t * C_::PARTS + q) * plane + idx) * 2)[0] = pr;
+                    a -= __bfloat162float(ha);
+                    b -= __bfloat162float(hb);
+                }
+            } else {
+                float a = v0[t], b = v1[t];
+                float a0 = tf32_round(a), b0 = tf32_round(b);
+                float a1 = tf32_round(a - a0), b1 = tf32_round(b - b0);
+                reinterpret_cast<float2*>(out + ((t * 2 + 0) * plane + idx) * 4)[0] = make_float2(a0, b0);
+                reinterpret_cast<float2*>(out + ((t * 2 + 1) * plane + idx) * 4)[0] = make_float2(a1, b1);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ host helpers
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+// 4D map over planes [batch][3*PARTS][rows][K]; box = (BK, 128, PARTS, 1).
+template <int KIND>
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int batch) {
+    using C_ = Cfg<KIND>;
+    EncodeFn enc = encoder();
+    if (!enc) return false;
+    const int Q = 3 * C_::PARTS;
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Q, (cuuint64_t)batch};
+    cuuint64_t strides[3] = {(cuuint64_t)(K * C_::ELEM), (cuuint64_t)(rows * K * C_::ELEM),
+                             (cuuint64_t)(Q * rows * K * C_::ELEM)};
+    cuuint32_t box[4] = {(cuuint32_t)C_::BK, 128u, (cuuint32_t)C_::PARTS, 1u};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, KIND == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int KIND>
+cudaError_t launch_tc_impl(const TcGemmParams& p, const void* planesA, const void* planesB, int batch,
+                           cudaStream_t s) {
+    using C_ = Cfg<KIND>;
+    const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
+    CUtensorMap ta, tb;
+    if (!make_map<KIND>(&ta, planesA, M, K, batch) || !make_map<KIND>(&tb, planesB, N, K, batch))
+        return cudaErrorInvalidValue;
+    const int smem = C_::STAGES * 2 * C_::PARTS * PART_TILE_BYTES + 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t tiles = (M / TM) * (N / TN);
+    k_cgemm_tc<KIND><<<dim3((unsigned)tiles, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts)
+static int kind_of(int mode) { return mode == 1 ? 1 : (mode == 2 ? 0 : 2); }
+
+int tc_plane_count(int mode) { return mode == 2 ? 9 : 6; }
+int tc_elem_bytes(int mode) { return mode == 1 ? 4 : 2; }
+int tc_min_kb(int) { return 6; }
+
+cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s) {
+    const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
+    if (R < SR || K < SK || batch < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
+    const int64_t blocks = (R / SR) * (K / SK);
+    const dim3 grid((unsigned)blocks, 1, batch);
+    switch (kind_of(mode)) {
+        case 0: k_split_operand<0><<<grid, 256, 0, s>>>(p); break;
+        case 1: k_split_operand<1><<<grid, 256, 0, s>>>(p); break;
+        default: k_split_operand<2><<<grid, 256, 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
+                            int batch, cudaStream_t s) {
+    if (p.mb < 7 || p.nb < 7 || p.kb < tc_min_kb(mode) || batch < 1 || batch > 65535)
+        return cudaErrorInvalidConfiguration;
+    switch (kind_of(mode)) {
+        case 0: return launch_tc_impl<0>(p, planesA, planesB, batch, s);
+        case 1: return launch_tc_impl<1>(p, planesA, planesB, batch, s);
+        default: return launch_tc_impl<2>(p, planesA, planesB, batch, s);
+    }
+}
+
+}  // namespace tnc

@@ -48,7 +48,13 @@ constexpr int64_t kAlign = 256;
 int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Kernel chosen for a contraction node.
-enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2 };
+enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4 };
+
+// Tensor-core eligibility of a non-root node in a split mode: both output
+// sides span whole 128-wide tiles and K spans whole 64-wide k-blocks.
+bool tc_node(int mode, int mb, int nb, int kb, bool is_root) {
+    return mode != TNC_FP32 && !is_root && mb >= 7 && nb >= 7 && kb >= tnc::tc_min_kb(mode);
+}
 
 struct NodePlan {
     int v = 0;            // tensor id produced
@@ -75,6 +81,7 @@ struct Plan {
 
 struct Arena {
     std::vector<int64_t> off;      // byte offset per tensor (-1 = none)
+    std::vector<int64_t> planes_a, planes_b;  // per node (tensor-core split planes)
     int64_t root_scratch_off = -1; // FP64 partials or FP32 per-slice root
     int64_t peak = 0;
 };
@@ -103,6 +110,7 @@ struct tnc_net {
     int64_t total_leaf_elems = 0;
     // device
     float2* d_leaves = nullptr;
+    int* d_err = nullptr;           // device error word of bounded waits
     bool dev_dirty = true;
     // path and slices
     std::vector<tnc::Pair> path;
@@ -125,6 +133,7 @@ struct tnc_net {
 
     ~tnc_net() {
         if (d_leaves) cudaFree(d_leaves);
+        if (d_err) cudaFree(d_err);
         if (ws_own) cudaFree(ws_own);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
@@ -248,12 +257,18 @@ void build_plan(tnc_net* net) {
 
 int64_t tensor_bytes(const Plan& P, int v) { return (int64_t)8 << P.layout[v].size(); }
 
+int64_t planes_bytes(int mode, int rb, int kb, int64_t batch) {
+    return batch * (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode) << (rb + kb);
+}
+
 // First-fit simulation of the workspace for a batch of `nb` slices.
-Arena plan_arena(const tnc_net* net, int64_t nb) {
+Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
     const Plan& P = net->plan;
     const tnc::Tree& T = *net->tree;
     Arena ar;
     ar.off.assign(T.n_tensors(), -1);
+    ar.planes_a.assign(P.nodes.size(), -1);
+    ar.planes_b.assign(P.nodes.size(), -1);
     std::map<int64_t, int64_t> used;  // off -> len
     int64_t top = 0;
     auto alloc = [&](int64_t len) {
@@ -269,10 +284,23 @@ Arena plan_arena(const tnc_net* net, int64_t nb) {
         return off;
     };
     auto release = [&](int64_t off) { used.erase(off); };
+    auto tc_planes = [&](const NodePlan& np, int64_t b) {
+        const size_t i = np.v - net->n_leaves;
+        ar.planes_a[i] = alloc(planes_bytes(mode, np.mb, np.kb, b));
+        ar.planes_b[i] = alloc(planes_bytes(mode, np.nb, np.kb, b));
+    };
+    auto tc_release = [&](const NodePlan& np) {
+        const size_t i = np.v - net->n_leaves;
+        release(ar.planes_a[i]);
+        release(ar.planes_b[i]);
+    };
     // phase 1: invariant nodes
     for (const NodePlan& np : P.nodes) {
         if (np.per_slice) continue;
+        const bool tc = tc_node(mode, np.mb, np.nb, np.kb, np.is_root);
+        if (tc) tc_planes(np, 1);
         ar.off[np.v] = alloc(tensor_bytes(P, np.v));
+        if (tc) tc_release(np);
         for (int c : {np.A, np.B})
             if (c >= net->n_leaves) release(ar.off[c]);
     }
@@ -285,7 +313,10 @@ Arena plan_arena(const tnc_net* net, int64_t nb) {
                                 : nb * tensor_bytes(P, np.v);
             ar.root_scratch_off = alloc(bytes);
         } else {
+            const bool tc = tc_node(mode, np.mb, np.nb, np.kb, np.is_root);
+            if (tc) tc_planes(np, nb);
             ar.off[np.v] = alloc(nb * tensor_bytes(P, np.v));
+            if (tc) tc_release(np);
         }
         for (int c : {np.A, np.B})
             if (c >= net->n_leaves && P.per_slice[c]) release(ar.off[c]);
@@ -347,6 +378,10 @@ tnc_status ensure_leaves(tnc_net* net, cudaStream_t st) {
         CUDA_TRY(cudaMalloc(&net->d_leaves, std::max<int64_t>(8, net->total_leaf_elems * 8)));
         net->dev_dirty = true;
     }
+    if (!net->d_err) {
+        CUDA_TRY(cudaMalloc(&net->d_err, 256));
+        CUDA_TRY(cudaMemsetAsync(net->d_err, 0, 256, st));
+    }
     if (net->dev_dirty) {
         CUDA_TRY(cudaMemcpyAsync(net->d_leaves, net->host_leaves.data(), net->total_leaf_elems * 8,
                                  cudaMemcpyHostToDevice, st));
@@ -376,15 +411,63 @@ cudaError_t timed_end(tnc_net* net, cudaStream_t s) {
     return cudaEventRecord(net->ev_pool[net->timed.back().ev + 1], s);
 }
 
-int64_t pick_batch(const tnc_net* net, int64_t want, size_t budget) {
+int64_t pick_batch(const tnc_net* net, int64_t want, size_t budget, int mode) {
     int64_t lo = 1, hi = std::max<int64_t>(1, std::min<int64_t>(want, 65535));
-    if ((size_t)plan_arena(net, 1).peak > budget) return 0;
+    if ((size_t)plan_arena(net, 1, mode).peak > budget) return 0;
     while (lo < hi) {
         int64_t mid = (lo + hi + 1) / 2;
-        if ((size_t)plan_arena(net, mid).peak <= budget) lo = mid;
+        if ((size_t)plan_arena(net, mid, mode).peak <= budget) lo = mid;
         else hi = mid - 1;
     }
     return lo;
+}
+
+// One non-root contraction: FP32 CUDA-core GEMM, or (split modes, large
+// nodes) operand split + tensor-core GEMM. `g` carries operands and output.
+tnc_status launch_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, const tnc::GemmParams& g,
+                       int b, int mode, cudaStream_t s) {
+    if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) {
+        CUDA_TRY(timed_begin(net, np.v, K_GEMM_F32, b, s));
+        CUDA_TRY(tnc::launch_gemm_f32(g, b, s));
+        CUDA_TRY(timed_end(net, s));
+        return TNC_OK;
+    }
+    const size_t i = np.v - net->n_leaves;
+    void* pa = ws + ar.planes_a[i];
+    void* pb = ws + ar.planes_b[i];
+    tnc::SplitParams sp{};
+    sp.src = g.A;
+    sp.rb = np.mb;
+    sp.kb = np.kb;
+    for (int j = 0; j < np.mb; ++j) sp.rs[j] = np.am[j];
+    for (int j = 0; j < np.kb; ++j) sp.ks[j] = np.ak[j];
+    sp.slice0 = g.slice0;
+    sp.dst = pa;
+    CUDA_TRY(timed_begin(net, np.v, K_SPLIT, b, s));
+    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
+    CUDA_TRY(timed_end(net, s));
+    sp = tnc::SplitParams{};
+    sp.src = g.B;
+    sp.rb = np.nb;
+    sp.kb = np.kb;
+    for (int j = 0; j < np.nb; ++j) sp.rs[j] = np.bn[j];
+    for (int j = 0; j < np.kb; ++j) sp.ks[j] = np.bk[j];
+    sp.slice0 = g.slice0;
+    sp.dst = pb;
+    CUDA_TRY(timed_begin(net, np.v, K_SPLIT, b, s));
+    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
+    CUDA_TRY(timed_end(net, s));
+    tnc::TcGemmParams tp{};
+    tp.mb = np.mb;
+    tp.nb = np.nb;
+    tp.kb = np.kb;
+    tp.C = g.C;
+    tp.c_batch_stride = g.c_batch_stride;
+    tp.err = net->d_err;
+    CUDA_TRY(timed_begin(net, np.v, K_TC, b, s));
+    CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
+    CUDA_TRY(timed_end(net, s));
+    return TNC_OK;
 }
 
 }  // namespace
@@ -557,7 +640,10 @@ tnc_status tnc_workspace_bytes(tnc_net_t net, int64_t max_batch, size_t* bytes) 
     if (!net || !bytes || max_batch < 1) return fail(TNC_E_INVALID, "bad argument");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
-    *bytes = (size_t)plan_arena(net, max_batch).peak;
+    size_t b = 0;
+    for (int mode = TNC_FP32; mode <= TNC_SPLIT_BF16X2; ++mode)
+        b = std::max(b, (size_t)plan_arena(net, max_batch, mode).peak);
+    *bytes = b;
     return TNC_OK;
 }
 
@@ -574,7 +660,6 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     if (!out_c128) return fail(TNC_E_INVALID, "NULL output");
     if (mode != TNC_FP32 && mode != TNC_SPLIT_TF32 && mode != TNC_SPLIT_BF16 && mode != TNC_SPLIT_BF16X2)
         return fail(TNC_E_INVALID, "unknown mode");
-    if (mode != TNC_FP32) return fail(TNC_E_INVALID, "split tensor-core modes are not available in this build");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
     const int64_t n_slices = 1ll << net->S_sorted.size();
@@ -591,14 +676,14 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     int64_t nb = 0;
     const int64_t want = hi - lo;
     if (net->ws_user) {
-        nb = pick_batch(net, want, net->ws_user_bytes);
+        nb = pick_batch(net, want, net->ws_user_bytes, mode);
         if (nb < 1) return fail(TNC_E_OOM, "workspace too small for one slice");
         ws = (char*)net->ws_user;
     } else {
-        size_t one = (size_t)plan_arena(net, 1).peak;
+        size_t one = (size_t)plan_arena(net, 1, mode).peak;
         size_t budget = std::max<size_t>(one, (size_t)1 << 30);
-        nb = pick_batch(net, std::min<int64_t>(want, 1024), budget);
-        size_t need = (size_t)plan_arena(net, nb).peak;
+        nb = pick_batch(net, std::min<int64_t>(want, 1024), budget, mode);
+        size_t need = (size_t)plan_arena(net, nb, mode).peak;
         if (net->ws_own_bytes < need) {
             if (net->ws_own) CUDA_TRY(cudaFree(net->ws_own));
             net->ws_own = nullptr;
@@ -609,7 +694,8 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
         ws = (char*)net->ws_own;
     }
     net->last_batch = nb;
-    const Arena ar = plan_arena(net, nb);
+    const Arena ar = plan_arena(net, nb, mode);
+    CUDA_TRY(cudaMemsetAsync(net->d_err, 0, sizeof(int), s));
 
     // invariant nodes once
     for (const NodePlan& np : P.nodes) {
@@ -618,9 +704,7 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
         g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
         g.c_batch_stride = 0;
         g.slice0 = 0;
-        CUDA_TRY(timed_begin(net, np.v, np.kind, 1, s));
-        CUDA_TRY(tnc::launch_gemm_f32(g, 1, s));
-        CUDA_TRY(timed_end(net, s));
+        if ((st = launch_node(net, ar, ws, np, g, 1, mode, s)) != TNC_OK) return st;
     }
     tnc::PermParams pp{};
     pp.obits = P.obits;
@@ -644,12 +728,14 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
             if (!np.per_slice) continue;
             tnc::GemmParams g = gemm_params(net, ar, ws, np, b);
             g.slice0 = s0;
-            CUDA_TRY(timed_begin(net, np.v, np.kind, b, s));
             if (!np.is_root) {
                 g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
                 g.c_batch_stride = tensor_bytes(P, np.v) / 8;
-                CUDA_TRY(tnc::launch_gemm_f32(g, b, s));
-            } else if (np.kind == K_ROOT_F64) {
+                if ((st = launch_node(net, ar, ws, np, g, b, mode, s)) != TNC_OK) return st;
+                continue;
+            }
+            CUDA_TRY(timed_begin(net, np.v, np.kind, b, s));
+            if (np.kind == K_ROOT_F64) {
                 tnc::RootParams rp{};
                 rp.g = g;
                 rp.chunks = np.chunks;
@@ -675,6 +761,17 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
             CUDA_TRY(timed_end(net, s));
         }
     }
+    return TNC_OK;
+}
+
+tnc_status tnc_check_device(tnc_net_t net, void* stream) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (!net->d_err) return TNC_OK;
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, net->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h == TNC_E_TIMEOUT) return fail(TNC_E_TIMEOUT, "a device-side wait gave up (tensor-core pipeline)");
+    if (h) return fail(TNC_E_CUDA, "device error word " + std::to_string(h));
     return TNC_OK;
 }
 
@@ -739,7 +836,7 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
         }
     }
     if (net->plan.valid) {
-        o << ",\"workspace_batch1\":" << plan_arena(net, 1).peak;
+        o << ",\"workspace_batch1\":" << plan_arena(net, 1, TNC_FP32).peak;
         o << ",\"last_batch\":" << net->last_batch;
         o << ",\"nodes\":[";
         bool first = true;

@@ -1,0 +1,88 @@
+"""GPU parity of the split-precision tensor-core path (tcgen05) against the
+FP64 oracle. Split BF16 (3 parts, 6 products) and split TF32 (2 parts, 3
+products) must match within 1e-4 relative per amplitude; the cheaper 2-part
+BF16 variant is reported and held to 1e-3."""
+
+import numpy as np
+import pytest
+
+from tnc_inputs import circuit_to_network, grid_rqc
+from oracle import tn
+
+from ._util import floored_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 1e-4, 2: 1e-4, 3: 1e-3}
+
+
+@pytest.fixture(scope="module")
+def lib(libtnc):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return libtnc
+
+
+def _three_leaf(seed, mb, nb, kb, permuted):
+    """A[m,k] B[k,n] D[n,o]: the A*B node is a tensor-core GEMM (M=2^mb,
+    N=2^nb, K=2^kb); the root contracts n with D."""
+    from tnc_inputs.network import TensorNetwork
+    rng = np.random.default_rng(seed)
+
+    def rnd(*shape):
+        return ((rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2)).astype(np.complex64)
+    # binary modes as separate indices so the operand permutation is exercised
+    m_ids = list(range(mb))
+    k_ids = list(range(mb, mb + kb))
+    n_ids = list(range(mb + kb, mb + kb + nb))
+    o_ids = [mb + kb + nb]
+    a_idx = m_ids + k_ids
+    if permuted:  # interleave k and m modes in A's memory order
+        a_idx = [x for pair in zip(k_ids, m_ids) for x in pair] + k_ids[len(m_ids):] + m_ids[len(k_ids):]
+    b_idx = n_ids[::-1] + k_ids if permuted else k_ids + n_ids
+    d_idx = n_ids + o_ids
+    tensors = [rnd(*([2] * len(a_idx))), rnd(*([2] * len(b_idx))), rnd(*([2] * len(d_idx)))]
+    dims = np.full(mb + kb + nb + 1, 2, dtype=np.int64)
+    return TensorNetwork(tensors, [tuple(a_idx), tuple(b_idx), tuple(d_idx)], dims,
+                         tuple(m_ids + o_ids), [-1, -1, -1])
+
+
+@pytest.mark.parametrize("mode", [2, 1, 3])
+@pytest.mark.parametrize("mb,nb,kb,permuted", [(7, 7, 6, False), (8, 9, 7, True), (9, 8, 10, False)])
+def test_tc_node_vs_oracle(lib, mode, mb, nb, kb, permuted):
+    from paper_2205_00393_gb300 import Network
+    net_ref = _three_leaf(100 + mb + nb + kb, mb, nb, kb, permuted)
+    net = Network.from_tn(net_ref)
+    path = [(0, 1), (2, 3)]
+    net.set_path(path)
+    st = net.stats()
+    assert st["nodes"][0][:3] in ([mb, nb, kb], [nb, mb, kb])
+    got = net.contract(0, 1, mode)
+    net.check_device()
+    got = got.cpu().numpy()
+    ref = tn.contract(net_ref, path)
+    err = floored_rel_err(got, ref, 0)
+    print("mode %d (%d,%d,%d) err %.3e" % (mode, mb, nb, kb, err))
+    assert err <= TOL[mode]
+    fp32 = net.contract(0, 1, 0).cpu().numpy()
+    assert floored_rel_err(fp32, ref, 0) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [2, 1])
+def test_c2_one_slice_split(lib, mode):
+    from paper_2205_00393_gb300 import Network
+    c = grid_rqc(5, 6, 14, 2, n_open=6)
+    ref_net = circuit_to_network(c).as_complex64()
+    net = Network.from_tn(ref_net)
+    path = net.greedy_path()
+    net.set_path(path)
+    S = net.find_slices(27, 7)
+    net.set_slices(S)
+    s = 5
+    got = net.contract(s, s + 1, mode)
+    net.check_device()
+    ref = tn.contract_slice(ref_net, path, S, s)
+    err = floored_rel_err(got.cpu().numpy(), ref, 30)
+    print("c2 slice %d mode %d err %.3e" % (s, mode, err))
+    assert err <= TOL[mode]
