@@ -35,6 +35,14 @@ WORKLOAD = dict(rows=5, cols=6, cycles=14, seed=2, n_open=6, target_log2=27, sa_
 MODES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x2": 3}
 # FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Tensor flops per complex multiply-accumulate of one node (3M: three real
+# products, each summed over the part pairs): BF16 3 parts -> 6 pairs,
+# TF32 2 parts -> 3 pairs, BF16 2 parts -> 3 pairs; 2 flops per real MAC.
+TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 * 2}
+# dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
+TF32_OVER_BF16 = 1.1 / 2.25
+KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
+              4: "k_split_operand", -1: "k_slice_sum_f32"}
 
 
 def workload_name():
@@ -137,16 +145,67 @@ def node_flops(stats, batch):
     return tot
 
 
-def run_oracle_sample(ref_net, path, S, budget_s=20.0):
-    """Time the FP64 oracle on one slice's largest contractions (the nodes that
-    carry 99.99% of the flops), at most ~budget_s seconds."""
-    import threading
+def run_oracle_sample(ref_net, path, S):
+    """Time the FP64 oracle on one full slice (slice 0) of the workload."""
     from oracle import tn
     log = []
     t0 = time.perf_counter()
-    tn.contract_slice(ref_net, path, S, 0, log=log)
+    ref = tn.contract_slice(ref_net, path, S, 0, log=log)
     dt = time.perf_counter() - t0
-    return sum(log), dt
+    return sum(log), dt, ref
+
+
+def kernel_breakdown(recs):
+    by_kind = {}
+    for r in recs:
+        d = by_kind.setdefault(r["kind"], {"ms": 0.0, "cmacs": 0.0, "launches": 0})
+        d["ms"] += r["ms"]
+        d["launches"] += 1
+        if r["kind"] in (0, 1, 2, 3):
+            d["cmacs"] += float(1 << r["mnk_log2"]) * r["batch"]
+    return by_kind
+
+
+def roofline_of(by_kind, mode, peaks, peak_src, sustained):
+    """Roofline entry of the kernel with the most time."""
+    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    d = by_kind[dom]
+    share = d["ms"] / sum(v["ms"] for v in by_kind.values())
+    sec = d["ms"] / 1e3
+    if dom == 3:
+        bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
+        peak = bf16 * (TF32_OVER_BF16 if mode == "tf32" else 1.0)
+        achieved = d["cmacs"] * TENSOR_FLOPS_PER_CMAC[mode] / sec / 1e12
+        src = "%s bf16 %s (MEASURED_PEAKS.json)%s" % (
+            "sustained" if sustained else "burst", peak_src,
+            " x nominal tf32/bf16 ratio 1.1/2.25" if mode == "tf32" else "")
+        r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "frac": achieved / peak, "peak_source": src,
+             "algorithmic_flops": "%d*M*N*K tensor flops per node (3M, %s part pairs)" % (
+                 TENSOR_FLOPS_PER_CMAC[mode], mode)}
+    else:
+        achieved = d["cmacs"] * 8 / sec / 1e12
+        r = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "frac": achieved / FP32_PEAK_TFLOPS,
+             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
+             "algorithmic_flops": "8*M*N*K FP32 flops per node (4 real FMAs per complex MAC)"}
+    r.update({"traffic": kernel_traffic(KIND_NAMES[dom]), "kernel": KIND_NAMES[dom],
+              "launches": d["launches"], "share_of_timed_kernel_time": share})
+    return r
+
+
+def top_nodes(recs, stats, n=6):
+    agg = {}
+    for r in recs:
+        key = (r["node"], r["kind"])
+        agg[key] = agg.get(key, 0.0) + r["ms"]
+    nodes = stats["nodes"]
+    out = []
+    for (node, kind), ms in sorted(agg.items(), key=lambda x: -x[1])[:n]:
+        i = node - stats["n_leaves"]
+        mnk = nodes[i][:3] if 0 <= i < len(nodes) else None
+        out.append({"node": node, "kernel": KIND_NAMES.get(kind, str(kind)), "log2_mnk": mnk, "ms": ms})
+    return out
 
 
 def cpu_threads():
@@ -194,13 +253,65 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def apply_options(net, args):
+    if args.tc_row_bytes:
+        net.set_option("tc_row_bytes", args.tc_row_bytes)
+    if args.tc_group_m:
+        net.set_option("tc_group_m", args.tc_group_m)
+
+
+def single_node(args):
+    """One isolated contraction C[m,n] = sum_k A[m,k] B[k,n] (plus a small root
+    that contracts n away), random complex64 data; prints the node's kernel
+    times. Used for isolated-kernel rooflines and ncu captures."""
+    import torch
+    from tnc_inputs.network import TensorNetwork
+    from paper_2205_00393_gb300 import Network
+    mb, nb, kb = (int(x) for x in args.single_node.split(","))
+    rng = np.random.default_rng(0)
+
+    def rnd(n):
+        return ((rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)) / np.sqrt(2)).astype(np.complex64)
+    # indices: m (dim 2^mb), k (2^kb), n (2^nb), o (2)
+    dims = np.array([1 << mb, 1 << kb, 1 << nb, 2], dtype=np.int64)
+    tn_ = TensorNetwork([rnd(mb + kb), rnd(kb + nb), rnd(nb + 1)], [(0, 1), (1, 2), (2, 3)], dims,
+                        (0, 3), [-1, -1, -1])
+    net = Network.from_tn(tn_)
+    net.set_path([(0, 1), (2, 3)])
+    apply_options(net, args)
+    mode = MODES[args.mode]
+    torch.cuda.set_device(0)
+    for _ in range(args.warmup):
+        net.contract(0, 1, mode)
+    torch.cuda.synchronize()
+    net.set_timing(True)
+    for _ in range(args.steps):
+        net.contract(0, 1, mode)
+    net.check_device()
+    recs, n_launches = net.last_timings()
+    net.set_timing(False)
+    by_kind = kernel_breakdown([r for r in recs if r["node"] == 3])
+    peaks, peak_src = load_peaks()
+    line = {"single_node": [mb, nb, kb], "mode": args.mode, "tc_row_bytes": args.tc_row_bytes, "tc_group_m": args.tc_group_m, "steps": args.steps,
+            "kernel_ms_per_call": {KIND_NAMES[k]: v["ms"] / args.steps for k, v in by_kind.items()},
+            "roofline": roofline_of(by_kind, args.mode, peaks, peak_src, sustained=False),
+            "gpu_launches": n_launches}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnc", choices=["tnc", "reference"])
-    ap.add_argument("--mode", default="fp32", choices=sorted(MODES))
+    ap.add_argument("--mode", default="bf16", choices=sorted(MODES))
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--tc-row-bytes", type=int, default=None)
+    ap.add_argument("--tc-group-m", type=int, default=None)
+    ap.add_argument("--single-node", default=None,
+                    help="MB,NB,KB: time one isolated contraction node (log2 sizes) instead")
     ap.add_argument("--slices-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -210,6 +321,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.single_node:
+        return single_node(args)
 
     import torch
     import torch.distributed as dist
@@ -224,6 +337,7 @@ def main():
     net.set_path(path)
     S = net.find_slices(WORKLOAD["target_log2"], WORKLOAD["sa_seed"])
     net.set_slices(S)
+    apply_options(net, args)
     n_slices = net.n_slices
     B = args.slices_per_step
     mode = MODES[args.mode]
@@ -278,24 +392,9 @@ def main():
     value = flops / T / 1e12
 
     # ---- dominant kernel roofline (per-launch CUDA events over the timed region)
-    by_kind = {}
-    for r in recs:
-        k = r["kind"]
-        d = by_kind.setdefault(k, {"ms": 0.0, "flops": 0.0, "launches": 0})
-        d["ms"] += r["ms"]
-        d["launches"] += 1
-        d["flops"] += 8.0 * (1 << r["mnk_log2"]) * r["batch"]
-    kind_names = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
-                  4: "k_split_operand", -1: "k_slice_sum_f32"}
-    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
-    d = by_kind[dom]
-    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    by_kind = kernel_breakdown(recs)
     peaks, peak_src = load_peaks()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(kind_names[dom]),
-                "kernel": kind_names[dom], "launches": d["launches"],
-                "share_of_timed_kernel_time": d["ms"] / sum(v["ms"] for v in by_kind.values()),
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    roofline = roofline_of(by_kind, args.mode, peaks, peak_src, sustained=True)
 
     # ---- end to end through the public API with host buffers
     leaf_bytes = net.leaf_bytes()
@@ -325,7 +424,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64-fp32" if args.mode == "fp32" else args.mode,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "c64-fp32", "bf16": "c64 via 3x bf16 split, fp32 accum",
+                  "tf32": "c64 via 2x tf32 split, fp32 accum",
+                  "bf16x2": "c64 via 2x bf16 split, fp32 accum"}[args.mode],
         "data": "synthetic",
         "s_per_1024_slices": T / n_sl_tot * 1024 * world if world > 1 else T / n_sl_tot * 1024,
         "config": {"workload": workload_name(), "mode": args.mode, "slices_per_step": B,
@@ -333,15 +434,42 @@ def main():
                    "l2": "working set > L2 (1 GiB intermediates), no flush",
                    "parallelism": "slices sharded over ranks" if world > 1 else "1 GPU"},
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launches,
-        "kernel_time_ms": {kind_names[k]: v["ms"] for k, v in by_kind.items()},
+        "kernel_time_ms": {KIND_NAMES[k]: v["ms"] for k, v in by_kind.items()},
+        "top_nodes": top_nodes(recs, stats),
     }
+    if args.mode != "fp32" and not args.no_fp32_compare:
+        # the plain FP32 CUDA-core path on the same slices, for the split-TC / FP32 ratio
+        for i in range(2):
+            lo, hi = slice_range(i)
+            net.contract(lo, hi, MODES["fp32"], out=out)
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        f32_flops = 0
+        for i in range(args.steps):
+            lo, hi = slice_range(args.warmup + i)
+            net.contract(lo, hi, MODES["fp32"], out=out)
+            f32_flops += node_flops(stats, hi - lo)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        Tf = ev0.elapsed_time(ev1) / 1e3
+        if world > 1:
+            t = torch.tensor([Tf], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            Tf = float(t.item())
+            f32_flops *= world
+        line["fp32_value"] = f32_flops / Tf / 1e12
+        line["speedup_vs_fp32"] = line["value"] / line["fp32_value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import planner
         path_py = [tuple(p) for p in path]
-        macs, dt = run_oracle_sample(ref_net, path_py, S)
+        macs, dt, ref0 = run_oracle_sample(ref_net, path_py, S)
         line["cpu_baseline"] = {"value": 8 * macs / dt / 1e12, "unit": UNIT, "cores": cpu_threads(),
                                 "kind": "oracle",
-                                "sample": "one full slice of the workload (NumPy complex128 tensordot per node), %.1f s" % dt}
+                                "sample": "one full slice (slice 0) of the workload, NumPy complex128 "
+                                          "tensordot per node, %.1f s" % dt}
+        got = net.contract(0, 1, mode, out=out).cpu().numpy()
+        rms = float(np.sqrt(np.mean(np.abs(ref0) ** 2)))
+        line["rel_err_vs_oracle"] = float(np.max(np.abs(got - ref0) / np.maximum(np.abs(ref0), rms)))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -152,6 +152,14 @@ tnc_status tnc_check_device(tnc_net_t net, void* stream);
  * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace. */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 
+/* Tuning options of the tensor-core GEMM (no effect on results):
+ *  "tc_row_bytes"  64 or 128 (default 128): bytes of K per tile row and
+ *                  pipeline stage, also the shared-memory swizzle width
+ *  "tc_group_m"    1..64 (default 1): output row tiles per rasterisation
+ *                  group (consecutive CTAs sweep all column tiles of a group)
+ * Errors: TNC_E_INVALID for an unknown key or value. */
+tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value);
+
 /* Per-launch timing: when enabled, every kernel launch of tnc_contract is
  * bracketed by CUDA events recorded on the contraction's stream. Each call
  * clears the records and the launch counter, which then accumulate over all

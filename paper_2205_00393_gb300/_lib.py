@@ -61,6 +61,7 @@ def load_library():
         "tnc_stats": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
         "tnc_set_timing": [ctypes.c_void_p, ctypes.c_int],
         "tnc_check_device": [ctypes.c_void_p, ctypes.c_void_p],
+        "tnc_set_option": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64],
         "tnc_last_timings": [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                              c_i64p, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int), c_i64p],
     }
@@ -200,6 +201,10 @@ class Network:
                                     _stream_ptr(stream))
         _check(self._lib, st)
         return out
+
+    def set_option(self, key, value):
+        """Tensor-core tuning option (see tnc_set_option in include/tnc.h)."""
+        _check(self._lib, self._lib.tnc_set_option(self._h, key.encode(), int(value)))
 
     def check_device(self, stream=None):
         """Wait for the stream; raise TNCError if a device-side wait gave up."""

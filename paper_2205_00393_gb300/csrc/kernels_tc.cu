@@ -35,19 +35,22 @@ namespace tnc {
 namespace {
 
 constexpr int TM = 128, TN = 128;
-constexpr int PART_TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes (one swizzle row each)
+constexpr int SMEM_PIPE = 192 * 1024;             // shared memory for the TMA ring
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kErrTimeout = 4;
 
-template <int KIND> struct Cfg;
-template <> struct Cfg<0> {  // BF16 parts, kind::f16
-    static constexpr int PARTS = 3, NPAIRS = 6, STAGES = 2, ELEM = 2, BK = 64;
-};
-template <> struct Cfg<1> {  // TF32 parts, kind::tf32
-    static constexpr int PARTS = 2, NPAIRS = 3, STAGES = 3, ELEM = 4, BK = 32;
-};
-template <> struct Cfg<2> {  // two BF16 parts, kind::f16 (cheaper, ~16-bit accurate)
-    static constexpr int PARTS = 2, NPAIRS = 3, STAGES = 3, ELEM = 2, BK = 64;
+// KIND 0: three BF16 parts (6 pairs), kind::f16; 1: two TF32 parts (3 pairs),
+// kind::tf32; 2: two BF16 parts (3 pairs), kind::f16. ROWB: bytes of K per
+// tile row and k-block, which is also the swizzle width (64 or 128).
+template <int KIND, int ROWB> struct Cfg {
+    static constexpr int PARTS = KIND == 0 ? 3 : 2;
+    static constexpr int NPAIRS = KIND == 0 ? 6 : 3;
+    static constexpr int ELEM = KIND == 1 ? 4 : 2;
+    static constexpr int BK = ROWB / ELEM;                     // K elements per k-block
+    static constexpr int PART_TILE = 128 * ROWB;               // bytes of one part tile
+    static constexpr int STAGE_BYTES = 2 * PARTS * PART_TILE;  // A and B parts of one product
+    static constexpr int STAGES = SMEM_PIPE / STAGE_BYTES;
+    static constexpr int KSTEPS = ROWB / 32;                   // MMAs per k-block (32 bytes of K each)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -92,15 +95,16 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart, descriptor version 1.
+// Shared-memory matrix descriptor: K-major, ROWB-byte swizzle (layout type
+// 2 = 128B, 4 = 64B), 8-row groups 8*ROWB bytes apart, descriptor version 1.
+template <int ROWB>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-    d |= (uint64_t)1 << 46;             // version
-    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * ROWB) >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;                    // version
+    d |= (uint64_t)(ROWB == 128 ? 2 : 4) << 61;
     return d;
 }
 
@@ -170,13 +174,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int KIND>
+template <int KIND, int ROWB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ TcGemmParams p) {
-    using C_ = Cfg<KIND>;
+    using C_ = Cfg<KIND, ROWB>;
+    constexpr int PART_TILE_BYTES = C_::PART_TILE;
     constexpr int STAGE_A = C_::PARTS * PART_TILE_BYTES;
     constexpr int STAGE_BYTES = 2 * STAGE_A;
+    const int GROUP_M = p.group_m < 1 ? 1 : p.group_m;
     extern __shared__ __align__(1024) uint8_t dsmem[];
     __shared__ __align__(8) uint64_t full_bar[C_::STAGES], empty_bar[C_::STAGES], tfull[3], tfree[3], drain_bar;
     __shared__ uint32_t tmem_base_sh;
@@ -185,9 +191,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     const int64_t N = 1ll << p.nb, K = 1ll << p.kb;
-    const int64_t tiles_n = N / TN;
-    const int m0 = (int)((blockIdx.x / tiles_n) * TM);
-    const int n0 = (int)((blockIdx.x % tiles_n) * TN);
+    // grouped rasterisation: consecutive CTAs cover GROUP_M row tiles x all column tiles
+    const int64_t tiles_n = N / TN, tiles_m = (1ll << p.mb) / TM;
+    const int64_t per_group = (int64_t)GROUP_M * tiles_n;
+    const int64_t grp = blockIdx.x / per_group, in_grp = blockIdx.x % per_group;
+    const int64_t gm = (tiles_m - grp * GROUP_M) < GROUP_M ? (tiles_m - grp * GROUP_M) : GROUP_M;
+    const int m0 = (int)((grp * GROUP_M + in_grp % gm) * TM);
+    const int n0 = (int)((in_grp / gm) * TN);
     const int z = blockIdx.z;
     const int nkb = (int)(K / C_::BK);
     const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;  // k-blocks per chunk
@@ -279,9 +289,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int pa = KIND == 0 ? kPairsBF16[q][0] : kPairs2[q][0];
                 const int pb = KIND == 0 ? kPairsBF16[q][1] : kPairs2[q][1];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {  // 4 MMAs of 32 bytes of K per 128-byte row
-                    const uint64_t ad = smem_desc(sa + pa * PART_TILE_BYTES + j * 32);
-                    const uint64_t bd = smem_desc(sb + pb * PART_TILE_BYTES + j * 32);
+                for (int j = 0; j < C_::KSTEPS; ++j) {  // MMAs of 32 bytes of K per swizzle row
+                    const uint64_t ad = smem_desc<ROWB>(sa + pa * PART_TILE_BYTES + j * 32);
+                    const uint64_t bd = smem_desc<ROWB>(sb + pb * PART_TILE_BYTES + j * 32);
                     mma<KIND>(d, ad, bd, idesc, (kbi > 0 || q > 0 || j > 0) ? 1u : 0u);
                 }
             }
@@ -382,41 +392,44 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
-constexpr int SR = 32, SK = 64;  // split tile: 32 rows x 64 k
+constexpr int SPLIT_TILE = 2048;  // elements per split tile: 32 rows x 64 k, or 64 rows x 32 k
 
 // planes: out[((z * (3*PARTS) + q) * R + r) * K + k], q = t * PARTS + part
 template <int KIND>
 __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ SplitParams p) {
-    using C_ = Cfg<KIND>;
-    __shared__ float2 tile[SR][SK + 1];
-    __shared__ int64_t roff[SR], koff[SK];
+    using C_ = Cfg<KIND, 64>;
+    __shared__ float2 tile[SPLIT_TILE + 64];
+    __shared__ int64_t roff[64], koff[64];
     const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
+    const int SK = K >= 64 ? 64 : (int)K;
+    const int SR = SPLIT_TILE / SK;
+    const int LD = SK + 1;
     const int64_t tiles_k = K / SK;
     const int64_t r0 = (blockIdx.x / tiles_k) * SR, k0 = (blockIdx.x % tiles_k) * SK;
     const int z = blockIdx.z;
     const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, p.slice0 + z);
     const int tid = threadIdx.x;
     if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
-    else if (tid < SR + SK) koff[tid - SR] = bits_offset(k0 + tid - SR, p.ks, p.kb, 0);
+    else if (tid >= 64 && tid < 64 + SK) koff[tid - 64] = bits_offset(k0 + tid - 64, p.ks, p.kb, 0);
     __syncthreads();
     const bool kfast = p.kb > 0 && p.ks[0] == 1;
 #pragma unroll
-    for (int i = 0; i < (SR * SK) / 256; ++i) {
+    for (int i = 0; i < SPLIT_TILE / 256; ++i) {
         int e = tid + i * 256;
         int rr, kk;
         if (kfast) { kk = e % SK; rr = e / SK; }
         else { rr = e % SR; kk = e / SR; }
-        tile[rr][kk] = src[roff[rr] + koff[kk]];
+        tile[rr * LD + kk] = src[roff[rr] + koff[kk]];
     }
     __syncthreads();
     constexpr int Q = 3 * C_::PARTS;
     const int64_t plane = R * K;
     uint8_t* out = reinterpret_cast<uint8_t*>(p.dst) + (int64_t)z * Q * plane * C_::ELEM;
 #pragma unroll
-    for (int i = 0; i < (SR * SK / 2) / 256; ++i) {
+    for (int i = 0; i < (SPLIT_TILE / 2) / 256; ++i) {
         int e = tid + i * 256;
         int kp = e % (SK / 2), rr = e / (SK / 2);
-        float2 x0 = tile[rr][2 * kp], x1 = tile[rr][2 * kp + 1];
+        float2 x0 = tile[rr * LD + 2 * kp], x1 = tile[rr * LD + 2 * kp + 1];
         float v0[3] = {x0.x, x0.y, x0.x + x0.y};
         float v1[3] = {x1.x, x1.y, x1.x + x1.y};
         const int64_t idx = (r0 + rr) * K + k0 + 2 * kp;
@@ -465,42 +478,54 @@ EncodeFn encoder() {
 }
 
 // 4D map over planes [batch][3*PARTS][rows][K]; box = (BK, 128, PARTS, 1).
-template <int KIND>
+template <int KIND, int ROWB>
 bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int batch) {
-    using C_ = Cfg<KIND>;
+    using C_ = Cfg<KIND, ROWB>;
     EncodeFn enc = encoder();
     if (!enc) return false;
     const int Q = 3 * C_::PARTS;
     cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Q, (cuuint64_t)batch};
     cuuint64_t strides[3] = {(cuuint64_t)(K * C_::ELEM), (cuuint64_t)(rows * K * C_::ELEM),
                              (cuuint64_t)(Q * rows * K * C_::ELEM)};
-    cuuint32_t box[4] = {(cuuint32_t)C_::BK, 128u, (cuuint32_t)C_::PARTS, 1u};
+    cuuint32_t box[4] = {(cuuint32_t)C_::BK, 128u, (cuuint32_t)C_::PARTS, 1u};  // BK * ELEM = ROWB bytes
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(map, KIND == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     ROWB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-template <int KIND>
+template <int KIND, int ROWB>
 cudaError_t launch_tc_impl(const TcGemmParams& p, const void* planesA, const void* planesB, int batch,
                            cudaStream_t s) {
-    using C_ = Cfg<KIND>;
+    using C_ = Cfg<KIND, ROWB>;
     const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
+    if (K % C_::BK) return cudaErrorInvalidValue;
     CUtensorMap ta, tb;
-    if (!make_map<KIND>(&ta, planesA, M, K, batch) || !make_map<KIND>(&tb, planesB, N, K, batch))
+    if (!make_map<KIND, ROWB>(&ta, planesA, M, K, batch) || !make_map<KIND, ROWB>(&tb, planesB, N, K, batch))
         return cudaErrorInvalidValue;
-    const int smem = C_::STAGES * 2 * C_::PARTS * PART_TILE_BYTES + 1024;
+    const int smem = C_::STAGES * C_::STAGE_BYTES + 1024;
+    static_assert(C_::STAGES >= 2 && C_::STAGES * C_::STAGE_BYTES + 1024 <= 227 * 1024, "shared memory");
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_cgemm_tc<KIND, ROWB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t tiles = (M / TM) * (N / TN);
-    k_cgemm_tc<KIND><<<dim3((unsigned)tiles, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
+    k_cgemm_tc<KIND, ROWB><<<dim3((unsigned)tiles, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
     return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_tc_rows(const TcGemmParams& p, const void* pa, const void* pb, int batch, cudaStream_t s) {
+    // 128-byte rows need K to span whole 128-byte k-blocks
+    const int64_t K = 1ll << p.kb;
+    if (p.row_bytes == 128 && K % Cfg<KIND, 128>::BK == 0) return launch_tc_impl<KIND, 128>(p, pa, pb, batch, s);
+    return launch_tc_impl<KIND, 64>(p, pa, pb, batch, s);
 }
 
 }  // namespace
@@ -510,11 +535,13 @@ static int kind_of(int mode) { return mode == 1 ? 1 : (mode == 2 ? 0 : 2); }
 
 int tc_plane_count(int mode) { return mode == 2 ? 9 : 6; }
 int tc_elem_bytes(int mode) { return mode == 1 ? 4 : 2; }
-int tc_min_kb(int) { return 6; }
+int tc_min_kb(int) { return 5; }
 
 cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s) {
     const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
-    if (R < SR || K < SK || batch < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
+    if (K < 32 || batch < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
+    const int64_t SK = K >= 64 ? 64 : K, SR = SPLIT_TILE / SK;
+    if (R < SR) return cudaErrorInvalidConfiguration;
     const int64_t blocks = (R / SR) * (K / SK);
     const dim3 grid((unsigned)blocks, 1, batch);
     switch (kind_of(mode)) {
@@ -530,9 +557,9 @@ cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA
     if (p.mb < 7 || p.nb < 7 || p.kb < tc_min_kb(mode) || batch < 1 || batch > 65535)
         return cudaErrorInvalidConfiguration;
     switch (kind_of(mode)) {
-        case 0: return launch_tc_impl<0>(p, planesA, planesB, batch, s);
-        case 1: return launch_tc_impl<1>(p, planesA, planesB, batch, s);
-        default: return launch_tc_impl<2>(p, planesA, planesB, batch, s);
+        case 0: return launch_tc_rows<0>(p, planesA, planesB, batch, s);
+        case 1: return launch_tc_rows<1>(p, planesA, planesB, batch, s);
+        default: return launch_tc_rows<2>(p, planesA, planesB, batch, s);
     }
 }
 

@@ -124,6 +124,9 @@ struct tnc_net {
     void* ws_own = nullptr;
     size_t ws_own_bytes = 0;
     int64_t last_batch = 0;
+    // tensor-core tile options (tnc_set_option)
+    int tc_row_bytes = 128;
+    int tc_group_m = 1;
     // per-launch timing (tnc_set_timing) and launch accounting
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -464,6 +467,8 @@ tnc_status launch_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& 
     tp.C = g.C;
     tp.c_batch_stride = g.c_batch_stride;
     tp.err = net->d_err;
+    tp.row_bytes = net->tc_row_bytes;
+    tp.group_m = net->tc_group_m;
     CUDA_TRY(timed_begin(net, np.v, K_TC, b, s));
     CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
     CUDA_TRY(timed_end(net, s));
@@ -772,6 +777,21 @@ tnc_status tnc_check_device(tnc_net_t net, void* stream) {
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     if (h == TNC_E_TIMEOUT) return fail(TNC_E_TIMEOUT, "a device-side wait gave up (tensor-core pipeline)");
     if (h) return fail(TNC_E_CUDA, "device error word " + std::to_string(h));
+    return TNC_OK;
+}
+
+tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
+    if (!net || !key) return fail(TNC_E_INVALID, "NULL argument");
+    std::string k(key);
+    if (k == "tc_row_bytes") {
+        if (value != 64 && value != 128) return fail(TNC_E_INVALID, "tc_row_bytes must be 64 or 128");
+        net->tc_row_bytes = (int)value;
+    } else if (k == "tc_group_m") {
+        if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");
+        net->tc_group_m = (int)value;
+    } else {
+        return fail(TNC_E_INVALID, "unknown option " + k);
+    }
     return TNC_OK;
 }
 

@@ -49,7 +49,7 @@ def _three_leaf(seed, mb, nb, kb, permuted):
 
 
 @pytest.mark.parametrize("mode", [2, 1, 3])
-@pytest.mark.parametrize("mb,nb,kb,permuted", [(7, 7, 6, False), (8, 9, 7, True), (9, 8, 10, False)])
+@pytest.mark.parametrize("mb,nb,kb,permuted", [(7, 7, 6, False), (8, 9, 7, True), (9, 8, 10, False), (8, 7, 5, True)])
 def test_tc_node_vs_oracle(lib, mode, mb, nb, kb, permuted):
     from paper_2205_00393_gb300 import Network
     net_ref = _three_leaf(100 + mb + nb + kb, mb, nb, kb, permuted)
