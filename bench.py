@@ -162,7 +162,7 @@ def kernel_breakdown(recs):
         d["ms"] += r["ms"]
         d["launches"] += 1
         if r["kind"] in (0, 1, 2, 3):
-            d["cmacs"] += float(1 << r["mnk_log2"]) * r["batch"]
+            d["cmacs"] += r["cmacs"]
     return by_kind
 
 
@@ -203,7 +203,7 @@ def top_nodes(recs, stats, n=6):
     out = []
     for (node, kind), ms in sorted(agg.items(), key=lambda x: -x[1])[:n]:
         i = node - stats["n_leaves"]
-        mnk = nodes[i][:3] if 0 <= i < len(nodes) else None
+        mnk = nodes[i][:3] if 0 <= i < len(nodes) and node >= 0 else "grouped level launches"
         out.append({"node": node, "kernel": KIND_NAMES.get(kind, str(kind)), "log2_mnk": mnk, "ms": ms})
     return out
 
@@ -290,7 +290,7 @@ def single_node(args):
     net.check_device()
     recs, n_launches = net.last_timings()
     net.set_timing(False)
-    by_kind = kernel_breakdown([r for r in recs if r["node"] == 3])
+    by_kind = kernel_breakdown([r for r in recs if r["node"] in (3, -1) and r["kind"] in (3, 4, 0)])
     peaks, peak_src = load_peaks()
     line = {"single_node": [mb, nb, kb], "mode": args.mode, "tc_row_bytes": args.tc_row_bytes, "tc_group_m": args.tc_group_m, "steps": args.steps,
             "kernel_ms_per_call": {KIND_NAMES[k]: v["ms"] / args.steps for k, v in by_kind.items()},

@@ -169,11 +169,12 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable);
 /* Launch records since the last tnc_set_timing (waits for their events): per timed
  * launch the node's tensor id, kernel kind (0 FP32 GEMM, 1 FP64 root reduction,
  * 2 GEMM root + FP64 slice sum, 3 tensor-core GEMM, 4 operand split,
- * -1 leaf slice sum), slice batch, log2(M*N*K)
- * and milliseconds; any output array may be NULL. *n_out receives the number
+ * -1 leaf slice sum), slice batch, complex multiply-accumulates of the
+ * launch (all its nodes and slices) and milliseconds; a grouped launch of
+ * several nodes of one tree level reports node -1. Any output array may be NULL. *n_out receives the number
  * of records (TNC_E_INVALID if it exceeds cap); *n_launches (may be NULL) the
  * number of kernels launched since then (counted with timing on or off). */
-tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, int64_t* mnk_log2,
+tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, double* cmacs,
                             float* ms, int cap, int* n_out, int64_t* n_launches);
 
 /* Capacity, in complex doubles, of the static scratch of tnc_reduce_pair_noalloc. */

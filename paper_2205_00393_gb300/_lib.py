@@ -63,7 +63,7 @@ def load_library():
         "tnc_check_device": [ctypes.c_void_p, ctypes.c_void_p],
         "tnc_set_option": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64],
         "tnc_last_timings": [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
-                             c_i64p, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int), c_i64p],
+                             P(ctypes.c_double), P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int), c_i64p],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -214,18 +214,19 @@ class Network:
         _check(self._lib, self._lib.tnc_set_timing(self._h, 1 if enable else 0))
 
     def last_timings(self, cap=1 << 16):
-        """Per-launch records of the last contraction: list of dicts with node,
-        kind, batch, mnk_log2 and ms; plus the number of kernels launched."""
+        """Per-launch records since set_timing(True): list of dicts with node
+        (-1 for a grouped launch), kind, batch, cmacs (complex multiply-
+        accumulates) and ms; plus the number of kernels launched."""
         node = (ctypes.c_int * cap)()
         kind = (ctypes.c_int * cap)()
         batch = (ctypes.c_int * cap)()
-        mnk = (ctypes.c_int64 * cap)()
+        mnk = (ctypes.c_double * cap)()
         ms = (ctypes.c_float * cap)()
         n = ctypes.c_int()
         nl = ctypes.c_int64()
         _check(self._lib, self._lib.tnc_last_timings(self._h, node, kind, batch, mnk, ms, cap,
                                                       ctypes.byref(n), ctypes.byref(nl)))
-        recs = [dict(node=node[i], kind=kind[i], batch=batch[i], mnk_log2=mnk[i], ms=ms[i])
+        recs = [dict(node=node[i], kind=kind[i], batch=batch[i], cmacs=mnk[i], ms=ms[i])
                 for i in range(n.value)]
         return recs, nl.value
 

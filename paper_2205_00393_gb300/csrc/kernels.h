@@ -99,6 +99,12 @@ cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA
 void set_last_error(const std::string& msg);
 
 cudaError_t launch_gemm_f32(const GemmParams& p, int batch, cudaStream_t s);
+// 64x64 output tiles of one FP32 contraction of 2^mb x 2^nb outputs.
+int64_t gemm_f32_tiles(int mb, int nb);
+// Independent FP32 contractions in one launch; params and tile_off (n + 1
+// prefix offsets of their tile counts) are device arrays.
+cudaError_t launch_gemm_f32_group(const GemmParams* d_params, const int64_t* d_tile_off, int n,
+                                  int64_t total_tiles, int64_t slice0, int batch, cudaStream_t s);
 cudaError_t launch_root_partials(const RootParams& p, int batch, double2* partials, cudaStream_t s);
 cudaError_t launch_accumulate_partials(const double2* partials, int count, const PermParams& pp,
                                        double2* out, cudaStream_t s);

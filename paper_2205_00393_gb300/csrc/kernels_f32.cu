@@ -55,18 +55,27 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
     sum = t;
 }
 
-__global__ void __launch_bounds__(NT) k_gemm_f32(const __grid_constant__ GemmParams p) {
-    __shared__ __align__(16) float2 As[2][BK][BM + PAD];
-    __shared__ __align__(16) float2 Bs[2][BK][BN + PAD];
-    __shared__ int64_t rowA[BM], colB[BN], klA[BK], klB[BK];
+struct GemmSmem {
+    float2 As[2][BK][BM + PAD];
+    float2 Bs[2][BK][BN + PAD];
+    int64_t rowA[BM], colB[BN], klA[BK], klB[BK];
+};
 
+// One 64x64 output tile `tile` of slice z (slice id slice0 + z) of the
+// contraction described by p.
+__device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int z, int64_t slice0,
+                                          GemmSmem& sm) {
+    auto& As = sm.As;
+    auto& Bs = sm.Bs;
+    auto& rowA = sm.rowA;
+    auto& colB = sm.colB;
+    auto& klA = sm.klA;
+    auto& klB = sm.klB;
     const int tid = threadIdx.x;
     const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
     const int64_t tiles_n = (N + BN - 1) / BN;
-    const int64_t tile = blockIdx.x;
     const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-    const int z = blockIdx.z;
-    const int64_t s = p.slice0 + z;
+    const int64_t s = slice0 + z;
     const float2* __restrict__ A = p.A.ptr + z * p.A.batch_stride + slice_offset(p.A, s);
     const float2* __restrict__ B = p.B.ptr + z * p.B.batch_stride + slice_offset(p.B, s);
 
@@ -180,6 +189,27 @@ __global__ void __launch_bounds__(NT) k_gemm_f32(const __grid_constant__ GemmPar
     }
 }
 
+__global__ void __launch_bounds__(NT) k_gemm_f32(const __grid_constant__ GemmParams p) {
+    __shared__ __align__(16) GemmSmem sm;
+    gemm_tile(p, blockIdx.x, blockIdx.z, p.slice0, sm);
+}
+
+// Many independent contractions in one launch (nodes of one tree level): CTA
+// b serves tile b - tile_off[i] of node i, tile_off[i] <= b < tile_off[i+1].
+__global__ void __launch_bounds__(NT) k_gemm_f32_group(const GemmParams* __restrict__ params,
+                                                       const int64_t* __restrict__ tile_off, int n,
+                                                       int64_t slice0) {
+    __shared__ __align__(16) GemmSmem sm;
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    gemm_tile(params[lo], b - tile_off[lo], blockIdx.z, slice0, sm);
+}
+
 // FP64 partial sums of a contraction with R = M*N <= 64 outputs.
 __global__ void __launch_bounds__(256) k_root_partials(const __grid_constant__ RootParams rp,
                                                        double2* __restrict__ partials) {
@@ -257,6 +287,19 @@ cudaError_t launch_gemm_f32(const GemmParams& p, int batch, cudaStream_t s) {
     int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     if (tiles > 0x7fffffffll || batch < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
     k_gemm_f32<<<dim3((unsigned)tiles, 1, batch), NT, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+int64_t gemm_f32_tiles(int mb, int nb) {
+    int64_t M = 1ll << mb, N = 1ll << nb;
+    return ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+}
+
+cudaError_t launch_gemm_f32_group(const GemmParams* d_params, const int64_t* d_tile_off, int n,
+                                  int64_t total_tiles, int64_t slice0, int batch, cudaStream_t s) {
+    if (n < 1 || total_tiles < 1 || total_tiles > 0x7fffffffll || batch < 1 || batch > 65535)
+        return cudaErrorInvalidConfiguration;
+    k_gemm_f32_group<<<dim3((unsigned)total_tiles, 1, batch), NT, 0, s>>>(d_params, d_tile_off, n, slice0);
     return cudaGetLastError();
 }
 

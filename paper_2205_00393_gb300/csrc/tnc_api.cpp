@@ -14,6 +14,7 @@
 #include "tnc.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -69,6 +70,7 @@ struct NodePlan {
 
 struct Plan {
     bool valid = false;
+    uint64_t version = 0;                                   // distinguishes rebuilt plans
     std::vector<int> slice_bit_of_mode;                     // by mode, -1 if not sliced
     std::vector<std::vector<int>> layout;                   // effective modes per tensor
     std::vector<std::vector<std::pair<int, int64_t>>> str;  // (mode, stride) per tensor
@@ -84,6 +86,25 @@ struct Arena {
     std::vector<int64_t> planes_a, planes_b;  // per node (tensor-core split planes)
     int64_t root_scratch_off = -1; // FP64 partials or FP32 per-slice root
     int64_t peak = 0;
+};
+
+// Level groups: nodes whose inputs are ready at the same time run in one
+// launch. Invariant nodes are levelled over the invariant forest, per-slice
+// nodes over per-slice dependencies; the root runs last on its own.
+struct Group {
+    bool per_slice = false;
+    std::vector<int> fp32;   // node tensor ids run by one grouped FP32 launch
+    std::vector<int> tc;     // nodes launched one by one: tensor-core nodes and large FP32 nodes
+    int first = 0;           // first entry of the group's parameters in the table
+    int off_first = 0;       // first entry of its n + 1 tile offsets
+    int64_t tiles = 0;
+    double cmacs = 0.0;      // per slice
+};
+
+struct GroupPlan {
+    std::vector<Group> inv, ps;
+    std::vector<tnc::GemmParams> params;
+    std::vector<int64_t> tile_off;
 };
 
 int64_t stride_of(const std::vector<std::pair<int, int64_t>>& s, int mode) {
@@ -127,16 +148,24 @@ struct tnc_net {
     // tensor-core tile options (tnc_set_option)
     int tc_row_bytes = 128;
     int tc_group_m = 1;
+    // cached level groups and their device parameter table
+    std::string group_key;
+    GroupPlan groups;
+    tnc::GemmParams* d_params = nullptr;
+    int64_t* d_tile_off = nullptr;
+    size_t d_params_cap = 0, d_tile_cap = 0;
     // per-launch timing (tnc_set_timing) and launch accounting
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    struct TimedLaunch { int node; int kind; int batch; size_t ev; };
+    struct TimedLaunch { int node; int kind; int batch; double cmacs; size_t ev; };
     std::vector<TimedLaunch> timed;
     int64_t launches = 0;
 
     ~tnc_net() {
         if (d_leaves) cudaFree(d_leaves);
         if (d_err) cudaFree(d_err);
+        if (d_params) cudaFree(d_params);
+        if (d_tile_off) cudaFree(d_tile_off);
         if (ws_own) cudaFree(ws_own);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
@@ -147,8 +176,10 @@ namespace {
 // ------------------------------------------------------------- planning ----
 
 void build_plan(tnc_net* net) {
+    static uint64_t counter = 0;
     Plan& P = net->plan;
     P = Plan();
+    P.version = ++counter;
     const tnc::Tree& T = *net->tree;
     const int nt = T.n_tensors();
     int total_modes = net->mode_base.empty() ? 0 : net->mode_base.back();
@@ -260,6 +291,8 @@ void build_plan(tnc_net* net) {
 
 int64_t tensor_bytes(const Plan& P, int v) { return (int64_t)8 << P.layout[v].size(); }
 
+std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice);
+
 int64_t planes_bytes(int mode, int rb, int kb, int64_t batch) {
     return batch * (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode) << (rb + kb);
 }
@@ -297,32 +330,34 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
         release(ar.planes_a[i]);
         release(ar.planes_b[i]);
     };
-    // phase 1: invariant nodes
-    for (const NodePlan& np : P.nodes) {
-        if (np.per_slice) continue;
-        const bool tc = tc_node(mode, np.mb, np.nb, np.kb, np.is_root);
-        if (tc) tc_planes(np, 1);
-        ar.off[np.v] = alloc(tensor_bytes(P, np.v));
-        if (tc) tc_release(np);
-        for (int c : {np.A, np.B})
-            if (c >= net->n_leaves) release(ar.off[c]);
-    }
-    // phase 2: one batch of per-slice nodes
-    for (const NodePlan& np : P.nodes) {
-        if (!np.per_slice) continue;
-        if (np.is_root) {
-            int64_t bytes = np.kind == K_ROOT_F64
-                                ? nb * np.chunks * (int64_t)16 << (np.mb + np.nb)
-                                : nb * tensor_bytes(P, np.v);
-            ar.root_scratch_off = alloc(bytes);
-        } else {
-            const bool tc = tc_node(mode, np.mb, np.nb, np.kb, np.is_root);
-            if (tc) tc_planes(np, nb);
-            ar.off[np.v] = alloc(nb * tensor_bytes(P, np.v));
-            if (tc) tc_release(np);
+    // Lifetimes follow the executed order: one tree level at a time; all
+    // outputs of a level are live together, inputs die after their level.
+    auto run_level = [&](const Group& g, int64_t b) {
+        for (int v : g.fp32) ar.off[v] = alloc(b * tensor_bytes(P, v));
+        for (int v : g.tc) ar.off[v] = alloc(b * tensor_bytes(P, v));
+        for (int v : g.tc) {
+            const NodePlan& np = P.nodes[v - net->n_leaves];
+            if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) continue;
+            tc_planes(np, b);
+            tc_release(np);
         }
-        for (int c : {np.A, np.B})
-            if (c >= net->n_leaves && P.per_slice[c]) release(ar.off[c]);
+        for (auto* list : {&g.fp32, &g.tc})
+            for (int v : *list) {
+                const NodePlan& np = P.nodes[v - net->n_leaves];
+                for (int c : {np.A, np.B})
+                    if (c >= net->n_leaves && P.per_slice[c] == (char)g.per_slice) release(ar.off[c]);
+            }
+    };
+    // phase 1: invariant levels (batch 1); invariant tensors consumed by
+    // per-slice nodes stay live for the whole call
+    for (const Group& g : level_groups(net, mode, false)) run_level(g, 1);
+    // phase 2: one batch of per-slice levels, then the root
+    for (const Group& g : level_groups(net, mode, true)) run_level(g, nb);
+    for (const NodePlan& np : P.nodes) {
+        if (!np.is_root) continue;
+        int64_t bytes = np.kind == K_ROOT_F64 ? nb * np.chunks * (int64_t)16 << (np.mb + np.nb)
+                                              : nb * tensor_bytes(P, np.v);
+        ar.root_scratch_off = alloc(bytes);
     }
     ar.peak = top;
     return ar;
@@ -395,9 +430,16 @@ tnc_status ensure_leaves(tnc_net* net, cudaStream_t st) {
 }
 
 // Event pair around one launch when timing is on; returns the pool slot.
-cudaError_t timed_begin(tnc_net* net, int node, int kind, int batch, cudaStream_t s) {
+double node_cmacs(const tnc_net* net, int node) {
+    if (node < net->n_leaves) return 0.0;
+    const NodePlan& np = net->plan.nodes[node - net->n_leaves];
+    return std::ldexp(1.0, np.mb + np.nb + np.kb);
+}
+
+cudaError_t timed_begin(tnc_net* net, int node, int kind, int batch, cudaStream_t s, double cmacs = -1.0) {
     net->launches += 1;
     if (!net->timing) return cudaSuccess;
+    if (cmacs < 0) cmacs = node_cmacs(net, node) * batch;
     size_t slot = net->timed.size() * 2;
     while (net->ev_pool.size() < slot + 2) {
         cudaEvent_t e;
@@ -405,7 +447,7 @@ cudaError_t timed_begin(tnc_net* net, int node, int kind, int batch, cudaStream_
         if (err != cudaSuccess) return err;
         net->ev_pool.push_back(e);
     }
-    net->timed.push_back({node, kind, batch, slot});
+    net->timed.push_back({node, kind, batch, cmacs, slot});
     return cudaEventRecord(net->ev_pool[slot], s);
 }
 
@@ -424,6 +466,87 @@ int64_t pick_batch(const tnc_net* net, int64_t want, size_t budget, int mode) {
     }
     return lo;
 }
+
+std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice) {
+    const Plan& P = net->plan;
+    std::map<int, int> level;  // tensor id -> level
+    std::map<int, Group> by_level;
+    for (const NodePlan& np : P.nodes) {
+        if (np.per_slice != per_slice || np.is_root) continue;
+        int l = 0;
+        for (int c : {np.A, np.B}) {
+            auto it = level.find(c);
+            if (it != level.end()) l = std::max(l, it->second);
+        }
+        level[np.v] = l + 1;
+        Group& g = by_level[l + 1];
+        g.per_slice = per_slice;
+        // large contractions keep their own launch (parameters in kernel parameter space)
+        if (tc_node(mode, np.mb, np.nb, np.kb, np.is_root) || tnc::gemm_f32_tiles(np.mb, np.nb) >= 256)
+            g.tc.push_back(np.v);
+        else
+            g.fp32.push_back(np.v);
+    }
+    std::vector<Group> out;
+    for (auto& kv : by_level) out.push_back(kv.second);
+    return out;
+}
+
+// Build (or reuse) the level groups and upload their parameter table for this
+// plan, mode, batch and workspace.
+tnc_status ensure_groups(tnc_net* net, const Arena& ar, char* ws, int mode, int64_t nb, cudaStream_t s) {
+    std::string key = std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string((uintptr_t)ws) +
+                      ":" + std::to_string(net->plan.version);
+    if (key == net->group_key) return TNC_OK;
+    GroupPlan G;
+    G.inv = level_groups(net, mode, false);
+    G.ps = level_groups(net, mode, true);
+    for (auto* list : {&G.inv, &G.ps}) {
+        for (Group& g : *list) {
+            g.first = (int)G.params.size();
+            g.off_first = (int)G.tile_off.size();
+            int64_t tiles = 0;
+            for (int v : g.fp32) {
+                const NodePlan& np = net->plan.nodes[v - net->n_leaves];
+                tnc::GemmParams gp = gemm_params(net, ar, ws, np, g.per_slice ? nb : 1);
+                gp.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
+                gp.c_batch_stride = g.per_slice ? tensor_bytes(net->plan, np.v) / 8 : 0;
+                gp.slice0 = 0;
+                G.params.push_back(gp);
+                G.tile_off.push_back(tiles);
+                tiles += tnc::gemm_f32_tiles(np.mb, np.nb);
+                g.cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb);
+            }
+            G.tile_off.push_back(tiles);
+            g.tiles = tiles;
+        }
+    }
+    if (G.params.size() > net->d_params_cap) {
+        if (net->d_params) CUDA_TRY(cudaFree(net->d_params));
+        net->d_params = nullptr;
+        CUDA_TRY(cudaMalloc(&net->d_params, std::max<size_t>(1, G.params.size()) * sizeof(tnc::GemmParams)));
+        net->d_params_cap = G.params.size();
+    }
+    if (G.tile_off.size() > net->d_tile_cap) {
+        if (net->d_tile_off) CUDA_TRY(cudaFree(net->d_tile_off));
+        net->d_tile_off = nullptr;
+        CUDA_TRY(cudaMalloc(&net->d_tile_off, std::max<size_t>(1, G.tile_off.size()) * sizeof(int64_t)));
+        net->d_tile_cap = G.tile_off.size();
+    }
+    if (!G.params.empty())
+        CUDA_TRY(cudaMemcpyAsync(net->d_params, G.params.data(), G.params.size() * sizeof(tnc::GemmParams),
+                                 cudaMemcpyHostToDevice, s));
+    if (!G.tile_off.empty())
+        CUDA_TRY(cudaMemcpyAsync(net->d_tile_off, G.tile_off.data(), G.tile_off.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors are freed below
+    net->groups = std::move(G);
+    net->group_key = key;
+    return TNC_OK;
+}
+
+tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, int b, int64_t slice0, int mode,
+                     cudaStream_t s);
 
 // One non-root contraction: FP32 CUDA-core GEMM, or (split modes, large
 // nodes) operand split + tensor-core GEMM. `g` carries operands and output.
@@ -472,6 +595,26 @@ tnc_status launch_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& 
     CUDA_TRY(timed_begin(net, np.v, K_TC, b, s));
     CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
     CUDA_TRY(timed_end(net, s));
+    return TNC_OK;
+}
+
+tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, int b, int64_t slice0, int mode,
+                     cudaStream_t s) {
+    tnc_status st;
+    if (!g.fp32.empty()) {
+        CUDA_TRY(timed_begin(net, -1, K_GEMM_F32, b, s, g.cmacs * b));
+        CUDA_TRY(tnc::launch_gemm_f32_group(net->d_params + g.first, net->d_tile_off + g.off_first,
+                                            (int)g.fp32.size(), g.tiles, slice0, b, s));
+        CUDA_TRY(timed_end(net, s));
+    }
+    for (int v : g.tc) {
+        const NodePlan& np = net->plan.nodes[v - net->n_leaves];
+        tnc::GemmParams gp = gemm_params(net, ar, ws, np, b);
+        gp.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
+        gp.c_batch_stride = g.per_slice ? tensor_bytes(net->plan, np.v) / 8 : 0;
+        gp.slice0 = slice0;
+        if ((st = launch_node(net, ar, ws, np, gp, b, mode, s)) != TNC_OK) return st;
+    }
     return TNC_OK;
 }
 
@@ -702,15 +845,10 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     const Arena ar = plan_arena(net, nb, mode);
     CUDA_TRY(cudaMemsetAsync(net->d_err, 0, sizeof(int), s));
 
-    // invariant nodes once
-    for (const NodePlan& np : P.nodes) {
-        if (np.per_slice) continue;
-        tnc::GemmParams g = gemm_params(net, ar, ws, np, 1);
-        g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
-        g.c_batch_stride = 0;
-        g.slice0 = 0;
-        if ((st = launch_node(net, ar, ws, np, g, 1, mode, s)) != TNC_OK) return st;
-    }
+    if ((st = ensure_groups(net, ar, ws, mode, nb, s)) != TNC_OK) return st;
+    // invariant nodes once, one launch per level
+    for (const Group& g : net->groups.inv)
+        if ((st = run_group(net, ar, ws, g, 1, 0, mode, s)) != TNC_OK) return st;
     tnc::PermParams pp{};
     pp.obits = P.obits;
     for (int j = 0; j < P.obits; ++j) pp.ostride[j] = P.out_stride[j];
@@ -729,16 +867,12 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
             CUDA_TRY(timed_end(net, s));
             continue;
         }
+        for (const Group& g : net->groups.ps)
+            if ((st = run_group(net, ar, ws, g, b, s0, mode, s)) != TNC_OK) return st;
         for (const NodePlan& np : P.nodes) {
-            if (!np.per_slice) continue;
+            if (!np.is_root) continue;
             tnc::GemmParams g = gemm_params(net, ar, ws, np, b);
             g.slice0 = s0;
-            if (!np.is_root) {
-                g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
-                g.c_batch_stride = tensor_bytes(P, np.v) / 8;
-                if ((st = launch_node(net, ar, ws, np, g, b, mode, s)) != TNC_OK) return st;
-                continue;
-            }
             CUDA_TRY(timed_begin(net, np.v, np.kind, b, s));
             if (np.kind == K_ROOT_F64) {
                 tnc::RootParams rp{};
@@ -803,7 +937,7 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable) {
     return TNC_OK;
 }
 
-tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, int64_t* mnk_log2,
+tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, double* cmacs,
                             float* ms, int cap, int* n_out, int64_t* n_launches) {
     if (!net || !n_out) return fail(TNC_E_INVALID, "NULL argument");
     if (n_launches) *n_launches = net->launches;
@@ -818,14 +952,7 @@ tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, int
         if (kind) kind[i] = t.kind;
         if (batch) batch[i] = t.batch;
         if (ms) ms[i] = v;
-        if (mnk_log2) {
-            int64_t x = 0;
-            if (t.node >= net->n_leaves) {
-                const NodePlan& np = net->plan.nodes[t.node - net->n_leaves];
-                x = np.mb + np.nb + np.kb;
-            }
-            mnk_log2[i] = x;
-        }
+        if (cmacs) cmacs[i] = t.cmacs;
     }
     return TNC_OK;
 }
