@@ -142,6 +142,35 @@ tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes);
 tnc_status tnc_contract(tnc_net_t net, int64_t slice_lo, int64_t slice_hi, int mode,
                         double* out_c128, void* stream);
 
+/* Reverse-mode (adjoint) pass. For F = sum_o g_o O_o, with O the sum over
+ * slices [slice_lo, slice_hi) of the sliced contraction and g = grad_out_c128
+ * (device, complex128, in open_ids order), writes the holomorphic
+ * environments dF/dL of every leaf L into grad_leaves_c64 (device,
+ * complex64, all leaves packed back to back as tnc_leaf_bytes describes,
+ * overwritten; leaves with leaf_mask[i] == 0 are left at zero, leaf_mask may
+ * be NULL = all). For a pairwise contraction C = A (x) B (Sec. 2.1.1) the
+ * environment of A is E_C contracted with B over B's free indices, and
+ * likewise for B; environments of slice-invariant subtrees are summed over
+ * the slices in FP64 and propagated once. The forward contractions use
+ * `mode`; the environment contractions run in FP32 on CUDA cores, leaf
+ * gradients accumulate in FP64. budget_bytes bounds the workspace (0 = 32
+ * GiB); as many slices as fit are processed per pass, every intermediate of a
+ * pass is kept for the reverse walk. Errors: TNC_E_OOM if one slice does not
+ * fit the budget; as tnc_contract otherwise. PyTorch's complex gradient
+ * convention (grad = dL/dRe + i dL/dIm) maps to g = conj(grad), and a real
+ * parameter theta then gets dL/dtheta = Re(sum dF/dL * dL/dtheta). */
+tnc_status tnc_contract_backward(tnc_net_t net, int64_t slice_lo, int64_t slice_hi, int mode,
+                                 const double* grad_out_c128, float* grad_leaves_c64,
+                                 const unsigned char* leaf_mask, size_t budget_bytes, void* stream);
+
+/* Chain rule to gate parameters: out_c128[q] = sum_e env[leaf q][e] * dleaf_q[e]
+ * in FP64, for n_params parameters whose leaf tensors are leaf_ids[q] (host
+ * array). dleaf_c64 (device) holds the derivative tensors dL/dparam, one per
+ * parameter, packed in order (each the size of its leaf); env_packed_c64 is
+ * the packed output of tnc_contract_backward; out_c128 is device memory. */
+tnc_status tnc_param_grads(tnc_net_t net, int n_params, const int* leaf_ids, const float* dleaf_c64,
+                           const float* env_packed_c64, double* out_c128, void* stream);
+
 /* Wait for `stream` and report device-side failures of the last
  * contraction: TNC_E_TIMEOUT if a bounded wait inside a tensor-core kernel
  * gave up (the kernel then drained its copies, freed its tensor memory and

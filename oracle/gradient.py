@@ -74,3 +74,25 @@ def statevector_amp_fn(circuit):
     def f(params):
         return statevector.amplitudes(with_fsim_params(circuit, params))
     return f
+
+
+def leaf_environments(network, path, sliced_ids=(), seed=None, slices=None):
+    """Holomorphic environments dF/dL of every leaf L, F = sum_o seed_o O_o
+    with O the (sliced) contraction. F is linear in every leaf, so
+    dF/dL[i] = F evaluated with L replaced by the unit tensor e_i.
+    Returns a list of complex128 arrays shaped like the leaves."""
+    n_out = int(np.prod([network.dims[e] for e in network.open_ids])) if network.open_ids else 1
+    seed = np.ones(n_out, dtype=np.complex128) if seed is None else np.asarray(seed, dtype=np.complex128)
+    envs = []
+    for li, t in enumerate(network.tensors):
+        t = np.asarray(t)
+        env = np.zeros(t.size, dtype=np.complex128)
+        for i in range(t.size):
+            unit = np.zeros(t.size, dtype=np.complex128)
+            unit[i] = 1.0
+            ts = list(network.tensors)
+            ts[li] = unit.reshape(t.shape)
+            out = tn.contract(network.with_tensors(ts), path, sliced_ids, slices)
+            env[i] = np.dot(seed, out)
+        envs.append(env.reshape(t.shape))
+    return envs

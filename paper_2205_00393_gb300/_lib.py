@@ -62,6 +62,10 @@ def load_library():
         "tnc_set_timing": [ctypes.c_void_p, ctypes.c_int],
         "tnc_check_device": [ctypes.c_void_p, ctypes.c_void_p],
         "tnc_set_option": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64],
+        "tnc_contract_backward": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
+        "tnc_param_grads": [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_void_p],
         "tnc_last_timings": [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                              P(ctypes.c_double), P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int), c_i64p],
     }
@@ -121,6 +125,7 @@ class Network:
         self.n_out = int(np.prod([self.dims[e] for e in self.open_ids])) if self.open_ids else 1
         self.sliced = []
         self._ws = None
+        self._sizes = [int(np.prod([self.dims[e] for e in ix])) if len(ix) else 1 for ix in indices]
 
     @classmethod
     def from_tn(cls, tn):
@@ -229,6 +234,47 @@ class Network:
         recs = [dict(node=node[i], kind=kind[i], batch=batch[i], cmacs=mnk[i], ms=ms[i])
                 for i in range(n.value)]
         return recs, nl.value
+
+    def contract_backward(self, grad_out, lo=0, hi=None, mode=FP32, leaf_mask=None, budget_bytes=0,
+                          stream=None):
+        """Holomorphic leaf environments dF/dL, F = sum_o grad_out[o] O[o], as a
+        packed complex64 CUDA tensor (leaves back to back, leaf order)."""
+        import torch
+        if hi is None:
+            hi = self.n_slices
+        # materialise lazy conjugate / negative views: the C ABI reads raw memory
+        g = grad_out.to(device="cuda", dtype=torch.complex128).resolve_conj().resolve_neg().contiguous()
+        out = torch.empty(self.leaf_bytes() // 8, dtype=torch.complex64, device="cuda")
+        mask = None
+        if leaf_mask is not None:
+            m = np.ascontiguousarray(np.asarray(leaf_mask, dtype=np.uint8))
+            mask = m.ctypes.data_as(ctypes.c_void_p)
+        st = self._lib.tnc_contract_backward(self._h, int(lo), int(hi), int(mode), ctypes.c_void_p(g.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), mask, int(budget_bytes),
+                                             _stream_ptr(stream))
+        _check(self._lib, st)
+        return out
+
+    def param_grads(self, leaf_ids, dleaf_packed, env_packed, stream=None):
+        """sum_e env[leaf][e] * dleaf[e] per parameter, FP64, as a complex128 CUDA tensor."""
+        import torch
+        ids = (ctypes.c_int * max(len(leaf_ids), 1))(*[int(x) for x in leaf_ids])
+        out = torch.empty(len(leaf_ids), dtype=torch.complex128, device="cuda")
+        d = dleaf_packed.to(device="cuda", dtype=torch.complex64).resolve_conj().resolve_neg().contiguous()
+        env_packed = env_packed.resolve_conj().resolve_neg().contiguous()
+        st = self._lib.tnc_param_grads(self._h, len(leaf_ids), ids, ctypes.c_void_p(d.data_ptr()),
+                                       ctypes.c_void_p(env_packed.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       _stream_ptr(stream))
+        _check(self._lib, st)
+        return out
+
+    def leaf_slices(self):
+        """(offset, size) in elements of every leaf in the packed layout."""
+        out, off = [], 0
+        for t in self._sizes:
+            out.append((off, t))
+            off += t
+        return out
 
     def stats(self):
         cap = 1 << 22

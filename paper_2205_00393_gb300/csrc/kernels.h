@@ -95,6 +95,36 @@ cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t
 cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
                             int batch, cudaStream_t s);
 
+// Adjoint pass. Root environment seed: E_z[sum_j bit_j(r) ostride[j]] = grad[r].
+struct SeedParams {
+    const double2* grad;
+    int obits;
+    int64_t ostride[kMaxBits];
+    float2* E;
+    int64_t batch_stride;
+};
+
+// Fold per-slice environments of one leaf into its FP64 gradient: leaf mode
+// q (most significant first) is either sliced (sl_bit[q] >= 0: the slice id
+// bit fixing it) or found at env_stride[q] in the environment.
+struct LeafEnvParams {
+    const float2* env;
+    int64_t env_batch_stride;
+    int L;
+    int sl_bit[kMaxBits];
+    int64_t env_stride[kMaxBits];
+    int64_t slice0;
+    double2* grad;
+};
+
+cudaError_t launch_env_seed(const SeedParams& p, int batch, cudaStream_t s);
+cudaError_t launch_leaf_env_accum(const LeafEnvParams& p, int batch, cudaStream_t s);
+cudaError_t launch_accum_batch_f64(const float2* E, int64_t n, int batch, int64_t bs, double2* acc,
+                                   cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double2* src, int64_t n, float2* dst, cudaStream_t s);
+cudaError_t launch_param_grads(int n, const int64_t* env_off, const int64_t* d_off, const int64_t* size,
+                               const float2* env, const float2* d, double2* out, cudaStream_t s);
+
 // Message returned by tnc_last_error() on this thread.
 void set_last_error(const std::string& msg);
 

@@ -27,3 +27,36 @@ def test_network_derivative_matches_statevector():
     a = gradient.exact_network(c, net, path, S)
     b = gradient.exact_statevector(c)
     assert np.allclose(a, b, atol=1e-13)
+
+
+def test_leaf_environments_euler_identity():
+    """F is linear in every leaf, so sum_i L[i] dF/dL[i] = F for each leaf."""
+    c = grid_rqc(2, 2, 3, seed=31, n_open=1)
+    net = circuit_to_network(c)
+    path = planner.greedy_path(net.indices, net.dims)
+    seed = np.array([0.3 - 0.7j, 1.1 + 0.2j])
+    F = np.dot(seed, tn_contract(net, path))
+    envs = gradient.leaf_environments(net, path, (), seed)
+    for L, E in zip(net.tensors, envs):
+        assert abs(np.sum(np.asarray(L) * E) - F) < 1e-13
+
+
+def test_leaf_environments_match_gate_derivatives():
+    c = grid_rqc(2, 2, 3, seed=32)
+    net = circuit_to_network(c)
+    path = planner.greedy_path(net.indices, net.dims)
+    envs = gradient.leaf_environments(net, path)
+    exact = gradient.exact_statevector(c)
+    from tnc_inputs import gates as G
+    k = 0
+    for li, g in enumerate(net.leaf_gate):
+        if g >= 0 and c.gates[g].name == "fsim":
+            th, ph = c.gates[g].params
+            dth = np.sum(envs[li] * G.dfsim_dtheta(th, ph).reshape(2, 2, 2, 2))
+            assert abs(dth - exact[k, 0, 0]) < 1e-13
+            k += 1
+
+
+def tn_contract(net, path):
+    from oracle import tn
+    return tn.contract(net, path)
