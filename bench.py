@@ -42,7 +42,7 @@ TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 *
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
-              4: "k_split_operand", -1: "k_slice_sum_f32"}
+              4: "k_split_operand", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
 
 
 def workload_name():
@@ -300,6 +300,54 @@ def single_node(args):
     return 0
 
 
+def backward_bench(args):
+    """Forward + adjoint pass over a batch of slices per step: environments of
+    every fSim leaf for F = sum of the 64 amplitudes (FP32 environment
+    contractions; forward in --mode)."""
+    import torch
+    from paper_2205_00393_gb300 import Network
+    torch.cuda.set_device(0)
+    c, ref_net = build_network()
+    net = Network.from_tn(ref_net)
+    net.set_path(net.greedy_path())
+    S = net.find_slices(WORKLOAD["target_log2"], WORKLOAD["sa_seed"])
+    net.set_slices(S)
+    apply_options(net, args)
+    mask = np.array([1 if g >= 0 and c.gates[g].name == "fsim" else 0 for g in ref_net.leaf_gate], dtype=np.uint8)
+    seed = torch.ones(net.n_out, dtype=torch.complex128, device="cuda")
+    B = args.slices_per_step
+    mode = MODES[args.mode]
+    for i in range(args.warmup):
+        net.contract_backward(seed, (i * B) % net.n_slices, (i * B) % net.n_slices + B, mode, leaf_mask=mask)
+    torch.cuda.synchronize()
+    net.set_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(args.steps):
+        lo = ((args.warmup + i) * B) % net.n_slices
+        net.contract_backward(seed, lo, lo + B, mode, leaf_mask=mask)
+    ev1.record()
+    torch.cuda.synchronize()
+    T = ev0.elapsed_time(ev1) / 1e3
+    net.check_device()
+    recs, n_launches = net.last_timings()
+    net.set_timing(False)
+    by_kind = kernel_breakdown(recs)
+    cmacs = sum(v["cmacs"] for k, v in by_kind.items() if k in (0, 3))
+    stats = net.stats()
+    line = {"metric": "adjoint pass (forward + environments of all fSim leaves), effective complex TFLOPS",
+            "value": 8 * cmacs / T / 1e12, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * T / args.steps, "s_per_1024_slices": T / (args.steps * B) * 1024,
+            "forward_mode": args.mode,
+            "env_precision": "same arithmetic as the forward mode (split precision: FP32 accumulate)",
+            "config": {"workload": workload_name(), "slices_per_step": B, "n_slices": net.n_slices,
+                       "fsim_leaves": int(mask.sum())},
+            "kernel_time_ms": {KIND_NAMES.get(k, str(k)): v["ms"] for k, v in by_kind.items()},
+            "gpu_launches": n_launches, "backward_batch": stats.get("last_batch")}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,6 +358,8 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
+    ap.add_argument("--backward", action="store_true",
+                    help="time the adjoint pass (leaf environments of all fSim gates) instead")
     ap.add_argument("--single-node", default=None,
                     help="MB,NB,KB: time one isolated contraction node (log2 sizes) instead")
     ap.add_argument("--slices-per-step", type=int, default=2)
@@ -323,6 +373,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.single_node:
         return single_node(args)
+    if args.backward:
+        return backward_bench(args)
 
     import torch
     import torch.distributed as dist

@@ -186,6 +186,11 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  pipeline stage, also the shared-memory swizzle width
  *  "tc_group_m"    1..64 (default 1): output row tiles per rasterisation
  *                  group (consecutive CTAs sweep all column tiles of a group)
+ *  "tc_spin_limit" polls before a bounded device-side wait gives up (0 = the
+ *                  kernel default, 2^24)
+ *  "tc_test_stall" tests only: nonzero makes the tensor-core producer issue no
+ *                  loads, so the consumers' bounded waits run out and the
+ *                  contraction reports TNC_E_TIMEOUT through tnc_check_device
  * Errors: TNC_E_INVALID for an unknown key or value. */
 tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value);
 

@@ -86,6 +86,8 @@ struct TcGemmParams {
     int* err;        // device error word (4 = a bounded wait gave up)
     int row_bytes;   // 64 or 128: bytes of K per tile row and stage (swizzle width)
     int group_m;     // tile rasterisation: row tiles per group (1 = row-major)
+    uint32_t spin_limit;  // polls before a bounded wait gives up
+    int test_stall;       // tests only: the producer issues no loads, so waits run out
 };
 
 int tc_plane_count(int mode);

@@ -78,8 +78,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait; false if it gave up or another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          uint32_t limit = kSpinLimit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_try(bar, parity)) return true;
         if ((i & 255) == 255 && *abort_flag) return false;
     }
@@ -229,14 +230,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
     volatile int* abort_flag = &abort_sh;
+    const uint32_t spin = p.spin_limit ? p.spin_limit : kSpinLimit;
 
     if (warp == PRODUCER_WARP && lane == 0) {
         // ---------------- TMA producer: stages in (chunk, product, k-block) order
         int issued = 0;
-        for (int it = 0; it < n_it; ++it) {
+        for (int it = 0; it < n_it && !p.test_stall; ++it) {
             const int s = it % C_::STAGES;
             const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag)) {
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag, spin)) {
                 abort_sh = 1;
                 atomicExch(p.err, kErrTimeout);
                 break;
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int it = first; it < issued; ++it) {
                 const int s = it % C_::STAGES;
                 const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-                for (uint32_t i = 0; i < kSpinLimit && !mbar_try(smem_u32(&full_bar[s]), ph); ++i) {
+                for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&full_bar[s]), ph); ++i) {
                 }
             }
         }
@@ -270,12 +272,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int c = it / (3 * kpc), r = it % (3 * kpc);
             const int t = r / kpc, kbi = r % kpc;
             if (kbi == 0 && c > 0 &&
-                !mbar_wait(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag)) {
+                !mbar_wait(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag, spin)) {
                 abort_sh = 1;
                 atomicExch(p.err, kErrTimeout);
                 break;
             }
-            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag)) {
+            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin)) {
                 abort_sh = 1;
                 atomicExch(p.err, kErrTimeout);
                 break;
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (*abort_flag && any) {
             mma_commit(smem_u32(&drain_bar));
-            for (uint32_t i = 0; i < kSpinLimit && !mbar_try(smem_u32(&drain_bar), 0); ++i) {
+            for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&drain_bar), 0); ++i) {
             }
         }
     } else if (warp < EPI_WARPS) {
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 int w = 0;
-                if (lane == 0) w = mbar_wait(smem_u32(&tfull[t]), (uint32_t)c & 1u, abort_flag) ? 1 : 0;
+                if (lane == 0) w = mbar_wait(smem_u32(&tfull[t]), (uint32_t)c & 1u, abort_flag, spin) ? 1 : 0;
                 w = __shfl_sync(0xffffffffu, w, 0);
                 if (!w) {
                     ok = false;

@@ -149,6 +149,8 @@ struct tnc_net {
     // tensor-core tile options (tnc_set_option)
     int tc_row_bytes = 128;
     int tc_group_m = 1;
+    uint32_t tc_spin_limit = 0;  // 0 = kernel default
+    int tc_test_stall = 0;
     // cached level groups and their device parameter table
     std::string group_key;
     GroupPlan groups;
@@ -555,6 +557,50 @@ tnc_status ensure_groups(tnc_net* net, const Arena& ar, char* ws, int mode, int6
 tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, int b, int64_t slice0, int mode,
                      cudaStream_t s);
 
+// Split + tensor-core GEMM for the contraction described by g (operands,
+// per-bit strides, output); planes are workspace temporaries of the sizes
+// planes_bytes() gives for (mb, kb) and (nb, kb).
+tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, int mode, void* pa, void* pb,
+                                 int node, cudaStream_t s) {
+    tnc::SplitParams sp{};
+    sp.src = g.A;
+    sp.rb = g.mb;
+    sp.kb = g.kb;
+    for (int j = 0; j < g.mb; ++j) sp.rs[j] = g.am[j];
+    for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.ak[j];
+    sp.slice0 = g.slice0;
+    sp.dst = pa;
+    CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
+    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
+    CUDA_TRY(timed_end(net, s));
+    sp = tnc::SplitParams{};
+    sp.src = g.B;
+    sp.rb = g.nb;
+    sp.kb = g.kb;
+    for (int j = 0; j < g.nb; ++j) sp.rs[j] = g.bn[j];
+    for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.bk[j];
+    sp.slice0 = g.slice0;
+    sp.dst = pb;
+    CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
+    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
+    CUDA_TRY(timed_end(net, s));
+    tnc::TcGemmParams tp{};
+    tp.mb = g.mb;
+    tp.nb = g.nb;
+    tp.kb = g.kb;
+    tp.C = g.C;
+    tp.c_batch_stride = g.c_batch_stride;
+    tp.err = net->d_err;
+    tp.row_bytes = net->tc_row_bytes;
+    tp.group_m = net->tc_group_m;
+    tp.spin_limit = net->tc_spin_limit;
+    tp.test_stall = net->tc_test_stall;
+    CUDA_TRY(timed_begin(net, node, K_TC, b, s, std::ldexp(1.0, g.mb + g.nb + g.kb) * b));
+    CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
+    CUDA_TRY(timed_end(net, s));
+    return TNC_OK;
+}
+
 // One non-root contraction: FP32 CUDA-core GEMM, or (split modes, large
 // nodes) operand split + tensor-core GEMM. `g` carries operands and output.
 tnc_status launch_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, const tnc::GemmParams& g,
@@ -566,43 +612,7 @@ tnc_status launch_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& 
         return TNC_OK;
     }
     const size_t i = np.v - net->n_leaves;
-    void* pa = ws + ar.planes_a[i];
-    void* pb = ws + ar.planes_b[i];
-    tnc::SplitParams sp{};
-    sp.src = g.A;
-    sp.rb = np.mb;
-    sp.kb = np.kb;
-    for (int j = 0; j < np.mb; ++j) sp.rs[j] = np.am[j];
-    for (int j = 0; j < np.kb; ++j) sp.ks[j] = np.ak[j];
-    sp.slice0 = g.slice0;
-    sp.dst = pa;
-    CUDA_TRY(timed_begin(net, np.v, K_SPLIT, b, s));
-    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
-    CUDA_TRY(timed_end(net, s));
-    sp = tnc::SplitParams{};
-    sp.src = g.B;
-    sp.rb = np.nb;
-    sp.kb = np.kb;
-    for (int j = 0; j < np.nb; ++j) sp.rs[j] = np.bn[j];
-    for (int j = 0; j < np.kb; ++j) sp.ks[j] = np.bk[j];
-    sp.slice0 = g.slice0;
-    sp.dst = pb;
-    CUDA_TRY(timed_begin(net, np.v, K_SPLIT, b, s));
-    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
-    CUDA_TRY(timed_end(net, s));
-    tnc::TcGemmParams tp{};
-    tp.mb = np.mb;
-    tp.nb = np.nb;
-    tp.kb = np.kb;
-    tp.C = g.C;
-    tp.c_batch_stride = g.c_batch_stride;
-    tp.err = net->d_err;
-    tp.row_bytes = net->tc_row_bytes;
-    tp.group_m = net->tc_group_m;
-    CUDA_TRY(timed_begin(net, np.v, K_TC, b, s));
-    CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
-    CUDA_TRY(timed_end(net, s));
-    return TNC_OK;
+    return launch_tc_contraction(net, g, b, mode, ws + ar.planes_a[i], ws + ar.planes_b[i], np.v, s);
 }
 
 tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, int b, int64_t slice0, int mode,
@@ -689,7 +699,21 @@ tnc_status env_child(Backward& bw, const NodePlan& np, int c, int64_t b, int64_t
     const int64_t bb = per ? b : b;  // per-slice environments of every child, batch b
     int64_t off = bw.A.alloc(bb * elems * 8);
     bw.env_off[c] = off;
-    if (!bw.exec) return TNC_OK;
+    // GEMM dims of this environment: E_A is (mb, kb) over nb; E_B is (kb, nb) over mb
+    const int gmb = is_a ? np.mb : np.kb, gnb = is_a ? np.kb : np.nb, gkb = is_a ? np.nb : np.mb;
+    const bool tc = tc_node(bw.mode, gmb, gnb, gkb, false);
+    int64_t pa = -1, pb = -1;
+    if (tc) {  // split-precision planes (allocated in the sizing pass too)
+        pa = bw.A.alloc(planes_bytes(bw.mode, gmb, gkb, b));
+        pb = bw.A.alloc(planes_bytes(bw.mode, gnb, gkb, b));
+    }
+    if (!bw.exec) {
+        if (tc) {
+            bw.A.release(pa);
+            bw.A.release(pb);
+        }
+        return TNC_OK;
+    }
     tnc::GemmParams g{};
     const std::vector<int>& ev = bw.env_layout[np.v];
     tnc::Operand E{};
@@ -726,6 +750,13 @@ tnc_status env_child(Backward& bw, const NodePlan& np, int c, int64_t b, int64_t
     g.C = reinterpret_cast<float2*>(bw.ws + off);
     g.c_batch_stride = elems;
     g.slice0 = slice0;
+    if (tc) {
+        // split precision with FP32 accumulation, as in the forward
+        tnc_status st = launch_tc_contraction(net, g, (int)b, bw.mode, bw.ws + pa, bw.ws + pb, np.v, bw.s);
+        bw.A.release(pa);
+        bw.A.release(pb);
+        return st;
+    }
     CUDA_TRY(timed_begin(net, np.v, K_GEMM_F32, (int)b, bw.s, std::ldexp(1.0, g.mb + g.nb + g.kb) * b));
     CUDA_TRY(tnc::launch_gemm_f32(g, (int)b, bw.s));
     CUDA_TRY(timed_end(net, bw.s));
@@ -1196,6 +1227,11 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "tc_group_m") {
         if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");
         net->tc_group_m = (int)value;
+    } else if (k == "tc_spin_limit") {
+        if (value < 0 || value > 0xFFFFFFFFll) return fail(TNC_E_INVALID, "tc_spin_limit out of range");
+        net->tc_spin_limit = (uint32_t)value;
+    } else if (k == "tc_test_stall") {
+        net->tc_test_stall = value != 0;
     } else {
         return fail(TNC_E_INVALID, "unknown option " + k);
     }

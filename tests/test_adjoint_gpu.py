@@ -135,3 +135,25 @@ def test_backward_budget_too_small(lib):
     with pytest.raises(TNCError) as e:
         amp.net.contract_backward(torch.ones(1, dtype=torch.complex128), 0, 16, 0, budget_bytes=1024)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("mode", [2, 1])
+def test_tensor_core_environments(lib, mode):
+    """Environment contractions large enough for the tensor cores: split
+    precision must agree with the FP32 environments, and F is linear in every
+    leaf, so sum_i L[i] dF/dL[i] = F (the forward result) for each leaf."""
+    from paper_2205_00393_gb300 import Network
+    from .test_parity_tc_gpu import _three_leaf
+    net_ref = _three_leaf(11, 8, 8, 7, True)
+    net = Network.from_tn(net_ref)
+    net.set_path([(0, 1), (2, 3)])
+    n_out = net.n_out
+    rng = np.random.default_rng(3)
+    seed = torch.from_numpy(rng.standard_normal(n_out) + 1j * rng.standard_normal(n_out))
+    F = complex(np.dot(seed.numpy(), net.contract(0, 1, 0).cpu().numpy()))
+    e32 = _unpack(net, net.contract_backward(seed, 0, 1, 0))
+    etc = _unpack(net, net.contract_backward(seed, 0, 1, mode))
+    net.check_device()
+    for (a, b, L) in zip(etc, e32, net_ref.tensors):
+        assert _rel(a, b) <= 1e-4
+        assert abs(np.sum(np.asarray(L).reshape(-1).astype(np.complex128) * a) - F) <= 1e-4 * abs(F)
