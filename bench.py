@@ -66,23 +66,24 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def kernel_traffic(kind_name):
-    """DRAM bytes per launch from the committed ncu summary, valid only while
-    the kernel source is unchanged (hash recorded beside the figure)."""
+def kernel_traffic(kind_name, mode, cmacs_per_launch):
+    """DRAM bytes per launch from the committed ncu capture, scaled by the
+    launch's complex multiply-accumulates; valid only for the captured mode and
+    while the kernel source is unchanged (hash recorded beside the figure)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(kind_name)
     except (OSError, ValueError):
         return None
-    if not rec:
+    if not rec or rec.get("mode") != mode:
         return None
     src = os.path.join(ROOT, rec["source"])
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return rec["bytes_per_unit"] if h == rec["source_sha"] else None
+    return rec["bytes_per_cmac"] * cmacs_per_launch if h == rec["source_sha"] else None
 
 
 class ClockSampler:
@@ -189,7 +190,8 @@ def roofline_of(by_kind, mode, peaks, peak_src, sustained):
              "frac": achieved / FP32_PEAK_TFLOPS,
              "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
              "algorithmic_flops": "8*M*N*K FP32 flops per node (4 real FMAs per complex MAC)"}
-    r.update({"traffic": kernel_traffic(KIND_NAMES[dom]), "kernel": KIND_NAMES[dom],
+    r.update({"traffic": kernel_traffic(KIND_NAMES[dom], mode, d["cmacs"] / max(d["launches"], 1)),
+              "kernel": KIND_NAMES[dom],
               "launches": d["launches"], "share_of_timed_kernel_time": share})
     return r
 
