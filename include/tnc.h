@@ -177,6 +177,20 @@ tnc_status tnc_param_grads(tnc_net_t net, int n_params, const int* leaf_ids, con
  * returned; the result is invalid but the context stays usable). */
 tnc_status tnc_check_device(tnc_net_t net, void* stream);
 
+/* Contract n networks together (many circuits of uneven size): network i over
+ * slices [slice_lo[i], slice_hi[i]) into outs_c128[i] (device, overwritten),
+ * with the same result as n tnc_contract calls. The level groups of all
+ * networks share launches (level L of every network in one grouped launch)
+ * and the final reductions of all networks share two launches per round of
+ * slice batches; tensor-core nodes keep their own launches. With use_graph
+ * != 0 and a non-default stream, the launch sequence is captured once into a
+ * CUDA graph and replayed by later calls with identical arguments (networks,
+ * ranges, outputs, workspaces and plans; leaf data may change between calls).
+ * Every network needs at most 64 outputs and at least two tensors. A network
+ * may appear once. Destroying a network drops the cached sequences using it. */
+tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_lo, const int64_t* slice_hi,
+                             int mode, double* const* outs_c128, int use_graph, void* stream);
+
 /* JSON statistics of the current plan: Eq. 1 cost, Eq. 3 cost, Eq. 2
  * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace. */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);

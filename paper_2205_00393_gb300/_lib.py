@@ -64,6 +64,8 @@ def load_library():
         "tnc_set_option": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64],
         "tnc_contract_backward": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
+        "tnc_contract_many": [ctypes.c_int, P(ctypes.c_void_p), c_i64p, c_i64p, ctypes.c_int,
+                              P(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p],
         "tnc_param_grads": [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p, ctypes.c_void_p],
         "tnc_last_timings": [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
@@ -93,6 +95,27 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def contract_many(networks, ranges=None, mode=FP32, outs=None, use_graph=True, stream=None):
+    """Contract several networks together (tnc_contract_many): shared grouped
+    launches across networks, replayed through a CUDA graph on repeat calls.
+    Returns one complex128 CUDA tensor per network."""
+    import torch
+    lib = load_library()
+    n = len(networks)
+    if ranges is None:
+        ranges = [(0, net.n_slices) for net in networks]
+    if outs is None:
+        outs = [torch.empty(net.n_out, dtype=torch.complex128, device="cuda") for net in networks]
+    hs = (ctypes.c_void_p * n)(*[net._h.value for net in networks])
+    lo = (ctypes.c_int64 * n)(*[int(r[0]) for r in ranges])
+    hi = (ctypes.c_int64 * n)(*[int(r[1]) for r in ranges])
+    op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib, lib.tnc_contract_many(n, hs, lo, hi, int(mode), op, 1 if use_graph else 0, _stream_ptr(stream)))
+    return outs
 
 
 class Network:

@@ -138,6 +138,15 @@ int64_t gemm_f32_tiles(int mb, int nb);
 cudaError_t launch_gemm_f32_group(const GemmParams* d_params, const int64_t* d_tile_off, int n,
                                   int64_t total_tiles, int64_t slice0, int batch, cudaStream_t s);
 cudaError_t launch_root_partials(const RootParams& p, int batch, double2* partials, cudaStream_t s);
+// Several networks per launch: node i of a grouped launch belongs to network
+// net[i]; rs0[w] / rb[w] are network w's first slice and batch of the round.
+cudaError_t launch_gemm_f32_group_multi(const GemmParams* d_params, const int64_t* d_tile_off, int n,
+                                        int64_t total_tiles, const int* d_net, const int64_t* d_rs0,
+                                        const int* d_rb, int max_batch, cudaStream_t s);
+// Final reductions of n networks (FP64 partials, then ordered sums into outs).
+cudaError_t launch_root_multi(const RootParams* d_roots, double2* const* d_partials, const int64_t* d_blk_off,
+                              int n, int64_t total_blocks, const PermParams* d_perms, double2* const* d_outs,
+                              const int64_t* d_rs0, const int* d_rb, int max_batch, cudaStream_t s);
 cudaError_t launch_accumulate_partials(const double2* partials, int count, const PermParams& pp,
                                        double2* out, cudaStream_t s);
 cudaError_t launch_slice_sum_f32(const SumParams& p, int batch, double2* out, cudaStream_t s);

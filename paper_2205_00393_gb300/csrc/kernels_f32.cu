@@ -290,6 +290,98 @@ cudaError_t launch_gemm_f32(const GemmParams& p, int batch, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Grouped contractions of several networks: node i belongs to network
+// net[i]; slice z of the launch maps to slice rs0[net] + z of that network and
+// exists only for z < rb[net] (networks batch different numbers of slices).
+__global__ void __launch_bounds__(NT) k_gemm_f32_group_multi(const GemmParams* __restrict__ params,
+                                                             const int64_t* __restrict__ tile_off, int n,
+                                                             const int* __restrict__ net,
+                                                             const int64_t* __restrict__ rs0,
+                                                             const int* __restrict__ rb) {
+    __shared__ __align__(16) GemmSmem sm;
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int w = net[lo];
+    if ((int)blockIdx.z >= rb[w]) return;
+    gemm_tile(params[lo], b - tile_off[lo], blockIdx.z, rs0[w], sm);
+}
+
+// Root reductions of several networks in one launch: block x serves chunk
+// x - blk_off[i] of network i; partial sums go to that network's buffer.
+__global__ void __launch_bounds__(256) k_root_partials_multi(const RootParams* __restrict__ roots,
+                                                             double2* const* __restrict__ partials,
+                                                             const int64_t* __restrict__ blk_off, int n,
+                                                             const int64_t* __restrict__ rs0,
+                                                             const int* __restrict__ rb) {
+    __shared__ double2 red[256];
+    const int64_t x = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (blk_off[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    const int z = blockIdx.z;
+    if (z >= rb[lo]) return;
+    const RootParams& rp = roots[lo];
+    const GemmParams& p = rp.g;
+    const int chunk = (int)(x - blk_off[lo]);
+    const int R = 1 << (p.mb + p.nb);
+    const int lanes = 256 / R;
+    const int r = threadIdx.x / lanes, lane = threadIdx.x % lanes;
+    const int64_t m = r >> p.nb, nn = r & ((1 << p.nb) - 1);
+    const int64_t s = rs0[lo] + z;
+    const float2* A = p.A.ptr + z * p.A.batch_stride + slice_offset(p.A, s) + bits_offset(m, p.am, p.mb, 0);
+    const float2* B = p.B.ptr + z * p.B.batch_stride + slice_offset(p.B, s) + bits_offset(nn, p.bn, p.nb, 0);
+    const int64_t K = 1ll << p.kb;
+    const int64_t kc = K / rp.chunks;
+    const int64_t k_lo = chunk * kc, k_hi = k_lo + kc;
+    double re = 0.0, im = 0.0;
+    for (int64_t k = k_lo + lane; k < k_hi; k += lanes) {
+        float2 a = A[bits_offset(k, p.ak, p.kb, 0)];
+        float2 bb = B[bits_offset(k, p.bk, p.kb, 0)];
+        re += (double)a.x * bb.x - (double)a.y * bb.y;
+        im += (double)a.x * bb.y + (double)a.y * bb.x;
+    }
+    red[threadIdx.x] = make_double2(re, im);
+    __syncthreads();
+    for (int st = lanes / 2; st > 0; st >>= 1) {
+        if (lane < st) {
+            double2 o = red[threadIdx.x + st];
+            red[threadIdx.x].x += o.x;
+            red[threadIdx.x].y += o.y;
+        }
+        __syncthreads();
+    }
+    if (lane == 0) partials[lo][((int64_t)z * rp.chunks + chunk) * R + r] = red[threadIdx.x];
+}
+
+// out_i[r] += sum over network i's partial sums (slices in order, then chunks).
+__global__ void k_accumulate_multi(const RootParams* __restrict__ roots, double2* const* __restrict__ partials,
+                                   const PermParams* __restrict__ perms, double2* const* __restrict__ outs,
+                                   const int* __restrict__ rb) {
+    const int i = blockIdx.x;
+    const PermParams& pp = perms[i];
+    const int64_t R = 1ll << pp.obits;
+    const int count = rb[i] * roots[i].chunks;
+    for (int64_t r = threadIdx.x; r < R; r += blockDim.x) {
+        const int64_t src = bits_offset(r, pp.ostride, pp.obits, 0);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = 0; c < count; ++c) {
+            double2 v = partials[i][(int64_t)c * R + src];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        outs[i][r].x += acc.x;
+        outs[i][r].y += acc.y;
+    }
+}
+
 int64_t gemm_f32_tiles(int mb, int nb) {
     int64_t M = 1ll << mb, N = 1ll << nb;
     return ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
@@ -300,6 +392,29 @@ cudaError_t launch_gemm_f32_group(const GemmParams* d_params, const int64_t* d_t
     if (n < 1 || total_tiles < 1 || total_tiles > 0x7fffffffll || batch < 1 || batch > 65535)
         return cudaErrorInvalidConfiguration;
     k_gemm_f32_group<<<dim3((unsigned)total_tiles, 1, batch), NT, 0, s>>>(d_params, d_tile_off, n, slice0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f32_group_multi(const GemmParams* d_params, const int64_t* d_tile_off, int n,
+                                        int64_t total_tiles, const int* d_net, const int64_t* d_rs0,
+                                        const int* d_rb, int max_batch, cudaStream_t s) {
+    if (n < 1 || total_tiles < 1 || total_tiles > 0x7fffffffll || max_batch < 1 || max_batch > 65535)
+        return cudaErrorInvalidConfiguration;
+    k_gemm_f32_group_multi<<<dim3((unsigned)total_tiles, 1, max_batch), NT, 0, s>>>(d_params, d_tile_off, n,
+                                                                                     d_net, d_rs0, d_rb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_root_multi(const RootParams* d_roots, double2* const* d_partials, const int64_t* d_blk_off,
+                              int n, int64_t total_blocks, const PermParams* d_perms, double2* const* d_outs,
+                              const int64_t* d_rs0, const int* d_rb, int max_batch, cudaStream_t s) {
+    if (n < 1 || total_blocks < 1 || total_blocks > 0x7fffffffll || max_batch < 1 || max_batch > 65535)
+        return cudaErrorInvalidConfiguration;
+    k_root_partials_multi<<<dim3((unsigned)total_blocks, 1, max_batch), 256, 0, s>>>(d_roots, d_partials, d_blk_off,
+                                                                                   n, d_rs0, d_rb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_accumulate_multi<<<n, 256, 0, s>>>(d_roots, d_partials, d_perms, d_outs, d_rb);
     return cudaGetLastError();
 }
 

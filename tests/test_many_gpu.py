@@ -1,0 +1,67 @@
+"""tnc_contract_many: several circuits of uneven size in shared launches and
+a replayed CUDA graph must give the same amplitudes as separate contractions
+and as the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+from tnc_inputs import circuit_to_network, grid_rqc
+from oracle import planner, tn
+
+from ._util import floored_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _circuits():
+    specs = [(3, 4, 8, 1, 0, 8), (2, 4, 6, 2, 2, 6), (3, 3, 7, 3, 1, 7), (4, 5, 10, 4, 3, 15),
+             (2, 3, 5, 5, 0, None), (3, 5, 9, 6, 6, 11)]
+    out = []
+    from paper_2205_00393_gb300 import Network
+    for (r, c, cyc, seed, n_open, t) in specs:
+        circ = grid_rqc(r, c, cyc, seed, n_open=n_open)
+        ref = circuit_to_network(circ).as_complex64()
+        net = Network.from_tn(ref)
+        path = net.greedy_path()
+        net.set_path(path)
+        S = net.find_slices(t, 7) if t is not None else []
+        net.set_slices(S)
+        out.append((circ, ref, net, path, S))
+    return out
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_many_matches_single_and_oracle(libtnc, mode):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_00393_gb300 import contract_many
+    cs = _circuits()
+    nets = [c[2] for c in cs]
+    ranges = [(0, n.n_slices) for n in nets]
+    ranges[3] = (1, nets[3].n_slices - 1)  # a partial range
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        outs = [torch.empty(n.n_out, dtype=torch.complex128, device="cuda") for n in nets]
+        for call in range(3):  # eager, capture + replay, replay
+            for o in outs:
+                o.fill_(float("nan"))
+            contract_many(nets, ranges, mode, outs=outs, stream=stream)
+            stream.synchronize()
+            for (circ, ref, net, path, S), (lo, hi), o in zip(cs, ranges, outs):
+                single = net.contract(lo, hi, mode, stream=stream).cpu().numpy()
+                stream.synchronize()
+                got = o.cpu().numpy()
+                assert np.allclose(got, single, rtol=1e-9, atol=1e-15), call
+                if call == 0:
+                    want = tn.contract(ref, path, S, range(lo, hi))
+                    assert floored_rel_err(got, want, circ.n_qubits) <= 1e-5
+
+
+def test_many_rejects_duplicates(libtnc):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_00393_gb300 import contract_many, TNCError
+    cs = _circuits()
+    with pytest.raises(TNCError):
+        contract_many([cs[0][2], cs[0][2]])
