@@ -302,6 +302,83 @@ def single_node(args):
     return 0
 
 
+def batched_circuits(n=256, seed0=1000, t_cap=24, cost_cap=2 ** 32):
+    """Plan the batched uneven workload (tnc_inputs.circuits.batched_workload):
+    target t = min(W - k, t_cap) for a greedy tree of width W. Circuits whose
+    slices cost more than cost_cap complex MACs are left out (returned
+    separately)."""
+    from tnc_inputs import circuit_to_network
+    from tnc_inputs.circuits import batched_workload
+    from paper_2205_00393_gb300 import Network
+    kept, dropped = [], []
+    for i, (circ, k) in enumerate(batched_workload(n, seed0)):
+        tn_ = circuit_to_network(circ).as_complex64()
+        net = Network.from_tn(tn_)
+        net.set_path(net.greedy_path())
+        W = net.stats()["max_log2_size"]
+        n_open = len(circ.open_qubits)
+        t = max(min(W - k, t_cap), n_open + 4)
+        net.set_slices(net.find_slices(t, 7))
+        st = net.stats()
+        per_slice = int(st["eq3"]) >> len(net.sliced)
+        entry = dict(index=i, qubits=circ.n_qubits, cycles=circ.cycles, n_open=n_open, t=t,
+                     slices=net.n_slices, per_slice_cmacs=per_slice, net=net, tn=tn_, circuit=circ)
+        (kept if per_slice <= cost_cap else dropped).append(entry)
+    return kept, dropped
+
+
+def many_bench(args):
+    """Batched uneven workload: every kept circuit contributes its first
+    --slices-per-step slices to each step. Times separate tnc_contract calls,
+    one tnc_contract_many launch sequence without a graph, and its graph replay."""
+    import torch
+    from paper_2205_00393_gb300 import contract_many
+    torch.cuda.set_device(0)
+    kept, dropped = batched_circuits()
+    mode = MODES[args.mode]
+    nets = [e["net"] for e in kept]
+    ranges = [(0, min(e["slices"], args.slices_per_step)) for e in kept]
+    cmacs = sum(e["per_slice_cmacs"] * (hi - lo) for e, (lo, hi) in zip(kept, ranges))
+    n_sl = sum(hi - lo for lo, hi in ranges)
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        outs = [torch.empty(n.n_out, dtype=torch.complex128, device="cuda") for n in nets]
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            stream.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            ev1.record(stream)
+            stream.synchronize()
+            return ev0.elapsed_time(ev1) / 1e3 / args.steps
+
+        def separate():
+            for net, (lo, hi), o in zip(nets, ranges, outs):
+                net.contract(lo, hi, mode, out=o, stream=stream)
+        res["separate"] = timed(separate)
+        res["many_no_graph"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs, use_graph=False,
+                                                           stream=stream))
+        res["many_graph"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs, use_graph=True,
+                                                        stream=stream))
+    T = res["many_graph"]
+    line = {"metric": "batched uneven circuits: effective complex TFLOPS & s/1024 slices (graph replay)",
+            "value": 8 * cmacs / T / 1e12, "unit": UNIT, "s_per_1024_slices": T / n_sl * 1024,
+            "ms_per_step": {k: 1e3 * v for k, v in res.items()},
+            "speedup_vs_separate_calls": res["separate"] / T, "mode": args.mode, "steps": args.steps,
+            "warmup": args.warmup,
+            "config": {"workload": "256 seeded grid circuits (seeds 1000..1255), qubits 20-36, cycles 10-16, "
+                                   "open 0-6, slicing depth 4-12, target t <= 24",
+                       "circuits_run": len(kept), "circuits_left_out_over_2^32_cmacs_per_slice": len(dropped),
+                       "slices_per_step": n_sl, "slices_per_circuit_max": args.slices_per_step}}
+    print(json.dumps(line))
+    return 0
+
+
 def backward_bench(args):
     """Forward + adjoint pass over a batch of slices per step: environments of
     every fSim leaf for F = sum of the 64 amplitudes (FP32 environment
@@ -360,6 +437,8 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
+    ap.add_argument("--many", action="store_true",
+                    help="time the batched uneven workload of many circuits instead")
     ap.add_argument("--backward", action="store_true",
                     help="time the adjoint pass (leaf environments of all fSim gates) instead")
     ap.add_argument("--single-node", default=None,
@@ -377,6 +456,8 @@ def main():
         return single_node(args)
     if args.backward:
         return backward_bench(args)
+    if args.many:
+        return many_bench(args)
 
     import torch
     import torch.distributed as dist

@@ -65,3 +65,30 @@ def test_many_rejects_duplicates(libtnc):
     cs = _circuits()
     with pytest.raises(TNCError):
         contract_many([cs[0][2], cs[0][2]])
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_batched_uneven_workload_subset(libtnc, mode):
+    """First 48 circuits of the seeded batched workload (those whose slices
+    cost at most 2^32 complex MACs), two slices each: the merged launches with
+    graph replay equal separate contractions."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from bench import batched_circuits
+    from paper_2205_00393_gb300 import contract_many
+    kept, dropped = batched_circuits(n=48)
+    assert len(kept) >= 20
+    nets = [e["net"] for e in kept]
+    ranges = [(0, min(2, e["slices"])) for e in kept]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        outs = [torch.empty(n.n_out, dtype=torch.complex128, device="cuda") for n in nets]
+        for call in range(3):
+            contract_many(nets, ranges, mode, outs=outs, stream=stream)
+        stream.synchronize()
+        for net, (lo, hi), o in zip(nets, ranges, outs):
+            single = net.contract(lo, hi, mode, stream=stream).cpu().numpy()
+            assert np.allclose(o.cpu().numpy(), single, rtol=1e-9, atol=1e-15)

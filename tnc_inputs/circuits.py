@@ -104,3 +104,24 @@ def with_fsim_params(circuit, params):
             out.append(g)
     return Circuit(circuit.n_qubits, out, circuit.bitstring.copy(), circuit.open_qubits,
                    list(circuit.sites), circuit.cycles)
+
+
+def batched_workload(n=256, seed0=1000):
+    """The batched uneven workload: n seeded grid circuits with qubits
+    U{20..36} (near-square grids, surplus sites removed from the last row),
+    cycles U{10..16}, open qubits U{0..6} and a slicing depth k U{4..12}, drawn
+    from default_rng(seed0) in that order per circuit; circuit i uses seed
+    seed0 + i. Returns a list of (circuit, k)."""
+    import math
+    rng = np.random.default_rng(seed0)
+    out = []
+    for i in range(n):
+        nq = int(rng.integers(20, 37))
+        cyc = int(rng.integers(10, 17))
+        n_open = int(rng.integers(0, 7))
+        k = int(rng.integers(4, 13))
+        r = int(math.floor(math.sqrt(nq)))
+        c = int(math.ceil(nq / r))
+        removed = [(r - 1, cc) for cc in range(c - (r * c - nq), c)]
+        out.append((grid_rqc(r, c, cyc, seed0 + i, n_open=n_open, removed=removed), k))
+    return out
