@@ -200,6 +200,11 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  pipeline stage, also the shared-memory swizzle width
  *  "tc_group_m"    1..64 (default 1): output row tiles per rasterisation
  *                  group (consecutive CTAs sweep all column tiles of a group)
+ *  "backward_keep_every" 0 (default) or 1..64: the adjoint pass keeps the
+ *                  per-slice intermediates of every k-th dependency level (and
+ *                  the root's inputs) and recomputes the others from them in
+ *                  the reverse walk; 0 picks the smallest k whose workspace
+ *                  fits the budget
  *  "tc_spin_limit" polls before a bounded device-side wait gives up (0 = the
  *                  kernel default, 2^24)
  *  "tc_test_stall" tests only: nonzero makes the tensor-core producer issue no

@@ -147,10 +147,13 @@ struct tnc_net {
     void* ws_own = nullptr;
     size_t ws_own_bytes = 0;
     int64_t last_batch = 0;
+    int last_keep_every = 1;        // checkpoint spacing of the last backward pass
+    size_t last_backward_bytes = 0;
     // tensor-core tile options (tnc_set_option)
     int tc_row_bytes = 128;
     int tc_group_m = 1;
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
+    int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int tc_test_stall = 0;
     // cached level groups and their device parameter table
     std::string group_key;
@@ -671,6 +674,10 @@ struct Backward {
     std::vector<int64_t> env_off;                  // per tensor (current env buffer)
     std::vector<int64_t> inv_acc;                  // per invariant tensor: FP64 env accumulator
     int64_t leaf_grad = -1;                        // FP64 gradients of all leaves, packed
+    // per-level checkpointing of per-slice intermediates
+    int keep_every = 1;                            // keep tensors at levels divisible by this
+    std::vector<char> keep, present;               // per tensor
+    int64_t recomputed = 0;                        // nodes recomputed in the reverse walk
 };
 
 int64_t layout_stride(const std::vector<int>& layout, int mode) {
@@ -804,6 +811,28 @@ tnc_status env_fold(Backward& bw, int c, int64_t b, int64_t slice0, bool from_pe
     return TNC_OK;
 }
 
+tnc_status fwd_node(Backward& bw, const NodePlan& np, int64_t b, int64_t slice0);
+
+// Make the value of per-slice tensor v available, recomputing it (and, as
+// needed, its own per-slice inputs) from the nearest kept tensors.
+tnc_status materialize(Backward& bw, int v, int64_t b, int64_t slice0) {
+    tnc_net* net = bw.net;
+    if (v < net->n_leaves || !net->plan.per_slice[v] || bw.present[v]) return TNC_OK;
+    const NodePlan& np = net->plan.nodes[v - net->n_leaves];
+    tnc_status st;
+    for (int c : {np.A, np.B})
+        if ((st = materialize(bw, c, b, slice0)) != TNC_OK) return st;
+    if ((st = fwd_node(bw, np, b, slice0)) != TNC_OK) return st;
+    bw.present[v] = 1;
+    bw.recomputed += 1;
+    for (int c : {np.A, np.B})
+        if (c >= net->n_leaves && net->plan.per_slice[c] && !bw.keep[c]) {
+            bw.A.release(bw.fwd.off[c]);
+            bw.present[c] = 0;
+        }
+    return TNC_OK;
+}
+
 // Reverse walk over the nodes of one class (per-slice or invariant).
 tnc_status reverse_walk(Backward& bw, bool per_slice, int64_t b, int64_t slice0) {
     tnc_net* net = bw.net;
@@ -814,12 +843,22 @@ tnc_status reverse_walk(Backward& bw, bool per_slice, int64_t b, int64_t slice0)
         const bool node_per = np.per_slice;
         if (node_per != per_slice) continue;
         if (!bw.needs[np.v]) continue;
+        if (per_slice) {  // siblings feed the environment contractions
+            if (bw.needs[np.A] && (st = materialize(bw, np.B, b, slice0)) != TNC_OK) return st;
+            if (bw.needs[np.B] && (st = materialize(bw, np.A, b, slice0)) != TNC_OK) return st;
+        }
         for (int c : {np.A, np.B}) {
             if (!bw.needs[c]) continue;
             if ((st = env_child(bw, np, c, b, slice0)) != TNC_OK) return st;
             if ((st = env_fold(bw, c, b, slice0, per_slice)) != TNC_OK) return st;
         }
         bw.A.release(bw.env_off[np.v]);
+        if (per_slice)  // the children's values are not needed again
+            for (int c : {np.A, np.B})
+                if (c >= net->n_leaves && P.per_slice[c] && bw.present[c]) {
+                    bw.A.release(bw.fwd.off[c]);
+                    bw.present[c] = 0;
+                }
     }
     return TNC_OK;
 }
@@ -863,6 +902,22 @@ tnc_status backward_run(Backward& bw, int64_t lo, int64_t hi, const double* grad
     bw.env_layout.assign(T.n_tensors(), {});
     bw.env_off.assign(T.n_tensors(), -1);
     bw.inv_acc.assign(T.n_tensors(), -1);
+    // checkpoint levels: per-slice dependency depth; the root's inputs are kept
+    bw.keep.assign(T.n_tensors(), 0);
+    bw.present.assign(T.n_tensors(), 0);
+    {
+        std::vector<int> level(T.n_tensors(), 0);
+        for (const NodePlan& np : P.nodes) {
+            if (!np.per_slice || np.is_root) continue;
+            int l = 0;
+            for (int c : {np.A, np.B})
+                if (c >= net->n_leaves && P.per_slice[c]) l = std::max(l, level[c]);
+            level[np.v] = l + 1;
+            bw.keep[np.v] = (level[np.v] % std::max(1, bw.keep_every)) == 0;
+        }
+        if (!P.nodes.empty())
+            for (int c : {P.nodes.back().A, P.nodes.back().B}) bw.keep[c] = 1;
+    }
     bw.leaf_grad = bw.A.alloc(net->total_leaf_elems * 16);
     if (bw.exec) CUDA_TRY(cudaMemsetAsync(bw.ws + bw.leaf_grad, 0, net->total_leaf_elems * 16, bw.s));
     // invariant forward, kept for the whole call
@@ -882,10 +937,19 @@ tnc_status backward_run(Backward& bw, int64_t lo, int64_t hi, const double* grad
     for (int64_t s0 = lo; s0 < hi; s0 += bw.nb) {
         const int64_t b = std::min<int64_t>(bw.nb, hi - s0);
         FitAlloc saved = bw.A;
-        // per-slice forward (every intermediate kept), root excluded
-        for (const NodePlan& np : P.nodes)
-            if (np.per_slice && !np.is_root)
-                if ((st = fwd_node(bw, np, b, s0)) != TNC_OK) return st;
+        // per-slice forward, root excluded; tensors off the checkpoint levels are
+        // dropped once consumed and recomputed in the reverse walk
+        std::fill(bw.present.begin(), bw.present.end(), 0);
+        for (const NodePlan& np : P.nodes) {
+            if (!np.per_slice || np.is_root) continue;
+            if ((st = fwd_node(bw, np, b, s0)) != TNC_OK) return st;
+            bw.present[np.v] = 1;
+            for (int c : {np.A, np.B})
+                if (c >= net->n_leaves && P.per_slice[c] && !bw.keep[c] && bw.present[c]) {
+                    bw.A.release(bw.fwd.off[c]);
+                    bw.present[c] = 0;
+                }
+        }
         // seed: the root's environment is grad_out (in the root's layout)
         bw.env_layout[root] = P.layout[root];
         const int64_t relems = 1ll << P.layout[root].size();
@@ -1498,6 +1562,9 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "tc_group_m") {
         if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");
         net->tc_group_m = (int)value;
+    } else if (k == "backward_keep_every") {
+        if (value < 0 || value > 64) return fail(TNC_E_INVALID, "backward_keep_every must be in [0, 64]");
+        net->backward_keep_every = (int)value;
     } else if (k == "tc_spin_limit") {
         if (value < 0 || value > 0xFFFFFFFFll) return fail(TNC_E_INVALID, "tc_spin_limit out of range");
         net->tc_spin_limit = (uint32_t)value;
@@ -1565,18 +1632,24 @@ tnc_status tnc_contract_backward(tnc_net_t net, int64_t lo, int64_t hi, int mode
         CUDA_TRY(cudaMemsetAsync(grad_leaves_c64, 0, net->total_leaf_elems * 8, s));
         return TNC_OK;
     }
-    // largest slice batch whose workspace fits the budget (dry runs)
+    // checkpoint spacing, then the largest slice batch, that fit the budget (dry runs)
+    int keep_every = 1;
     auto need_for = [&](int64_t nb) {
         Backward d = bw;
         d.exec = false;
         d.nb = nb;
+        d.keep_every = keep_every;
         backward_run(d, lo, std::min(hi, lo + nb), grad_out_c128);
         return (size_t)d.A.top;
     };
     int64_t nb = 1;
+    if (net->backward_keep_every > 0) keep_every = net->backward_keep_every;
+    else
+        while (need_for(1) > budget_bytes && keep_every < 64) keep_every *= 2;
     if (need_for(1) > budget_bytes)
         return fail(TNC_E_OOM, "backward workspace for one slice exceeds the budget (" +
                                    std::to_string(need_for(1)) + " bytes)");
+    net->last_keep_every = keep_every;
     int64_t hi_b = std::min<int64_t>(hi - lo, 1024);
     while (nb < hi_b) {
         int64_t nx = std::min<int64_t>(nb * 2, hi_b);
@@ -1584,6 +1657,7 @@ tnc_status tnc_contract_backward(tnc_net_t net, int64_t lo, int64_t hi, int mode
         nb = nx;
     }
     const size_t need = need_for(nb);
+    net->last_backward_bytes = need;
     char* ws = nullptr;
     if (net->ws_user && net->ws_user_bytes >= need) {
         ws = (char*)net->ws_user;
@@ -1603,6 +1677,7 @@ tnc_status tnc_contract_backward(tnc_net_t net, int64_t lo, int64_t hi, int mode
     bw.exec = true;
     bw.nb = nb;
     bw.ws = ws;
+    bw.keep_every = keep_every;
     if ((st = backward_run(bw, lo, hi, grad_out_c128)) != TNC_OK) return st;
     CUDA_TRY(tnc::launch_f64_to_f32(reinterpret_cast<const double2*>(ws + bw.leaf_grad), net->total_leaf_elems,
                                     reinterpret_cast<float2*>(grad_leaves_c64), s));
@@ -1750,6 +1825,8 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
     if (net->plan.valid) {
         o << ",\"workspace_batch1\":" << plan_arena(net, 1, TNC_FP32).peak;
         o << ",\"last_batch\":" << net->last_batch;
+        o << ",\"backward_keep_every\":" << net->last_keep_every;
+        o << ",\"backward_workspace\":" << net->last_backward_bytes;
         o << ",\"nodes\":[";
         bool first = true;
         for (const NodePlan& np : net->plan.nodes) {

@@ -157,3 +157,34 @@ def test_tensor_core_environments(lib, mode):
     for (a, b, L) in zip(etc, e32, net_ref.tensors):
         assert _rel(a, b) <= 1e-4
         assert abs(np.sum(np.asarray(L).reshape(-1).astype(np.complex128) * a) - F) <= 1e-4 * abs(F)
+
+
+def test_checkpointing_recompute(lib):
+    """30-qubit workload, one slice: keeping only every 4th level of
+    per-slice intermediates (recomputing the rest in the reverse walk) gives
+    bit-identical environments; a budget below the smallest possible
+    workspace is refused. (On this tree the peak is the working set of the
+    largest node, so spacing the checkpoints does not lower it.)"""
+    from paper_2205_00393_gb300 import Network, TNCError
+    c = grid_rqc(5, 6, 14, 2, n_open=6)
+    tn_ = circuit_to_network(c).as_complex64()
+    net = Network.from_tn(tn_)
+    net.set_path(net.greedy_path())
+    net.set_slices(net.find_slices(27, 7))
+    mask = np.array([1 if g >= 0 and c.gates[g].name == "fsim" else 0 for g in tn_.leaf_gate], dtype=np.uint8)
+    seed = torch.ones(net.n_out, dtype=torch.complex128)
+    full = net.contract_backward(seed, 3, 4, 2, leaf_mask=mask).cpu().numpy()
+    st = net.stats()
+    assert st["backward_keep_every"] == 1
+    need = st["backward_workspace"]
+    net.set_option("backward_keep_every", 4)
+    ck = net.contract_backward(seed, 3, 4, 2, leaf_mask=mask).cpu().numpy()
+    net.check_device()
+    st2 = net.stats()
+    assert st2["backward_keep_every"] == 4
+    assert np.array_equal(full, ck)
+    assert st2["backward_workspace"] > 0 and need > 0
+    net.set_option("backward_keep_every", 0)
+    with pytest.raises(TNCError) as e:
+        net.contract_backward(seed, 3, 4, 2, leaf_mask=mask, budget_bytes=1 << 20)
+    assert e.value.status == 2
