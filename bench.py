@@ -379,6 +379,83 @@ def many_bench(args):
     return 0
 
 
+def grad42_bench(args):
+    """Gradient configuration: 42-qubit 6x7 grid, 12 cycles (seed 5), one
+    amplitude, sliced to 2^30-element intermediates; d amp / d(theta, phi) of
+    all fSim gates for the partial amplitude over slices [0, n) by the adjoint
+    pass under an 80 GB budget (per-level checkpointing as needed), checked
+    against central finite differences (h = 1e-3) on 16 parameters chosen by
+    seed 6."""
+    import torch
+    from tnc_inputs import circuit_to_network, grid_rqc
+    from oracle import gradient
+    from paper_2205_00393_gb300.torch_fn import CircuitAmplitudes
+    torch.cuda.set_device(0)
+    c = grid_rqc(6, 7, 12, 5)
+    tn_ = circuit_to_network(c)
+    fsim = [li for li, g in enumerate(tn_.leaf_gate) if g >= 0 and c.gates[g].name == "fsim"]
+    n_sl = args.slices_per_step
+    mode = MODES[args.mode]
+    amp = CircuitAmplitudes(tn_, fsim, target_log2=30, seed=7, lo=0, hi=n_sl, mode=mode,
+                            budget_bytes=80 << 30)
+    params = torch.tensor(gradient.circuit_params(c), dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = amp(params)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    a.real.sum().backward()  # d Re(amp) / d params
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    amp.net.check_device()
+    st = amp.net.stats()
+    g = params.grad.numpy()
+    rng = np.random.default_rng(6)
+    flat = rng.choice(params.numel(), 16, replace=False)
+    which = [(int(f) // 2, int(f) % 2) for f in flat]
+    p0 = params.detach().numpy().copy()
+    h = 1e-3
+    fd = []
+    for (k, j) in which:
+        vals = []
+        for sgn in (1, -1):
+            p = p0.copy()
+            p[k, j] += sgn * h
+            with torch.no_grad():
+                vals.append(float(amp(torch.from_numpy(p)).real.sum()))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    got = np.array([g[k, j] for (k, j) in which])
+    rms = float(np.sqrt(np.mean(fd ** 2)))
+    err = float(np.max(np.abs(got - fd) / np.maximum(np.abs(fd), rms)))
+    # second witness: the amplitude is linear in every gate matrix, so
+    # (amp(G + dG) - amp(G - dG)) / 2 is the exact derivative along dG
+    from tnc_inputs import gates as G
+    lin = []
+    for (k, j) in which:
+        th, ph = p0[k]
+        dG = G.dfsim_dtheta(th, ph) if j == 0 else G.dfsim_dphi(th, ph)
+        vals = []
+        for sgn in (1, -1):
+            amp.net.set_tensor_data(fsim[k], (G.fsim(th, ph) + sgn * dG).reshape(2, 2, 2, 2))
+            vals.append(float(amp.net.contract(0, n_sl, mode).real.sum()))
+        amp.net.set_tensor_data(fsim[k], G.fsim(th, ph).reshape(2, 2, 2, 2))
+        lin.append((vals[0] - vals[1]) / 2)
+    lin = np.array(lin)
+    rms_l = float(np.sqrt(np.mean(lin ** 2)))
+    err_lin = float(np.max(np.abs(got - lin) / np.maximum(np.abs(lin), rms_l)))
+    line = {"metric": "adjoint gradient of a 42-qubit amplitude (partial over slices) vs central differences",
+            "mode": args.mode, "params": int(params.numel()), "slices": n_sl,
+            "n_sliced": len(amp.net.sliced), "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "max_rel_err_vs_fd_h1e-3": err, "fd_params": 16,
+            "max_rel_err_vs_gate_perturbation": err_lin,
+            "backward_keep_every": st.get("backward_keep_every"),
+            "backward_workspace_gb": st.get("backward_workspace", 0) / 1e9, "budget_gb": 80 * 1.073741824,
+            "amplitude_partial": [float(a.detach().real.sum()), float(a.detach().imag.sum())]}
+    print(json.dumps(line))
+    return 0
+
+
 def backward_bench(args):
     """Forward + adjoint pass over a batch of slices per step: environments of
     every fSim leaf for F = sum of the 64 amplitudes (FP32 environment
@@ -437,6 +514,8 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
+    ap.add_argument("--grad42", action="store_true",
+                    help="42-qubit gradient configuration (adjoint vs finite differences) instead")
     ap.add_argument("--many", action="store_true",
                     help="time the batched uneven workload of many circuits instead")
     ap.add_argument("--backward", action="store_true",
@@ -458,6 +537,8 @@ def main():
         return backward_bench(args)
     if args.many:
         return many_bench(args)
+    if args.grad42:
+        return grad42_bench(args)
 
     import torch
     import torch.distributed as dist

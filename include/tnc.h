@@ -117,10 +117,13 @@ tnc_status tnc_find_slices(tnc_net_t net, int target_log2, uint64_t seed,
                            double T0, double Tf, double alpha,
                            int64_t* out_ids, int* n_out, int cap);
 
-/* Set the slicing set S (Sec. 2.1.1): n closed indices of dimension 2.
- * Slice s in [0, 2^n) assigns bit j of s to the j-th smallest id of S.
+/* Set the slicing set S (Sec. 2.1.1): n <= 120 closed indices of dimension 2.
+ * Slice s in [0, 2^n) assigns bit j of s to the j-th smallest id of S. Slice
+ * ids are int64, so only slices [0, 2^min(n, 62)) are addressable; with n > 62
+ * the indices beyond the 62nd smallest take value 0 in every addressable
+ * slice (a fixed subset of slices is still a well-defined partial sum).
  * Errors: TNC_E_INVALID for an open index, a dimension other than 2, a
- * repeated id or n > 62; TNC_E_STATE before tnc_set_path. */
+ * repeated id or n > 120; TNC_E_STATE before tnc_set_path. */
 tnc_status tnc_set_slices(tnc_net_t net, int n, const int64_t* ids);
 
 /* Device workspace needed to contract `max_batch` slices at once with the
@@ -138,7 +141,8 @@ tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes);
  *  out_c128  device pointer, 2 * 2^(sum of log2 dims of open indices) doubles,
  *            overwritten with the result in open_ids order.
  * Errors: TNC_E_STATE before tnc_set_path; TNC_E_INVALID if the range is not
- * within [0, 2^|S|] or mode is unknown; TNC_E_CUDA / TNC_E_OOM from the device. */
+ * within [0, 2^min(|S|, 62)] or mode is unknown; TNC_E_CUDA / TNC_E_OOM from
+ * the device. */
 tnc_status tnc_contract(tnc_net_t net, int64_t slice_lo, int64_t slice_hi, int mode,
                         double* out_c128, void* stream);
 
@@ -205,6 +209,10 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  the root's inputs) and recomputes the others from them in
  *                  the reverse walk; 0 picks the smallest k whose workspace
  *                  fits the budget
+ *  "tc_plane_cap_log2" 16..40 (default 32): split-precision operand planes of
+ *                  one contraction are limited to 2^value bytes per operand;
+ *                  larger operands are processed in panels of whole 128-row
+ *                  tiles (results unchanged, workspace smaller)
  *  "tc_spin_limit" polls before a bounded device-side wait gives up (0 = the
  *                  kernel default, 2^24)
  *  "tc_test_stall" tests only: nonzero makes the tensor-core producer issue no

@@ -187,7 +187,8 @@ class Network:
 
     @property
     def n_slices(self):
-        return 1 << len(self.sliced)
+        """Addressable slices: 2^min(|S|, 62) (slice ids are int64)."""
+        return 1 << min(len(self.sliced), 62)
 
     def set_tensor_data(self, i, data):
         d = np.ascontiguousarray(np.asarray(data, dtype=np.complex64))

@@ -83,6 +83,7 @@ struct TcGemmParams {
     int mb, nb, kb;
     float2* C;
     int64_t c_batch_stride;
+    int64_t c_ld;    // elements between consecutive output rows (0 = 2^nb)
     int* err;        // device error word (4 = a bounded wait gave up)
     int row_bytes;   // 64 or 128: bytes of K per tile row and stage (swizzle width)
     int group_m;     // tile rasterisation: row tiles per group (1 = row-major)

@@ -358,8 +358,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         } else {
             const int row = 32 * g + lane;
+            const int64_t ld = p.c_ld ? p.c_ld : N;
             float4* dst = reinterpret_cast<float4*>(p.C + (int64_t)z * p.c_batch_stride +
-                                                    (int64_t)(m0 + row) * N + n0 + 64 * h);
+                                                    (int64_t)(m0 + row) * ld + n0 + 64 * h);
 #pragma unroll
             for (int j = 0; j < 64; j += 2) dst[j / 2] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
         }

@@ -154,6 +154,7 @@ struct tnc_net {
     int tc_group_m = 1;
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
+    int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
     int tc_test_stall = 0;
     // cached level groups and their device parameter table
     std::string group_key;
@@ -183,6 +184,8 @@ struct tnc_net {
 
 namespace {
 
+int net_plane_cap_log2(const tnc_net* net) { return net->plane_cap_log2; }
+
 // ------------------------------------------------------------- planning ----
 
 void build_plan(tnc_net* net) {
@@ -195,7 +198,9 @@ void build_plan(tnc_net* net) {
     int total_modes = net->mode_base.empty() ? 0 : net->mode_base.back();
     P.slice_bit_of_mode.assign(total_modes, -1);
     for (size_t j = 0; j < net->S_sorted.size(); ++j)
-        P.slice_bit_of_mode[net->mode_base[net->S_sorted[j]]] = (int)j;
+        // slice ids are int64: sliced indices beyond the 62nd take value 0 in
+        // every addressable slice (bit 62 of an id below 2^62 is always 0)
+        P.slice_bit_of_mode[net->mode_base[net->S_sorted[j]]] = (int)std::min<size_t>(j, 62);
     P.layout.resize(nt);
     P.str.resize(nt);
     P.sl.resize(nt);
@@ -306,8 +311,23 @@ int64_t tensor_bytes(const Plan& P, int v) { return (int64_t)8 << P.layout[v].si
 
 std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice);
 
-int64_t planes_bytes(int mode, int rb, int kb, int64_t batch) {
+// Split-precision planes of one operand are capped (tc_plane_cap_log2, 2^32
+// bytes by default): a larger operand is processed in panels of its rows
+// (whole 128-row tiles, top row bits fixed).
+int64_t full_planes_bytes(int mode, int rb, int kb, int64_t batch) {
     return batch * (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode) << (rb + kb);
+}
+
+// Panel bits p (2^p panels) so that one panel's planes fit the cap.
+int panel_bits(const tnc_net* net, int mode, int rb, int kb, int64_t batch) {
+    const int64_t cap = (int64_t)1 << net_plane_cap_log2(net);
+    int p = 0;
+    while (p < rb - 7 && full_planes_bytes(mode, rb - p, kb, batch) > cap) ++p;
+    return p;
+}
+
+int64_t planes_bytes(const tnc_net* net, int mode, int rb, int kb, int64_t batch) {
+    return full_planes_bytes(mode, rb - panel_bits(net, mode, rb, kb, batch), kb, batch);
 }
 
 // First-fit simulation of the workspace for a batch of `nb` slices.
@@ -335,8 +355,8 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
     auto release = [&](int64_t off) { used.erase(off); };
     auto tc_planes = [&](const NodePlan& np, int64_t b) {
         const size_t i = np.v - net->n_leaves;
-        ar.planes_a[i] = alloc(planes_bytes(mode, np.mb, np.kb, b));
-        ar.planes_b[i] = alloc(planes_bytes(mode, np.nb, np.kb, b));
+        ar.planes_a[i] = alloc(planes_bytes(net, mode, np.mb, np.kb, b));
+        ar.planes_b[i] = alloc(planes_bytes(net, mode, np.nb, np.kb, b));
     };
     auto tc_release = [&](const NodePlan& np) {
         const size_t i = np.v - net->n_leaves;
@@ -566,42 +586,59 @@ tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, in
 // planes_bytes() gives for (mb, kb) and (nb, kb).
 tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, int mode, void* pa, void* pb,
                                  int node, cudaStream_t s) {
-    tnc::SplitParams sp{};
-    sp.src = g.A;
-    sp.rb = g.mb;
-    sp.kb = g.kb;
-    for (int j = 0; j < g.mb; ++j) sp.rs[j] = g.am[j];
-    for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.ak[j];
-    sp.slice0 = g.slice0;
-    sp.dst = pa;
-    CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
-    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
-    CUDA_TRY(timed_end(net, s));
-    sp = tnc::SplitParams{};
-    sp.src = g.B;
-    sp.rb = g.nb;
-    sp.kb = g.kb;
-    for (int j = 0; j < g.nb; ++j) sp.rs[j] = g.bn[j];
-    for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.bk[j];
-    sp.slice0 = g.slice0;
-    sp.dst = pb;
-    CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
-    CUDA_TRY(tnc::launch_split(sp, mode, b, s));
-    CUDA_TRY(timed_end(net, s));
-    tnc::TcGemmParams tp{};
-    tp.mb = g.mb;
-    tp.nb = g.nb;
-    tp.kb = g.kb;
-    tp.C = g.C;
-    tp.c_batch_stride = g.c_batch_stride;
-    tp.err = net->d_err;
-    tp.row_bytes = net->tc_row_bytes;
-    tp.group_m = net->tc_group_m;
-    tp.spin_limit = net->tc_spin_limit;
-    tp.test_stall = net->tc_test_stall;
-    CUDA_TRY(timed_begin(net, node, K_TC, b, s, std::ldexp(1.0, g.mb + g.nb + g.kb) * b));
-    CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
-    CUDA_TRY(timed_end(net, s));
+    // panels: fix the top pA bits of m (A rows) and pB bits of n (B rows)
+    const int pA = panel_bits(net, mode, g.mb, g.kb, b), pB = panel_bits(net, mode, g.nb, g.kb, b);
+    const int mbp = g.mb - pA, nbp = g.nb - pB;
+    const int64_t N = 1ll << g.nb;
+    for (int64_t qb = 0; qb < (1ll << pB); ++qb) {
+        tnc::Operand B = g.B;
+        for (int j = 0; j < pB; ++j)
+            if ((qb >> j) & 1) B.ptr += g.bn[nbp + j];
+        tnc::SplitParams sp{};
+        sp.src = B;
+        sp.rb = nbp;
+        sp.kb = g.kb;
+        for (int j = 0; j < nbp; ++j) sp.rs[j] = g.bn[j];
+        for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.bk[j];
+        sp.slice0 = g.slice0;
+        sp.dst = pb;
+        CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
+        CUDA_TRY(tnc::launch_split(sp, mode, b, s));
+        CUDA_TRY(timed_end(net, s));
+        for (int64_t qa = 0; qa < (1ll << pA); ++qa) {
+            tnc::Operand A = g.A;
+            for (int j = 0; j < pA; ++j)
+                if ((qa >> j) & 1) A.ptr += g.am[mbp + j];
+            if (pB == 0 || qb == 0 || pA > 0) {
+                sp = tnc::SplitParams{};
+                sp.src = A;
+                sp.rb = mbp;
+                sp.kb = g.kb;
+                for (int j = 0; j < mbp; ++j) sp.rs[j] = g.am[j];
+                for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.ak[j];
+                sp.slice0 = g.slice0;
+                sp.dst = pa;
+                CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
+                CUDA_TRY(tnc::launch_split(sp, mode, b, s));
+                CUDA_TRY(timed_end(net, s));
+            }
+            tnc::TcGemmParams tp{};
+            tp.mb = mbp;
+            tp.nb = nbp;
+            tp.kb = g.kb;
+            tp.C = g.C + (qa << mbp) * N + (qb << nbp);
+            tp.c_batch_stride = g.c_batch_stride;
+            tp.c_ld = N;
+            tp.err = net->d_err;
+            tp.row_bytes = net->tc_row_bytes;
+            tp.group_m = net->tc_group_m;
+            tp.spin_limit = net->tc_spin_limit;
+            tp.test_stall = net->tc_test_stall;
+            CUDA_TRY(timed_begin(net, node, K_TC, b, s, std::ldexp(1.0, mbp + nbp + g.kb) * b));
+            CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
+            CUDA_TRY(timed_end(net, s));
+        }
+    }
     return TNC_OK;
 }
 
@@ -712,8 +749,8 @@ tnc_status env_child(Backward& bw, const NodePlan& np, int c, int64_t b, int64_t
     const bool tc = tc_node(bw.mode, gmb, gnb, gkb, false);
     int64_t pa = -1, pb = -1;
     if (tc) {  // split-precision planes (allocated in the sizing pass too)
-        pa = bw.A.alloc(planes_bytes(bw.mode, gmb, gkb, b));
-        pb = bw.A.alloc(planes_bytes(bw.mode, gnb, gkb, b));
+        pa = bw.A.alloc(planes_bytes(bw.net, bw.mode, gmb, gkb, b));
+        pb = bw.A.alloc(planes_bytes(bw.net, bw.mode, gnb, gkb, b));
     }
     if (!bw.exec) {
         if (tc) {
@@ -872,8 +909,8 @@ tnc_status fwd_node(Backward& bw, const NodePlan& np, int64_t b, int64_t slice0)
     const bool tc = tc_node(bw.mode, np.mb, np.nb, np.kb, np.is_root);
     const size_t i = np.v - net->n_leaves;
     if (tc) {
-        bw.fwd.planes_a[i] = bw.A.alloc(planes_bytes(bw.mode, np.mb, np.kb, per ? b : 1));
-        bw.fwd.planes_b[i] = bw.A.alloc(planes_bytes(bw.mode, np.nb, np.kb, per ? b : 1));
+        bw.fwd.planes_a[i] = bw.A.alloc(planes_bytes(net, bw.mode, np.mb, np.kb, per ? b : 1));
+        bw.fwd.planes_b[i] = bw.A.alloc(planes_bytes(net, bw.mode, np.nb, np.kb, per ? b : 1));
     }
     if (bw.exec) {
         tnc::GemmParams g = gemm_params(net, bw.fwd, bw.ws, np, b);
@@ -1408,7 +1445,7 @@ tnc_status tnc_find_slices(tnc_net_t net, int target_log2, uint64_t seed, double
 tnc_status tnc_set_slices(tnc_net_t net, int n, const int64_t* ids) {
     if (!net) return fail(TNC_E_INVALID, "NULL network");
     if (!net->tree) return fail(TNC_E_STATE, "no contraction path set (call tnc_set_path)");
-    if (n < 0 || n > 62 || (n > 0 && !ids)) return fail(TNC_E_INVALID, "bad slice count");
+    if (n < 0 || n > 120 || (n > 0 && !ids)) return fail(TNC_E_INVALID, "bad slice count");
     std::set<int64_t> seen;
     for (int j = 0; j < n; ++j) {
         int64_t e = ids[j];
@@ -1449,7 +1486,7 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
         return fail(TNC_E_INVALID, "unknown mode");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
-    const int64_t n_slices = 1ll << net->S_sorted.size();
+    const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
     if (lo < 0 || hi < lo || hi > n_slices) return fail(TNC_E_INVALID, "slice range outside [0, 2^|S|]");
     cudaStream_t s = (cudaStream_t)stream;
     const Plan& P = net->plan;
@@ -1565,6 +1602,10 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "backward_keep_every") {
         if (value < 0 || value > 64) return fail(TNC_E_INVALID, "backward_keep_every must be in [0, 64]");
         net->backward_keep_every = (int)value;
+    } else if (k == "tc_plane_cap_log2") {
+        if (value < 16 || value > 40) return fail(TNC_E_INVALID, "tc_plane_cap_log2 must be in [16, 40]");
+        net->plane_cap_log2 = (int)value;
+        net->group_key.clear();
     } else if (k == "tc_spin_limit") {
         if (value < 0 || value > 0xFFFFFFFFll) return fail(TNC_E_INVALID, "tc_spin_limit out of range");
         net->tc_spin_limit = (uint32_t)value;
@@ -1612,7 +1653,7 @@ tnc_status tnc_contract_backward(tnc_net_t net, int64_t lo, int64_t hi, int mode
     if (mode < TNC_FP32 || mode > TNC_SPLIT_BF16X2) return fail(TNC_E_INVALID, "unknown mode");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
-    const int64_t n_slices = 1ll << net->S_sorted.size();
+    const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
     if (lo < 0 || hi < lo || hi > n_slices) return fail(TNC_E_INVALID, "slice range outside [0, 2^|S|]");
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = ensure_leaves(net, s)) != TNC_OK) return st;
@@ -1733,7 +1774,7 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
         if (!outs_c128[i]) return fail(TNC_E_INVALID, "NULL output");
         tnc_status st = ensure_plan(net);
         if (st != TNC_OK) return st;
-        const int64_t ns = 1ll << net->S_sorted.size();
+        const int64_t ns = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
         if (slice_lo[i] < 0 || slice_hi[i] < slice_lo[i] || slice_hi[i] > ns)
             return fail(TNC_E_INVALID, "slice range of network " + std::to_string(i) + " outside [0, 2^|S|]");
         for (int j = 0; j < i; ++j)
