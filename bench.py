@@ -512,6 +512,7 @@ def main():
     ap.add_argument("--impl", default="tnc", choices=["tnc", "reference"])
     ap.add_argument("--mode", default="bf16", choices=sorted(MODES))
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
     ap.add_argument("--grad42", action="store_true",
@@ -545,7 +546,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
-    from paper_2205_00393_gb300 import Network
+    from paper_2205_00393_gb300 import Network, tune_table
 
     c, ref_net = build_network()
     net = Network.from_tn(ref_net)
@@ -557,6 +558,8 @@ def main():
     n_slices = net.n_slices
     B = args.slices_per_step
     mode = MODES[args.mode]
+    if mode != 0 and not args.no_autotune:
+        net.autotune(mode, 0)  # setup: kernel choice per contraction shape
     ws = torch.empty(net.workspace_bytes(B), dtype=torch.uint8, device="cuda")
     net.set_workspace(ws)
     stats = net.stats()
@@ -652,6 +655,7 @@ def main():
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launches,
         "kernel_time_ms": {KIND_NAMES[k]: v["ms"] for k, v in by_kind.items()},
         "top_nodes": top_nodes(recs, stats),
+        "tuned_shapes": [e for e in tune_table() if e[0] == mode],
     }
     if args.mode != "fp32" and not args.no_fp32_compare:
         # the plain FP32 CUDA-core path on the same slices, for the split-TC / FP32 ratio

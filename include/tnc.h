@@ -221,6 +221,18 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  * Errors: TNC_E_INVALID for an unknown key or value. */
 tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value);
 
+/* Autotuner: for every contraction of the current plan that the tensor
+ * cores can take in `mode`, time one slice (`slice`) with that contraction on
+ * the FP32 CUDA cores and on the tensor cores with 128- and 64-byte rows, and
+ * record the fastest per (mode, log2 M, log2 N, log2 K) in a table shared by
+ * all networks of the process (results are the same up to rounding either
+ * way). Later contractions of any network follow the table. */
+tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream);
+
+/* The tuning table as JSON: [[mode, log2 M, log2 N, log2 K, choice], ...]
+ * with choice 0 = FP32 CUDA cores, 64 / 128 = tensor-core row width. */
+tnc_status tnc_tune_table(char* json, size_t cap);
+
 /* Per-launch timing: when enabled, every kernel launch of tnc_contract is
  * bracketed by CUDA events recorded on the contraction's stream. Each call
  * clears the records and the launch counter, which then accumulate over all

@@ -61,6 +61,8 @@ def load_library():
         "tnc_stats": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
         "tnc_set_timing": [ctypes.c_void_p, ctypes.c_int],
         "tnc_check_device": [ctypes.c_void_p, ctypes.c_void_p],
+        "tnc_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p],
+        "tnc_tune_table": [ctypes.c_char_p, ctypes.c_size_t],
         "tnc_set_option": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64],
         "tnc_contract_backward": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
@@ -95,6 +97,14 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def tune_table():
+    """The process-wide tuning table: list of [mode, log2 M, log2 N, log2 K, choice]."""
+    lib = load_library()
+    buf = ctypes.create_string_buffer(1 << 20)
+    _check(lib, lib.tnc_tune_table(buf, 1 << 20))
+    return json.loads(buf.value.decode())
 
 
 def contract_many(networks, ranges=None, mode=FP32, outs=None, use_graph=True, stream=None):
@@ -234,6 +244,10 @@ class Network:
     def set_option(self, key, value):
         """Tensor-core tuning option (see tnc_set_option in include/tnc.h)."""
         _check(self._lib, self._lib.tnc_set_option(self._h, key.encode(), int(value)))
+
+    def autotune(self, mode, slice=0, stream=None):
+        """Time FP32 vs tensor-core kernels per contraction shape (tnc_autotune)."""
+        _check(self._lib, self._lib.tnc_autotune(self._h, int(mode), int(slice), _stream_ptr(stream)))
 
     def check_device(self, stream=None):
         """Wait for the stream; raise TNCError if a device-side wait gave up."""

@@ -42,22 +42,21 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
 // Shared-memory stages are double buffered: the gather of tile t+1 goes to
 // registers while tile t is multiplied, then to the other stage (one barrier
 // per tile). Accumulation is two-level: each group of GROUP_TILES k-tiles is
-// summed in a fresh partial, and the partials are added to the result with
-// Kahan compensation, so the FP32 rounding error grows with sqrt(64) per
-// group instead of sqrt(K).
+// summed in a fresh partial that is then added to the result, so the FP32
+// rounding error grows like sqrt(64) + sqrt(K / 64) instead of sqrt(K). The
+// register budget (128 per thread) keeps two CTAs per SM.
 constexpr int PAD = 2;           // keeps 16-byte alignment of fragment rows
 constexpr int GROUP_TILES = 4;   // 64 k-terms per partial sum
 
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
-    float y = x - comp;
-    float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
-}
 
+// B columns are stored interleaved: column n goes to half (n >> 1) & 1 at
+// position (n >> 2) * 2 + (n & 1), so the two 16-byte halves of the four
+// columns a thread owns are contiguous across the warp (one 256-byte span per
+// load instead of a 512-byte stride).
+constexpr int BH = BN / 2 + PAD;
 struct GemmSmem {
     float2 As[2][BK][BM + PAD];
-    float2 Bs[2][BK][BN + PAD];
+    float2 Bs[2][BK][2][BH];
     int64_t rowA[BM], colB[BN], klA[BK], klB[BK];
 };
 
@@ -120,18 +119,17 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             As[st][la_k[i]][la_m[i]] = ra[i];
-            Bs[st][lb_k[i]][lb_n[i]] = rb[i];
+            Bs[st][lb_k[i]][(lb_n[i] >> 1) & 1][(lb_n[i] >> 2) * 2 + (lb_n[i] & 1)] = rb[i];
         }
     };
 
     const int tx = tid & 15, ty = tid >> 4;
-    float2 acc[4][4], cmp[4][4], part[4][4];
+    float2 acc[4][4], part[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             acc[i][j] = make_float2(0.f, 0.f);
-            cmp[i][j] = make_float2(0.f, 0.f);
             part[i][j] = make_float2(0.f, 0.f);
         }
 
@@ -146,8 +144,8 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
         for (int kk = 0; kk < BK; ++kk) {
             float4 a01 = *reinterpret_cast<const float4*>(&As[st][kk][4 * ty]);
             float4 a23 = *reinterpret_cast<const float4*>(&As[st][kk][4 * ty + 2]);
-            float4 b01 = *reinterpret_cast<const float4*>(&Bs[st][kk][4 * tx]);
-            float4 b23 = *reinterpret_cast<const float4*>(&Bs[st][kk][4 * tx + 2]);
+            float4 b01 = *reinterpret_cast<const float4*>(&Bs[st][kk][0][2 * tx]);
+            float4 b23 = *reinterpret_cast<const float4*>(&Bs[st][kk][1][2 * tx]);
             float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
                            make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
             float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
@@ -162,8 +160,8 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    kahan_add(acc[i][j].x, cmp[i][j].x, part[i][j].x);
-                    kahan_add(acc[i][j].y, cmp[i][j].y, part[i][j].y);
+                    acc[i][j].x += part[i][j].x;
+                    acc[i][j].y += part[i][j].y;
                     part[i][j] = make_float2(0.f, 0.f);
                 }
         }
@@ -189,14 +187,14 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
     }
 }
 
-__global__ void __launch_bounds__(NT) k_gemm_f32(const __grid_constant__ GemmParams p) {
+__global__ void __launch_bounds__(NT, 2) k_gemm_f32(const __grid_constant__ GemmParams p) {
     __shared__ __align__(16) GemmSmem sm;
     gemm_tile(p, blockIdx.x, blockIdx.z, p.slice0, sm);
 }
 
 // Many independent contractions in one launch (nodes of one tree level): CTA
 // b serves tile b - tile_off[i] of node i, tile_off[i] <= b < tile_off[i+1].
-__global__ void __launch_bounds__(NT) k_gemm_f32_group(const GemmParams* __restrict__ params,
+__global__ void __launch_bounds__(NT, 2) k_gemm_f32_group(const GemmParams* __restrict__ params,
                                                        const int64_t* __restrict__ tile_off, int n,
                                                        int64_t slice0) {
     __shared__ __align__(16) GemmSmem sm;
@@ -293,7 +291,7 @@ cudaError_t launch_gemm_f32(const GemmParams& p, int batch, cudaStream_t s) {
 // Grouped contractions of several networks: node i belongs to network
 // net[i]; slice z of the launch maps to slice rs0[net] + z of that network and
 // exists only for z < rb[net] (networks batch different numbers of slices).
-__global__ void __launch_bounds__(NT) k_gemm_f32_group_multi(const GemmParams* __restrict__ params,
+__global__ void __launch_bounds__(NT, 2) k_gemm_f32_group_multi(const GemmParams* __restrict__ params,
                                                              const int64_t* __restrict__ tile_off, int n,
                                                              const int* __restrict__ net,
                                                              const int64_t* __restrict__ rs0,

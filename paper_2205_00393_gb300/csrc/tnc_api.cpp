@@ -14,6 +14,7 @@
 #include "tnc.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -56,6 +57,15 @@ enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K
 bool tc_node(int mode, int mb, int nb, int kb, bool is_root) {
     return mode != TNC_FP32 && !is_root && mb >= 7 && nb >= 7 && kb >= tnc::tc_min_kb(mode);
 }
+
+// Autotuned kernel choice per (mode, log2 M, log2 N, log2 K): 0 = FP32 CUDA
+// cores, 64 / 128 = tensor cores with that row width. Filled by
+// tnc_autotune; shared by every network of the process.
+std::map<std::tuple<int, int, int, int>, int>& tune_table() {
+    static std::map<std::tuple<int, int, int, int>, int> t;
+    return t;
+}
+uint64_t g_tune_version = 0;
 
 struct NodePlan {
     int v = 0;            // tensor id produced
@@ -155,6 +165,8 @@ struct tnc_net {
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
+    int force_choice = -1;       // autotuning: force 0 (FP32) or a tensor-core row width
+    bool tuning = false;         // autotuning: every eligible node gets its own launch
     int tc_test_stall = 0;
     // cached level groups and their device parameter table
     std::string group_key;
@@ -185,6 +197,17 @@ struct tnc_net {
 namespace {
 
 int net_plane_cap_log2(const tnc_net* net) { return net->plane_cap_log2; }
+
+// Kernel for a contraction of this shape: 0 = FP32 CUDA cores, otherwise the
+// tensor-core row width. Eligibility first, then a forced choice (autotuning
+// runs), then the tuning table, then the network's default row width.
+int shape_choice(const tnc_net* net, int mode, int mb, int nb, int kb, bool is_root) {
+    if (!tc_node(mode, mb, nb, kb, is_root)) return 0;
+    if (net->force_choice >= 0) return net->force_choice;
+    auto it = tune_table().find(std::make_tuple(mode, mb, nb, kb));
+    if (it != tune_table().end()) return it->second;
+    return net->tc_row_bytes;
+}
 
 // ------------------------------------------------------------- planning ----
 
@@ -370,7 +393,7 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
         for (int v : g.tc) ar.off[v] = alloc(b * tensor_bytes(P, v));
         for (int v : g.tc) {
             const NodePlan& np = P.nodes[v - net->n_leaves];
-            if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) continue;
+            if (!shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root)) continue;
             tc_planes(np, b);
             tc_release(np);
         }
@@ -515,7 +538,9 @@ std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice) {
         Group& g = by_level[l + 1];
         g.per_slice = per_slice;
         // large contractions keep their own launch (parameters in kernel parameter space)
-        if (tc_node(mode, np.mb, np.nb, np.kb, np.is_root) || tnc::gemm_f32_tiles(np.mb, np.nb) >= 256)
+        if (shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root) ||
+            (net->tuning && tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) ||
+            tnc::gemm_f32_tiles(np.mb, np.nb) >= 256)
             g.tc.push_back(np.v);
         else
             g.fp32.push_back(np.v);
@@ -529,7 +554,8 @@ std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice) {
 // plan, mode, batch and workspace.
 tnc_status ensure_groups(tnc_net* net, const Arena& ar, char* ws, int mode, int64_t nb, cudaStream_t s) {
     std::string key = std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string((uintptr_t)ws) +
-                      ":" + std::to_string(net->plan.version);
+                      ":" + std::to_string(net->plan.version) + ":" + std::to_string(g_tune_version) + ":" +
+                      std::to_string(net->force_choice) + ":" + std::to_string(net->tuning ? 1 : 0);
     if (key == net->group_key) return TNC_OK;
     GroupPlan G;
     G.inv = level_groups(net, mode, false);
@@ -585,7 +611,7 @@ tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, in
 // per-bit strides, output); planes are workspace temporaries of the sizes
 // planes_bytes() gives for (mb, kb) and (nb, kb).
 tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, int mode, void* pa, void* pb,
-                                 int node, cudaStream_t s) {
+                                 int node, cudaStream_t s, int row_bytes) {
     // panels: fix the top pA bits of m (A rows) and pB bits of n (B rows)
     const int pA = panel_bits(net, mode, g.mb, g.kb, b), pB = panel_bits(net, mode, g.nb, g.kb, b);
     const int mbp = g.mb - pA, nbp = g.nb - pB;
@@ -630,7 +656,7 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tp.c_batch_stride = g.c_batch_stride;
             tp.c_ld = N;
             tp.err = net->d_err;
-            tp.row_bytes = net->tc_row_bytes;
+            tp.row_bytes = row_bytes;
             tp.group_m = net->tc_group_m;
             tp.spin_limit = net->tc_spin_limit;
             tp.test_stall = net->tc_test_stall;
@@ -646,14 +672,15 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
 // nodes) operand split + tensor-core GEMM. `g` carries operands and output.
 tnc_status launch_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, const tnc::GemmParams& g,
                        int b, int mode, cudaStream_t s) {
-    if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) {
+    const int choice = shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root);
+    if (!choice) {
         CUDA_TRY(timed_begin(net, np.v, K_GEMM_F32, b, s));
         CUDA_TRY(tnc::launch_gemm_f32(g, b, s));
         CUDA_TRY(timed_end(net, s));
         return TNC_OK;
     }
     const size_t i = np.v - net->n_leaves;
-    return launch_tc_contraction(net, g, b, mode, ws + ar.planes_a[i], ws + ar.planes_b[i], np.v, s);
+    return launch_tc_contraction(net, g, b, mode, ws + ar.planes_a[i], ws + ar.planes_b[i], np.v, s, choice);
 }
 
 tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, int b, int64_t slice0, int mode,
@@ -746,7 +773,8 @@ tnc_status env_child(Backward& bw, const NodePlan& np, int c, int64_t b, int64_t
     bw.env_off[c] = off;
     // GEMM dims of this environment: E_A is (mb, kb) over nb; E_B is (kb, nb) over mb
     const int gmb = is_a ? np.mb : np.kb, gnb = is_a ? np.kb : np.nb, gkb = is_a ? np.nb : np.mb;
-    const bool tc = tc_node(bw.mode, gmb, gnb, gkb, false);
+    const int env_choice = shape_choice(net, bw.mode, gmb, gnb, gkb, false);
+    const bool tc = env_choice != 0;
     int64_t pa = -1, pb = -1;
     if (tc) {  // split-precision planes (allocated in the sizing pass too)
         pa = bw.A.alloc(planes_bytes(bw.net, bw.mode, gmb, gkb, b));
@@ -797,7 +825,8 @@ tnc_status env_child(Backward& bw, const NodePlan& np, int c, int64_t b, int64_t
     g.slice0 = slice0;
     if (tc) {
         // split precision with FP32 accumulation, as in the forward
-        tnc_status st = launch_tc_contraction(net, g, (int)b, bw.mode, bw.ws + pa, bw.ws + pb, np.v, bw.s);
+        tnc_status st =
+            launch_tc_contraction(net, g, (int)b, bw.mode, bw.ws + pa, bw.ws + pb, np.v, bw.s, env_choice);
         bw.A.release(pa);
         bw.A.release(pb);
         return st;
@@ -906,7 +935,7 @@ tnc_status fwd_node(Backward& bw, const NodePlan& np, int64_t b, int64_t slice0)
     const Plan& P = net->plan;
     const bool per = np.per_slice;
     bw.fwd.off[np.v] = bw.A.alloc((per ? b : 1) * tensor_bytes(P, np.v));
-    const bool tc = tc_node(bw.mode, np.mb, np.nb, np.kb, np.is_root);
+    const bool tc = shape_choice(net, bw.mode, np.mb, np.nb, np.kb, np.is_root) != 0;
     const size_t i = np.v - net->n_leaves;
     if (tc) {
         bw.fwd.planes_a[i] = bw.A.alloc(planes_bytes(net, bw.mode, np.mb, np.kb, per ? b : 1));
@@ -1576,6 +1605,77 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
             CUDA_TRY(timed_end(net, s));
         }
     }
+    return TNC_OK;
+}
+
+tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (mode == TNC_FP32) return TNC_OK;  // nothing to choose
+    tnc_status st = ensure_plan(net);
+    if (st != TNC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
+    if (slice < 0 || slice >= n_slices) return fail(TNC_E_INVALID, "slice out of range");
+    const int R = 1 << net->plan.obits;
+    double* out = nullptr;
+    CUDA_TRY(cudaMalloc(&out, (size_t)R * 16));
+    const int variants[3] = {0, 128, 64};
+    std::map<int, double> t[3];  // per node: milliseconds of all its launches
+    const bool timing = net->timing;
+    net->tuning = true;
+    for (int vi = 0; vi < 3 && st == TNC_OK; ++vi) {
+        net->force_choice = variants[vi];
+        for (int rep = 0; rep < 2 && st == TNC_OK; ++rep) {  // the first run warms up
+            net->timing = true;
+            net->timed.clear();
+            st = tnc_contract(net, slice, slice + 1, mode, out, stream);
+            if (st != TNC_OK) break;
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (rep == 1)
+                for (const auto& r : net->timed) {
+                    float ms = 0.f;
+                    CUDA_TRY(cudaEventElapsedTime(&ms, net->ev_pool[r.ev], net->ev_pool[r.ev + 1]));
+                    if (r.node >= net->n_leaves) t[vi][r.node] += ms;
+                }
+        }
+    }
+    net->force_choice = -1;
+    net->tuning = false;
+    net->timing = timing;
+    net->timed.clear();
+    cudaFree(out);
+    if (st != TNC_OK) return st;
+    std::map<std::tuple<int, int, int, int>, std::array<double, 3>> by_shape;
+    for (const NodePlan& np : net->plan.nodes) {
+        if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) continue;
+        auto& acc = by_shape[std::make_tuple(mode, np.mb, np.nb, np.kb)];
+        for (int vi = 0; vi < 3; ++vi) acc[vi] += t[vi][np.v];
+    }
+    for (auto& kv : by_shape) {
+        int best = 0;
+        for (int vi = 1; vi < 3; ++vi)
+            if (kv.second[vi] < kv.second[best]) best = vi;
+        tune_table()[kv.first] = variants[best];
+    }
+    ++g_tune_version;
+    net->group_key.clear();
+    return TNC_OK;
+}
+
+tnc_status tnc_tune_table(char* json, size_t cap) {
+    if (!json) return fail(TNC_E_INVALID, "NULL argument");
+    std::ostringstream o;
+    o << "[";
+    bool first = true;
+    for (auto& kv : tune_table()) {
+        o << (first ? "" : ",") << "[" << std::get<0>(kv.first) << "," << std::get<1>(kv.first) << ","
+          << std::get<2>(kv.first) << "," << std::get<3>(kv.first) << "," << kv.second << "]";
+        first = false;
+    }
+    o << "]";
+    std::string str = o.str();
+    if (str.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small");
+    std::memcpy(json, str.c_str(), str.size() + 1);
     return TNC_OK;
 }
 
