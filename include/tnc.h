@@ -213,6 +213,11 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  one contraction are limited to 2^value bytes per operand;
  *                  larger operands are processed in panels of whole 128-row
  *                  tiles (results unchanged, workspace smaller)
+ *  "cache_invariants" 0 (default) or 1: keep the slice-invariant tensors that
+ *                  feed per-slice contractions in the workspace between calls
+ *                  and skip their recomputation while the plan, leaf data,
+ *                  mode, batch, workspace and tuning are unchanged (the
+ *                  workspace must not be used for anything else meanwhile)
  *  "tc_spin_limit" polls before a bounded device-side wait gives up (0 = the
  *                  kernel default, 2^24)
  *  "tc_test_stall" tests only: nonzero makes the tensor-core producer issue no

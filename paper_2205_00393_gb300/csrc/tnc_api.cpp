@@ -166,6 +166,9 @@ struct tnc_net {
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
     int force_choice = -1;       // autotuning: force 0 (FP32) or a tensor-core row width
+    bool cache_invariants = false;  // keep slice-invariant inputs of per-slice nodes across calls
+    std::string inv_key;            // state under which the cached invariants were computed
+    uint64_t leaf_version = 0;      // bumped whenever leaf data changes
     bool tuning = false;         // autotuning: every eligible node gets its own launch
     int tc_test_stall = 0;
     // cached level groups and their device parameter table
@@ -1205,6 +1208,7 @@ tnc_status many_build(ManyCall& mc, cudaStream_t s) {
         }
         mc.nb[i] = nb;
         mc.wss[i] = ws;
+        net->inv_key.clear();
         mc.arenas[i] = plan_arena(net, nb, mc.mode);
         if ((st = ensure_groups(net, mc.arenas[i], ws, mc.mode, nb, s)) != TNC_OK) return st;
         max_inv = std::max(max_inv, (int)net->groups.inv.size());
@@ -1397,6 +1401,7 @@ tnc_status tnc_set_tensor_data(tnc_net_t net, int tensor, const float* data_c64)
     if (tensor < 0 || tensor >= net->n_leaves) return fail(TNC_E_INVALID, "tensor out of range");
     std::memcpy(net->host_leaves.data() + 2 * net->leaf_off[tensor], data_c64, net->leaf_elems[tensor] * 8);
     net->dev_dirty = true;
+    net->leaf_version += 1;
     return TNC_OK;
 }
 
@@ -1413,6 +1418,7 @@ tnc_status tnc_upload_leaves(tnc_net_t net, const float* packed, void* stream) {
     std::memcpy(net->host_leaves.data(), packed, net->total_leaf_elems * 8);
     CUDA_TRY(cudaMemcpyAsync(net->d_leaves, packed, net->total_leaf_elems * 8, cudaMemcpyHostToDevice, st));
     net->dev_dirty = false;
+    net->leaf_version += 1;
     return TNC_OK;
 }
 
@@ -1505,6 +1511,7 @@ tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes) {
     if (((uintptr_t)dev_ptr) % kAlign) return fail(TNC_E_INVALID, "workspace must be 256-byte aligned");
     net->ws_user = dev_ptr;
     net->ws_user_bytes = dev_ptr ? bytes : 0;
+    net->inv_key.clear();
     return TNC_OK;
 }
 
@@ -1551,9 +1558,14 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     CUDA_TRY(cudaMemsetAsync(net->d_err, 0, sizeof(int), s));
 
     if ((st = ensure_groups(net, ar, ws, mode, nb, s)) != TNC_OK) return st;
-    // invariant nodes once, one launch per level
-    for (const Group& g : net->groups.inv)
-        if ((st = run_group(net, ar, ws, g, 1, 0, mode, s)) != TNC_OK) return st;
+    // invariant nodes once, one launch per level (or reused from an earlier
+    // call when caching is on and nothing they depend on has changed)
+    const std::string ikey = net->group_key + "|" + std::to_string(net->leaf_version);
+    if (!(net->cache_invariants && net->inv_key == ikey)) {
+        for (const Group& g : net->groups.inv)
+            if ((st = run_group(net, ar, ws, g, 1, 0, mode, s)) != TNC_OK) return st;
+        net->inv_key = net->cache_invariants ? ikey : std::string();
+    }
     tnc::PermParams pp{};
     pp.obits = P.obits;
     for (int j = 0; j < P.obits; ++j) pp.ostride[j] = P.out_stride[j];
@@ -1706,6 +1718,9 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
         if (value < 16 || value > 40) return fail(TNC_E_INVALID, "tc_plane_cap_log2 must be in [16, 40]");
         net->plane_cap_log2 = (int)value;
         net->group_key.clear();
+    } else if (k == "cache_invariants") {
+        net->cache_invariants = value != 0;
+        net->inv_key.clear();
     } else if (k == "tc_spin_limit") {
         if (value < 0 || value > 0xFFFFFFFFll) return fail(TNC_E_INVALID, "tc_spin_limit out of range");
         net->tc_spin_limit = (uint32_t)value;
@@ -1814,6 +1829,7 @@ tnc_status tnc_contract_backward(tnc_net_t net, int64_t lo, int64_t hi, int mode
     }
     net->last_batch = nb;
     net->group_key.clear();  // the workspace may now hold other data
+    net->inv_key.clear();
     CUDA_TRY(cudaMemsetAsync(net->d_err, 0, sizeof(int), s));
     bw.exec = true;
     bw.nb = nb;

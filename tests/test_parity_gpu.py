@@ -150,3 +150,32 @@ def test_invalid_range_and_mode(lib):
         net.contract(3, 2)
     with pytest.raises(TNCError):
         net.contract(0, 1, mode=9)
+
+
+def test_cached_invariants(lib):
+    """cache_invariants: the second call reuses the slice-invariant tensors
+    (fewer launches) with identical results; changing a leaf recomputes them."""
+    c, ref_net, net, path, S = _setup(4, 5, 12, 7, 2, 16)
+    n = net.n_slices
+    base = _gpu(net, 0, n)
+    net.set_option("cache_invariants", 1)
+    net.set_timing(True)
+    a = _gpu(net, 0, n)
+    _, l1 = net.last_timings()
+    net.set_timing(True)
+    b = _gpu(net, 0, n)
+    _, l2 = net.last_timings()
+    net.set_timing(False)
+    assert np.array_equal(a, base) and np.array_equal(b, base)
+    assert l2 < l1
+    # change a leaf that no sliced index touches: the cache must be refreshed
+    tree = planner.Tree(ref_net.indices, ref_net.dims, ref_net.open_ids, path)
+    i = next(v for v in range(ref_net.n_tensors)
+             if len(ref_net.indices[v]) == 4 and not set(ref_net.indices[v]) & set(S))
+    new = (ref_net.tensors[i] * np.complex64(-1j)).astype(np.complex64)
+    net.set_tensor_data(i, new)
+    got = _gpu(net, 0, n)
+    ts = list(ref_net.tensors)
+    ts[i] = new
+    want = tn.contract(ref_net.with_tensors(ts), path, S)
+    assert floored_rel_err(got, want, 20) <= TOL_FP32
