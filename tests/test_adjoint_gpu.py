@@ -188,3 +188,39 @@ def test_checkpointing_recompute(lib):
     with pytest.raises(TNCError) as e:
         net.contract_backward(seed, 3, 4, 2, leaf_mask=mask, budget_bytes=1 << 20)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_30q_gradients_vs_gate_perturbation(lib, mode):
+    """30-qubit 5x6 grid (14 cycles), one amplitude, one slice of the t = 27
+    slicing: the amplitude is linear in every gate matrix G, so
+    (F(G + dG) - F(G - dG)) / 2 is the exact derivative along dG = dG/dtheta
+    (or dG/dphi) up to the forward's rounding. The adjoint gradient of
+    Re(F) on 16 seeded parameters matches it within 1e-4 (floored at the rms
+    of the checked set)."""
+    from paper_2205_00393_gb300.torch_fn import CircuitAmplitudes
+    c = grid_rqc(5, 6, 14, 2)
+    tn_ = circuit_to_network(c)
+    fsim = [li for li, g in enumerate(tn_.leaf_gate) if g >= 0 and c.gates[g].name == "fsim"]
+    amp = CircuitAmplitudes(tn_, fsim, target_log2=27, seed=7, lo=3, hi=4, mode=mode)
+    p0 = gradient.circuit_params(c)
+    params = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    amp(params).real.sum().backward()
+    amp.net.check_device()
+    g = params.grad.numpy()
+    rng = np.random.default_rng(6)
+    which = [(int(f) // 2, int(f) % 2) for f in rng.choice(p0.size, 16, replace=False)]
+    lin = []
+    for (k, j) in which:
+        th, ph = p0[k]
+        dG = G.dfsim_dtheta(th, ph) if j == 0 else G.dfsim_dphi(th, ph)
+        vals = []
+        for sgn in (1, -1):
+            amp.net.set_tensor_data(fsim[k], (G.fsim(th, ph) + sgn * dG).reshape(2, 2, 2, 2))
+            vals.append(complex(amp.net.contract(3, 4, mode).sum()))
+        amp.net.set_tensor_data(fsim[k], G.fsim(th, ph).reshape(2, 2, 2, 2))
+        lin.append(((vals[0] - vals[1]) / 2).real)
+    got = np.array([g[k, j] for (k, j) in which])
+    err = _rel(got, np.array(lin))
+    print("30q mode %d adjoint vs gate perturbation %.3e" % (mode, err))
+    assert err <= 1e-4
