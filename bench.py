@@ -399,7 +399,7 @@ def grad42_bench(args):
     tn_ = circuit_to_network(c)
     fsim = [li for li, g in enumerate(tn_.leaf_gate) if g >= 0 and c.gates[g].name == "fsim"]
     n_sl = args.slices_per_step
-    mode = MODES[args.mode]
+    mode = MODES[args.mode]  # FP32 by default: complex64 forward, FP32 adjoint
     amp = CircuitAmplitudes(tn_, fsim, target_log2=30, seed=7, lo=0, hi=n_sl, mode=mode,
                             budget_bytes=80 << 30)
     params = torch.tensor(gradient.circuit_params(c), dtype=torch.float64, requires_grad=True)
@@ -517,7 +517,8 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnc", choices=["tnc", "reference"])
-    ap.add_argument("--mode", default="bf16", choices=sorted(MODES))
+    ap.add_argument("--mode", default=None, choices=sorted(MODES),
+                    help="arithmetic of the contractions (default bf16; fp32 for --grad42)")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
@@ -535,6 +536,8 @@ def main():
     ap.add_argument("--slices-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.mode is None:
+        args.mode = "fp32" if args.grad42 else "bf16"
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

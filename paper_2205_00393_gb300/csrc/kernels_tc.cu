@@ -374,6 +374,348 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
+// ------------------------------------------------------------ CTA pair
+//
+// k_cgemm_tc2: the same contraction on 256x128 output tiles computed by a
+// cluster of two CTAs with 2-SM MMAs (tcgen05.mma.cta_group::2, M = 256).
+// Each CTA loads its own 128 rows of A and one half (64 rows) of the tile's
+// B rows; the tensor cores of both SMs read both halves of B, so an SM's
+// shared memory takes 72 KB of TMA writes and 144 KB of MMA operand reads
+// per stage instead of 96 + 192 KB. Roles:
+//   both CTAs  warp 8: TMA producer into its own ring, signalling its own
+//                      full barrier; warps 0-7: epilogue of its own 128 rows;
+//   leader     warp 9: MMA issuer; commits multicast to both CTAs' empty
+//                      and TMEM-full barriers;
+//   peer       warp 9: relay: when its own stage is full, arrives on the
+//                      leader's peer-full barrier for that stage.
+// Every CTA thus only waits on barriers its own loads or the leader's
+// commits complete; every wait is bounded, and a wait that gives up raises
+// the abort flag of both CTAs.
+
+constexpr int SMEM_PIPE2 = 216 * 1024;
+
+template <int KIND> struct Cfg2 {
+    using C1 = Cfg<KIND, 128>;
+    static constexpr int PARTS = C1::PARTS, NPAIRS = C1::NPAIRS, BK = C1::BK, KSTEPS = C1::KSTEPS;
+    static constexpr int A_PART = TM * 128;         // bytes of one A part tile: 128 rows x 128 B
+    static constexpr int B_PART = (TN / 2) * 128;   // one B part tile: this CTA's 64 rows
+    static constexpr int STAGE_A = PARTS * A_PART;
+    static constexpr int STAGE_BYTES = STAGE_A + PARTS * B_PART;
+    static constexpr int STAGES = SMEM_PIPE2 / STAGE_BYTES;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of `saddr` (a shared::cta address) in CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
+    return d;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+// Non-suspending test: a waiter suspended in try_wait is not necessarily woken
+// by an arrive from the other CTA, so barriers with remote arrivals are polled.
+__device__ __forceinline__ bool mbar_try_acq_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        "selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a barrier that the other CTA arrives on.
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                  uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_try_acq_cluster(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+// stop both CTAs of the pair and record a timeout
+__device__ __forceinline__ void raise_abort_pair(volatile int* abort_local, uint32_t peer_abort, int* err) {
+    *abort_local = 1;
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1) : "memory");
+    atomicExch(err, kErrTimeout);
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma2(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (KIND != 1) {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+// arrive once on the barrier at this offset in both CTAs when the MMAs issued so far complete
+__device__ __forceinline__ void mma_commit2_both(uint32_t bar) {
+    const uint16_t mask = 3;
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit2_local(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Instruction descriptor of the 2-SM MMA: M = 256 (128 rows per CTA), N = 128.
+template <int KIND>
+__host__ __device__ constexpr uint32_t instr_desc2() {
+    return (1u << 4) | ((KIND == 1 ? 2u : 1u) << 7) | ((KIND == 1 ? 2u : 1u) << 10) |
+           ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
+}
+
+template <int KIND>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    k_cgemm_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const __grid_constant__ TcGemmParams p) {
+    using C_ = Cfg2<KIND>;
+    const int GROUP_M = p.group_m < 1 ? 1 : p.group_m;
+    extern __shared__ __align__(1024) uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t full_bar[C_::STAGES], pfull_bar[C_::STAGES], empty_bar[C_::STAGES], tfull[3],
+        tfree[3], drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+    const int64_t N = 1ll << p.nb, K = 1ll << p.kb;
+    // grouped rasterisation over pair tiles (256 rows x 128 columns)
+    const int64_t tiles_n = N / TN, tiles_m = (1ll << p.mb) / (2 * TM);
+    const int64_t per_group = (int64_t)GROUP_M * tiles_n;
+    const int64_t pair = blockIdx.x >> 1;
+    const int64_t grp = pair / per_group, in_grp = pair % per_group;
+    const int64_t gm = (tiles_m - grp * GROUP_M) < GROUP_M ? (tiles_m - grp * GROUP_M) : GROUP_M;
+    const int m0 = (int)((grp * GROUP_M + in_grp % gm) * 2 * TM) + (int)rank * TM;  // this CTA's rows
+    const int n0 = (int)((in_grp / gm) * TN);
+    const int nb0 = n0 + (int)rank * (TN / 2);  // this CTA's half of the tile's B rows
+    const int z = blockIdx.z;
+    const int nkb = (int)(K / C_::BK);
+    const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;
+    const int nchunks = nkb / kpc;
+    const int n_it = nchunks * 3 * kpc;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C_::STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&pfull_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int t = 0; t < 3; ++t) {
+            mbar_init(smem_u32(&tfull[t]), 1);
+            mbar_init(smem_u32(&tfree[t]), 2 * EPI_WARPS);
+        }
+        mbar_init(smem_u32(&drain_bar), 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    cluster_sync_all();  // both CTAs' barriers initialised and TMEM allocated
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    volatile int* abort_flag = &abort_sh;
+    const uint32_t spin = p.spin_limit ? p.spin_limit : kSpinLimit;
+    const uint32_t peer_abort = map_rank(smem_u32(&abort_sh), rank ^ 1u);
+
+    if (warp == PRODUCER_WARP && lane == 0) {
+        // ---------------- TMA producer (both CTAs): own A rows and own half of B
+        int issued = 0;
+        for (int it = 0; it < n_it && !p.test_stall; ++it) {
+            const int s = it % C_::STAGES;
+            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag, spin)) {
+                raise_abort_pair(abort_flag, peer_abort, p.err);
+                break;
+            }
+            const int c = it / (3 * kpc), r = it % (3 * kpc);
+            const int t = r / kpc, kb = c * kpc + r % kpc;
+            const uint32_t sa = smem_u32(smem + s * C_::STAGE_BYTES);
+            const uint32_t fb = smem_u32(&full_bar[s]);
+            mbar_expect_tx(fb, C_::STAGE_BYTES);
+            tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, z, fb);
+            tma_load_4d(sa + C_::STAGE_A, &tmB, kb * C_::BK, nb0, t * C_::PARTS, z, fb);
+            issued = it + 1;
+        }
+        if (*abort_flag || issued < n_it) {
+            // drain: wait (bounded) for this CTA's loads that may still be in flight
+            int first = issued - C_::STAGES < 0 ? 0 : issued - C_::STAGES;
+            for (int it = first; it < issued; ++it) {
+                const int s = it % C_::STAGES;
+                const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+                for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&full_bar[s]), ph); ++i) {
+                }
+            }
+        } else {
+            // tail: the leader's last commits arrive on this CTA's empty barriers;
+            // wait until they have, so none lands after this CTA exits (an abort
+            // ends the wait: the leader then drains its MMAs before the pair's
+            // final cluster barrier)
+            int first = n_it - C_::STAGES < 0 ? 0 : n_it - C_::STAGES;
+            for (int it = first; it < n_it; ++it) {
+                const int s = it % C_::STAGES;
+                const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&empty_bar[s]), ph, abort_flag, spin)) break;
+            }
+        }
+    } else if (warp == MMA_WARP && lane == 0 && !leader) {
+        // ---------------- relay (peer): own stage full -> leader's peer-full barrier
+        for (int it = 0; it < n_it && !*abort_flag; ++it) {
+            const int s = it % C_::STAGES;
+            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin)) {
+                raise_abort_pair(abort_flag, peer_abort, p.err);
+                break;
+            }
+            mbar_arrive_cluster(map_rank(smem_u32(&pfull_bar[s]), 0));
+        }
+    } else if (warp == MMA_WARP && lane == 0) {
+        // ---------------- MMA issuer (leader)
+        constexpr uint32_t idesc = instr_desc2<KIND>();
+        bool any = false;
+        for (int it = 0; it < n_it && !*abort_flag; ++it) {
+            const int s = it % C_::STAGES;
+            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+            const int c = it / (3 * kpc), r = it % (3 * kpc);
+            const int t = r / kpc, kbi = r % kpc;
+            if (kbi == 0 && c > 0 &&
+                !mbar_wait_cluster(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag, spin)) {
+                raise_abort_pair(abort_flag, peer_abort, p.err);
+                break;
+            }
+            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin) ||
+                !mbar_wait_cluster(smem_u32(&pfull_bar[s]), ph, abort_flag, spin)) {
+                raise_abort_pair(abort_flag, peer_abort, p.err);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + s * C_::STAGE_BYTES);
+            const uint32_t sb = sa + C_::STAGE_A;
+            const uint32_t d = tmem + (uint32_t)(t * TN);
+#pragma unroll
+            for (int q = 0; q < C_::NPAIRS; ++q) {
+                const int pa = KIND == 0 ? kPairsBF16[q][0] : kPairs2[q][0];
+                const int pb = KIND == 0 ? kPairsBF16[q][1] : kPairs2[q][1];
+#pragma unroll
+                for (int j = 0; j < C_::KSTEPS; ++j) {
+                    const uint64_t ad = smem_desc<128>(sa + pa * C_::A_PART + j * 32);
+                    const uint64_t bd = smem_desc<128>(sb + pb * C_::B_PART + j * 32);
+                    mma2<KIND>(d, ad, bd, idesc, (kbi > 0 || q > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            any = true;
+            mma_commit2_both(smem_u32(&empty_bar[s]));
+            if (kbi == kpc - 1) mma_commit2_both(smem_u32(&tfull[t]));
+        }
+        if (*abort_flag && any) {
+            mma_commit2_local(smem_u32(&drain_bar));
+            for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&drain_bar), 0); ++i) {
+            }
+        }
+    } else if (warp < EPI_WARPS) {
+        // ---------------- epilogue (both CTAs): own 128 rows, chunk partials -> FP32 registers -> C
+        const int g = warp & 3, h = warp >> 2;
+        float cr[64], ci[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            cr[j] = 0.f;
+            ci[j] = 0.f;
+        }
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                int w = 0;
+                if (lane == 0) w = mbar_wait(smem_u32(&tfull[t]), (uint32_t)c & 1u, abort_flag, spin) ? 1 : 0;
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(t * TN + 64 * h + 32 * half), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = 32 * half + j;
+                        if (t == 0) {
+                            cr[col] += v[j];
+                            ci[col] -= v[j];
+                        } else if (t == 1) {
+                            cr[col] -= v[j];
+                            ci[col] -= v[j];
+                        } else {
+                            ci[col] += v[j];
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(map_rank(smem_u32(&tfree[t]), 0));
+            }
+        }
+        if (!ok) {
+            if (lane == 0 && !abort_sh) raise_abort_pair(abort_flag, peer_abort, p.err);
+        } else {
+            const int row = 32 * g + lane;
+            const int64_t ld = p.c_ld ? p.c_ld : N;
+            float4* dst = reinterpret_cast<float4*>(p.C + (int64_t)z * p.c_batch_stride +
+                                                    (int64_t)(m0 + row) * ld + n0 + 64 * h);
+#pragma unroll
+            for (int j = 0; j < 64; j += 2) dst[j / 2] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    cluster_sync_all();  // no CTA leaves while the other may still signal it or use the pair's TMEM
+    if (warp == MMA_WARP) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
 // ------------------------------------------------------------ operand split
 
 __device__ __forceinline__ int64_t slice_offset(const Operand& op, int64_t s) {
@@ -480,9 +822,9 @@ EncodeFn encoder() {
     return fn;
 }
 
-// 4D map over planes [batch][3*PARTS][rows][K]; box = (BK, 128, PARTS, 1).
+// 4D map over planes [batch][3*PARTS][rows][K]; box = (BK, box_rows, PARTS, 1).
 template <int KIND, int ROWB>
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int batch) {
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int batch, int box_rows = 128) {
     using C_ = Cfg<KIND, ROWB>;
     EncodeFn enc = encoder();
     if (!enc) return false;
@@ -490,7 +832,7 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int b
     cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Q, (cuuint64_t)batch};
     cuuint64_t strides[3] = {(cuuint64_t)(K * C_::ELEM), (cuuint64_t)(rows * K * C_::ELEM),
                              (cuuint64_t)(Q * rows * K * C_::ELEM)};
-    cuuint32_t box[4] = {(cuuint32_t)C_::BK, 128u, (cuuint32_t)C_::PARTS, 1u};  // BK * ELEM = ROWB bytes
+    cuuint32_t box[4] = {(cuuint32_t)C_::BK, (cuuint32_t)box_rows, (cuuint32_t)C_::PARTS, 1u};  // BK * ELEM = ROWB bytes
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(map, KIND == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -524,14 +866,43 @@ cudaError_t launch_tc_impl(const TcGemmParams& p, const void* planesA, const voi
 }
 
 template <int KIND>
+cudaError_t launch_tc2_impl(const TcGemmParams& p, const void* planesA, const void* planesB, int batch,
+                            cudaStream_t s) {
+    using C_ = Cfg2<KIND>;
+    const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
+    if (K % C_::BK || M % (2 * TM) || N % TN) return cudaErrorInvalidValue;
+    CUtensorMap ta, tb;
+    if (!make_map<KIND, 128>(&ta, planesA, M, K, batch, TM) ||
+        !make_map<KIND, 128>(&tb, planesB, N, K, batch, TN / 2))
+        return cudaErrorInvalidValue;
+    const int smem = C_::STAGES * C_::STAGE_BYTES + 1024;
+    static_assert(C_::STAGES >= 2 && C_::STAGES * C_::STAGE_BYTES + 1024 <= 227 * 1024, "shared memory");
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc2<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t ctas = 2 * (M / (2 * TM)) * (N / TN);  // two CTAs (one cluster) per 256x128 tile
+    k_cgemm_tc2<KIND><<<dim3((unsigned)ctas, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
+    return cudaGetLastError();
+}
+
+template <int KIND>
 cudaError_t launch_tc_rows(const TcGemmParams& p, const void* pa, const void* pb, int batch, cudaStream_t s) {
     // 128-byte rows need K to span whole 128-byte k-blocks
     const int64_t K = 1ll << p.kb;
+    if (tc_uses_pair(p)) return launch_tc2_impl<KIND>(p, pa, pb, batch, s);
     if (p.row_bytes == 128 && K % Cfg<KIND, 128>::BK == 0) return launch_tc_impl<KIND, 128>(p, pa, pb, batch, s);
     return launch_tc_impl<KIND, 64>(p, pa, pb, batch, s);
 }
 
 }  // namespace
+
+// CTA pairs need 256-row tiles and K >= 64 (whole 128-byte k-blocks in every mode)
+bool tc_uses_pair(const TcGemmParams& p) {
+    return p.pair && p.row_bytes == 128 && p.mb >= 8 && p.kb >= 6;
+}
 
 // tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts)
 static int kind_of(int mode) { return mode == 1 ? 1 : (mode == 2 ? 0 : 2); }

@@ -50,7 +50,7 @@ constexpr int64_t kAlign = 256;
 int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Kernel chosen for a contraction node.
-enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4 };
+enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_TC2 = 5 };
 
 // Tensor-core eligibility of a non-root node in a split mode: both output
 // sides span whole 128-wide tiles and K spans whole 64-wide k-blocks.
@@ -59,7 +59,8 @@ bool tc_node(int mode, int mb, int nb, int kb, bool is_root) {
 }
 
 // Autotuned kernel choice per (mode, log2 M, log2 N, log2 K): 0 = FP32 CUDA
-// cores, 64 / 128 = tensor cores with that row width. Filled by
+// cores, 64 / 128 = tensor cores with that row width, 256 = tensor cores with
+// 128-byte rows on CTA pairs (2-SM MMA, 256x128 tiles). Filled by
 // tnc_autotune; shared by every network of the process.
 std::map<std::tuple<int, int, int, int>, int>& tune_table() {
     static std::map<std::tuple<int, int, int, int>, int> t;
@@ -162,6 +163,7 @@ struct tnc_net {
     // tensor-core tile options (tnc_set_option)
     int tc_row_bytes = 128;
     int tc_group_m = 1;
+    int tc_pair = 0;             // untuned default: 128-byte rows on CTA pairs where M >= 256
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
@@ -209,7 +211,7 @@ int shape_choice(const tnc_net* net, int mode, int mb, int nb, int kb, bool is_r
     if (net->force_choice >= 0) return net->force_choice;
     auto it = tune_table().find(std::make_tuple(mode, mb, nb, kb));
     if (it != tune_table().end()) return it->second;
-    return net->tc_row_bytes;
+    return net->tc_row_bytes == 128 && net->tc_pair ? 256 : net->tc_row_bytes;
 }
 
 // ------------------------------------------------------------- planning ----
@@ -659,11 +661,13 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tp.c_batch_stride = g.c_batch_stride;
             tp.c_ld = N;
             tp.err = net->d_err;
-            tp.row_bytes = row_bytes;
+            tp.row_bytes = row_bytes == 256 ? 128 : row_bytes;
+            tp.pair = row_bytes == 256 ? 1 : 0;
             tp.group_m = net->tc_group_m;
             tp.spin_limit = net->tc_spin_limit;
             tp.test_stall = net->tc_test_stall;
-            CUDA_TRY(timed_begin(net, node, K_TC, b, s, std::ldexp(1.0, mbp + nbp + g.kb) * b));
+            CUDA_TRY(timed_begin(net, node, tnc::tc_uses_pair(tp) ? K_TC2 : K_TC, b, s,
+                                 std::ldexp(1.0, mbp + nbp + g.kb) * b));
             CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
             CUDA_TRY(timed_end(net, s));
         }
@@ -1631,11 +1635,12 @@ tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
     const int R = 1 << net->plan.obits;
     double* out = nullptr;
     CUDA_TRY(cudaMalloc(&out, (size_t)R * 16));
-    const int variants[3] = {0, 128, 64};
-    std::map<int, double> t[3];  // per node: milliseconds of all its launches
+    constexpr int NV = 4;
+    const int variants[NV] = {0, 256, 128, 64};
+    std::map<int, double> t[NV];  // per node: milliseconds of all its launches
     const bool timing = net->timing;
     net->tuning = true;
-    for (int vi = 0; vi < 3 && st == TNC_OK; ++vi) {
+    for (int vi = 0; vi < NV && st == TNC_OK; ++vi) {
         net->force_choice = variants[vi];
         for (int rep = 0; rep < 2 && st == TNC_OK; ++rep) {  // the first run warms up
             net->timing = true;
@@ -1657,15 +1662,15 @@ tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
     net->timed.clear();
     cudaFree(out);
     if (st != TNC_OK) return st;
-    std::map<std::tuple<int, int, int, int>, std::array<double, 3>> by_shape;
+    std::map<std::tuple<int, int, int, int>, std::array<double, NV>> by_shape;
     for (const NodePlan& np : net->plan.nodes) {
         if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) continue;
         auto& acc = by_shape[std::make_tuple(mode, np.mb, np.nb, np.kb)];
-        for (int vi = 0; vi < 3; ++vi) acc[vi] += t[vi][np.v];
+        for (int vi = 0; vi < NV; ++vi) acc[vi] += t[vi][np.v];
     }
     for (auto& kv : by_shape) {
         int best = 0;
-        for (int vi = 1; vi < 3; ++vi)
+        for (int vi = 1; vi < NV; ++vi)
             if (kv.second[vi] < kv.second[best]) best = vi;
         tune_table()[kv.first] = variants[best];
     }
@@ -1708,6 +1713,9 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     if (k == "tc_row_bytes") {
         if (value != 64 && value != 128) return fail(TNC_E_INVALID, "tc_row_bytes must be 64 or 128");
         net->tc_row_bytes = (int)value;
+    } else if (k == "tc_pair") {
+        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "tc_pair must be 0 or 1");
+        net->tc_pair = (int)value;
     } else if (k == "tc_group_m") {
         if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");
         net->tc_group_m = (int)value;

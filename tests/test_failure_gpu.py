@@ -16,12 +16,17 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_wait_timeout_reports_and_recovers(libtnc):
+@pytest.mark.parametrize("mb", [7, 8])
+def test_bounded_wait_timeout_reports_and_recovers(libtnc, mb):
+    """mb = 7: one 128x128 tile on one CTA; mb = 8: one 256x128 tile on a
+    CTA pair, where the leader's MMA wait runs out and raises the abort flag
+    of both CTAs."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2205_00393_gb300 import Network, TNCError
-    net_ref = _three_leaf(7, 7, 7, 6, False)  # one 128x128 tile, one CTA
+    net_ref = _three_leaf(7, mb, 7, 6, False)
     net = Network.from_tn(net_ref)
+    net.set_option("tc_pair", 1)
     path = [(0, 1), (2, 3)]
     net.set_path(path)
     net.set_option("tc_spin_limit", 1 << 14)
