@@ -32,13 +32,13 @@ if ROOT not in sys.path:
 METRIC = "sliced contraction complex TFLOPS & s/1024 slices, split-TC vs FP32 at rel err≤1e-4"
 UNIT = "TFLOPS (complex, effective 8*M*N*K per node)"
 WORKLOAD = dict(rows=5, cols=6, cycles=14, seed=2, n_open=6, target_log2=27, sa_seed=7)
-MODES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x2": 3}
+MODES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x2": 3, "fp16x2": 4}
 # FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Tensor flops per complex multiply-accumulate of one node (3M: three real
 # products, each summed over the part pairs): BF16 3 parts -> 6 pairs,
 # TF32 2 parts -> 3 pairs, BF16 2 parts -> 3 pairs; 2 flops per real MAC.
-TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 * 2}
+TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 * 2, "fp16x2": 3 * 3 * 2}
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
@@ -262,6 +262,8 @@ def apply_options(net, args):
         net.set_option("tc_group_m", args.tc_group_m)
     if args.tc_pair is not None:
         net.set_option("tc_pair", args.tc_pair)
+    if args.tc_prefetch is not None:
+        net.set_option("tc_prefetch", args.tc_prefetch)
 
 
 def single_node(args):
@@ -297,7 +299,7 @@ def single_node(args):
     by_kind = kernel_breakdown([r for r in recs if r["node"] in (3, -1) and r["kind"] in (3, 4, 0, 5)])
     peaks, peak_src = load_peaks()
     line = {"single_node": [mb, nb, kb], "mode": args.mode, "tc_row_bytes": args.tc_row_bytes, "tc_group_m": args.tc_group_m,
-            "tc_pair": args.tc_pair, "steps": args.steps,
+            "tc_pair": args.tc_pair, "tc_prefetch": args.tc_prefetch, "steps": args.steps,
             "kernel_ms_per_call": {KIND_NAMES[k]: v["ms"] / args.steps for k, v in by_kind.items()},
             "roofline": roofline_of(by_kind, args.mode, peaks, peak_src, sustained=False),
             "gpu_launches": n_launches}
@@ -523,6 +525,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
+    ap.add_argument("--tc-prefetch", type=int, default=None,
+                    help="L2 prefetch distance (stages) of the tensor-core producer (library default 0)")
     ap.add_argument("--tc-pair", type=int, default=None, choices=(0, 1),
                     help="tensor-core GEMMs on CTA pairs (2-SM MMA) where eligible (library default 1)")
     ap.add_argument("--grad42", action="store_true",
@@ -657,7 +661,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "c64-fp32", "bf16": "c64 via 3x bf16 split, fp32 accum",
                   "tf32": "c64 via 2x tf32 split, fp32 accum",
-                  "bf16x2": "c64 via 2x bf16 split, fp32 accum"}[args.mode],
+                  "bf16x2": "c64 via 2x bf16 split, fp32 accum",
+                  "fp16x2": "c64 via 2x fp16 split of the 2^e-scaled operand, fp32 accum"}[args.mode],
         "data": "synthetic",
         "s_per_1024_slices": T / n_sl_tot * 1024 * world if world > 1 else T / n_sl_tot * 1024,
         "config": {"workload": workload_name(), "mode": args.mode, "slices_per_step": B,

@@ -54,7 +54,9 @@ typedef enum {
     TNC_FP32 = 0,        /* complex64 on FP32 CUDA cores (4 real FMAs per complex MAC)     */
     TNC_SPLIT_TF32 = 1,  /* x = hi + lo in TF32, 3 products, tcgen05 kind::tf32, FP32 accum */
     TNC_SPLIT_BF16 = 2,  /* x = x0 + x1 + x2 in BF16, 6 products, tcgen05 kind::f16, FP32   */
-    TNC_SPLIT_BF16X2 = 3 /* x = x0 + x1 in BF16, 3 products (cheaper, lower accuracy)       */
+    TNC_SPLIT_BF16X2 = 3, /* x = x0 + x1 in BF16, 3 products (cheaper, lower accuracy)      */
+    TNC_SPLIT_FP16X2 = 4  /* 2^e x = x0 + x1 in FP16, 3 products, kind::f16, FP32 accum; e per
+                             operand (and slice) puts max |Re|, |Im| in [2^13, 2^14)         */
 } tnc_mode;
 
 /* Build a network (Sec. 2.1.1: G = (V, E, w)).
@@ -207,6 +209,9 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  run on CTA pairs (a cluster of two CTAs issuing 2-SM MMAs
  *                  on 256x128 output tiles, each CTA holding half of the
  *                  tile's B operand)
+ *  "tc_prefetch"   0..64 (default 0): when issuing the loads of pipeline stage
+ *                  i, the single-CTA tensor-core producer also prefetches the
+ *                  tiles of stage i + value into L2 (0: no prefetch)
  *  "tc_group_m"    1..64 (default 1): output row tiles per rasterisation
  *                  group (consecutive CTAs sweep all column tiles of a group)
  *  "backward_keep_every" 0 (default) or 1..64: the adjoint pass keeps the

@@ -6,8 +6,8 @@ device memory and streams. There is no CPU fallback: if the library is
 missing, importing the binding raises.
 """
 
-from ._lib import (Network, TNCError, FP32, SPLIT_TF32, SPLIT_BF16, SPLIT_BF16X2, contract_many, tune_table, lib_path,
+from ._lib import (Network, TNCError, FP32, SPLIT_TF32, SPLIT_BF16, SPLIT_BF16X2, SPLIT_FP16X2, contract_many, tune_table, lib_path,
                    load_library)
 
-__all__ = ["Network", "TNCError", "contract_many", "tune_table", "FP32", "SPLIT_TF32", "SPLIT_BF16", "SPLIT_BF16X2",
+__all__ = ["Network", "TNCError", "contract_many", "tune_table", "FP32", "SPLIT_TF32", "SPLIT_BF16", "SPLIT_BF16X2", "SPLIT_FP16X2",
            "lib_path", "load_library"]

@@ -12,7 +12,7 @@ import os
 
 import numpy as np
 
-FP32, SPLIT_TF32, SPLIT_BF16, SPLIT_BF16X2 = 0, 1, 2, 3
+FP32, SPLIT_TF32, SPLIT_BF16, SPLIT_BF16X2, SPLIT_FP16X2 = 0, 1, 2, 3, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None

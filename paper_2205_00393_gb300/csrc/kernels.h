@@ -77,6 +77,7 @@ struct SplitParams {
     int64_t rs[kMaxBits], ks[kMaxBits];
     int64_t slice0;
     void* dst;
+    uint32_t* amax;  // split FP16x2: per batch entry, bits of max |Re|, |Im| (written by launch_split)
 };
 
 struct TcGemmParams {
@@ -90,6 +91,9 @@ struct TcGemmParams {
     uint32_t spin_limit;  // polls before a bounded wait gives up
     int test_stall;       // tests only: the producer issues no loads, so waits run out
     int pair;             // 1: 256x128 tiles on CTA pairs (2-SM MMA) where M >= 256 and rows are 128 B
+    const uint32_t* amax_a;  // split FP16x2: the operands' scale words (SplitParams::amax), else null
+    const uint32_t* amax_b;
+    int prefetch;            // > 0: the producer also prefetches the tiles of stage it + prefetch into L2
 };
 
 int tc_plane_count(int mode);

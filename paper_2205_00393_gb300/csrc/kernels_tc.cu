@@ -25,6 +25,7 @@
 // its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstring>
 
@@ -40,8 +41,9 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kErrTimeout = 4;
 
 // KIND 0: three BF16 parts (6 pairs), kind::f16; 1: two TF32 parts (3 pairs),
-// kind::tf32; 2: two BF16 parts (3 pairs), kind::f16. ROWB: bytes of K per
-// tile row and k-block, which is also the swizzle width (64 or 128).
+// kind::tf32; 2: two BF16 parts (3 pairs), kind::f16; 3: two FP16 parts of
+// the operand scaled by a power of two (3 pairs), kind::f16. ROWB: bytes of K
+// per tile row and k-block, which is also the swizzle width (64 or 128).
 template <int KIND, int ROWB> struct Cfg {
     static constexpr int PARTS = KIND == 0 ? 3 : 2;
     static constexpr int NPAIRS = KIND == 0 ? 6 : 3;
@@ -52,6 +54,20 @@ template <int KIND, int ROWB> struct Cfg {
     static constexpr int STAGES = SMEM_PIPE / STAGE_BYTES;
     static constexpr int KSTEPS = ROWB / 32;                   // MMAs per k-block (32 bytes of K each)
 };
+
+// Split FP16x2 operand scale. With m = max |Re|, |Im| of the operand, the
+// scale 2^e puts m * 2^e in [2^13, 2^14), so Re + Im (at most 2m) stays below
+// the FP16 maximum; x = x0 + x1 carries 22 significant bits wherever x1 is a
+// normal FP16 (|x| >= m 2^-16), and below that an absolute error under
+// m 2^-38 (half the FP16 subnormal spacing after scaling). e is clamped to
+// [-126, 126] so that 2^e and 2^-e are normal floats.
+__host__ __device__ __forceinline__ int fp16_scale_exp(uint32_t amax_bits) {
+    if (amax_bits == 0) return 0;
+    const int e = 140 - (int)((amax_bits >> 23) & 0xFFu);
+    return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -96,6 +112,14 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// L2 prefetch of one tensor-map box (a hint: no completion, no shared memory).
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, ROWB-byte swizzle (layout type
 // 2 = 128B, 4 = 64B), 8-row groups 8*ROWB bytes apart, descriptor version 1.
 template <int ROWB>
@@ -135,9 +159,15 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
 // both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+// A/B format: kind::f16 0 = F16, 1 = BF16; kind::tf32 2 = TF32.
+template <int KIND>
+__host__ __device__ constexpr uint32_t ab_format() {
+    return KIND == 1 ? 2u : (KIND == 3 ? 0u : 1u);
+}
+
 template <int KIND>
 __host__ __device__ constexpr uint32_t instr_desc() {
-    return (1u << 4) | ((KIND == 1 ? 2u : 1u) << 7) | ((KIND == 1 ? 2u : 1u) << 10) |
+    return (1u << 4) | (ab_format<KIND>() << 7) | (ab_format<KIND>() << 10) |
            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
@@ -251,6 +281,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, z, fb);
             tma_load_4d(sa + STAGE_A, &tmB, kb * C_::BK, n0, t * C_::PARTS, z, fb);
             issued = it + 1;
+            if (p.prefetch > 0 && it + p.prefetch < n_it) {  // the tiles of a later stage into L2
+                const int ip = it + p.prefetch;
+                const int cp = ip / (3 * kpc), rp = ip % (3 * kpc);
+                const int tp = rp / kpc, kbp = cp * kpc + rp % kpc;
+                tma_prefetch_4d(&tmA, kbp * C_::BK, m0, tp * C_::PARTS, z);
+                tma_prefetch_4d(&tmB, kbp * C_::BK, n0, tp * C_::PARTS, z);
+            }
         }
         if (*abort_flag) {
             // drain: wait (bounded) for every load that may still be in flight
@@ -361,6 +398,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int64_t ld = p.c_ld ? p.c_ld : N;
             float4* dst = reinterpret_cast<float4*>(p.C + (int64_t)z * p.c_batch_stride +
                                                     (int64_t)(m0 + row) * ld + n0 + 64 * h);
+            if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
+                const float sa = pow2f(-fp16_scale_exp(p.amax_a[z])), sb = pow2f(-fp16_scale_exp(p.amax_b[z]));
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    cr[j] = cr[j] * sa * sb;
+                    ci[j] = ci[j] * sa * sb;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 64; j += 2) dst[j / 2] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
         }
@@ -491,7 +536,7 @@ __device__ __forceinline__ void mma_commit2_local(uint32_t bar) {
 // Instruction descriptor of the 2-SM MMA: M = 256 (128 rows per CTA), N = 128.
 template <int KIND>
 __host__ __device__ constexpr uint32_t instr_desc2() {
-    return (1u << 4) | ((KIND == 1 ? 2u : 1u) << 7) | ((KIND == 1 ? 2u : 1u) << 10) |
+    return (1u << 4) | (ab_format<KIND>() << 7) | (ab_format<KIND>() << 10) |
            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
 }
 
@@ -702,6 +747,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             const int64_t ld = p.c_ld ? p.c_ld : N;
             float4* dst = reinterpret_cast<float4*>(p.C + (int64_t)z * p.c_batch_stride +
                                                     (int64_t)(m0 + row) * ld + n0 + 64 * h);
+            if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
+                const float sa = pow2f(-fp16_scale_exp(p.amax_a[z])), sb = pow2f(-fp16_scale_exp(p.amax_b[z]));
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    cr[j] = cr[j] * sa * sb;
+                    ci[j] = ci[j] * sa * sb;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 64; j += 2) dst[j / 2] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
         }
@@ -775,12 +828,28 @@ __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ S
         int e = tid + i * 256;
         int kp = e % (SK / 2), rr = e / (SK / 2);
         float2 x0 = tile[rr * LD + 2 * kp], x1 = tile[rr * LD + 2 * kp + 1];
+        if constexpr (KIND == 3) {  // operand scale 2^e (exact)
+            const float sc = pow2f(fp16_scale_exp(p.amax[z]));
+            x0.x *= sc;
+            x0.y *= sc;
+            x1.x *= sc;
+            x1.y *= sc;
+        }
         float v0[3] = {x0.x, x0.y, x0.x + x0.y};
         float v1[3] = {x1.x, x1.y, x1.x + x1.y};
         const int64_t idx = (r0 + rr) * K + k0 + 2 * kp;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            if constexpr (KIND != 1) {
+            if constexpr (KIND == 3) {
+                float a = v0[t], b = v1[t];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    __half2 pr = __halves2half2(__float2half_rn(a), __float2half_rn(b));
+                    reinterpret_cast<__half2*>(out + ((t * 2 + q) * plane + idx) * 2)[0] = pr;
+                    a -= __low2float(pr);
+                    b -= __high2float(pr);
+                }
+            } else if constexpr (KIND != 1) {
                 float a = v0[t], b = v1[t];
 #pragma unroll
                 for (int q = 0; q < C_::PARTS; ++q) {
@@ -801,6 +870,38 @@ __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ S
             }
         }
     }
+}
+
+// Split FP16x2: max of |Re| and |Im| over the operand of each batch entry (the
+// split kernel's tiles and gather), as float bits (non-negative floats order
+// like their bits). amax must be zeroed first.
+__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ SplitParams p) {
+    __shared__ int64_t roff[64], koff[64];
+    const int64_t K = 1ll << p.kb;
+    const int SK = K >= 64 ? 64 : (int)K;
+    const int SR = SPLIT_TILE / SK;
+    const int64_t tiles_k = K / SK;
+    const int64_t r0 = (blockIdx.x / tiles_k) * SR, k0 = (blockIdx.x % tiles_k) * SK;
+    const int z = blockIdx.z;
+    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, p.slice0 + z);
+    const int tid = threadIdx.x;
+    if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
+    else if (tid >= 64 && tid < 64 + SK) koff[tid - 64] = bits_offset(k0 + tid - 64, p.ks, p.kb, 0);
+    __syncthreads();
+    const bool kfast = p.kb > 0 && p.ks[0] == 1;
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < SPLIT_TILE / 256; ++i) {
+        int e = tid + i * 256;
+        int rr, kk;
+        if (kfast) { kk = e % SK; rr = e / SK; }
+        else { rr = e % SR; kk = e / SR; }
+        const float2 v = src[roff[rr] + koff[kk]];
+        const uint32_t a = __float_as_uint(fabsf(v.x)), b = __float_as_uint(fabsf(v.y));
+        m = max(m, max(a, b));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((tid & 31) == 0) atomicMax(p.amax + z, m);
 }
 
 // ------------------------------------------------------------ host helpers
@@ -834,7 +935,10 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int b
                              (cuuint64_t)(Q * rows * K * C_::ELEM)};
     cuuint32_t box[4] = {(cuuint32_t)C_::BK, (cuuint32_t)box_rows, (cuuint32_t)C_::PARTS, 1u};  // BK * ELEM = ROWB bytes
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = enc(map, KIND == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+    const CUtensorMapDataType dt = KIND == 1   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : KIND == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(map, dt, 4,
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      ROWB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -904,8 +1008,9 @@ bool tc_uses_pair(const TcGemmParams& p) {
     return p.pair && p.row_bytes == 128 && p.mb >= 8 && p.kb >= 6;
 }
 
-// tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts)
-static int kind_of(int mode) { return mode == 1 ? 1 : (mode == 2 ? 0 : 2); }
+// tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts),
+// 4 scaled FP16 (2 parts)
+static int kind_of(int mode) { return mode == 1 ? 1 : (mode == 2 ? 0 : (mode == 4 ? 3 : 2)); }
 
 int tc_plane_count(int mode) { return mode == 2 ? 9 : 6; }
 int tc_elem_bytes(int mode) { return mode == 1 ? 4 : 2; }
@@ -921,6 +1026,14 @@ cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t
     switch (kind_of(mode)) {
         case 0: k_split_operand<0><<<grid, 256, 0, s>>>(p); break;
         case 1: k_split_operand<1><<<grid, 256, 0, s>>>(p); break;
+        case 3: {
+            if (!p.amax) return cudaErrorInvalidValue;
+            cudaError_t e = cudaMemsetAsync(p.amax, 0, sizeof(uint32_t) * (size_t)batch, s);
+            if (e != cudaSuccess) return e;
+            k_absmax<<<grid, 256, 0, s>>>(p);
+            k_split_operand<3><<<grid, 256, 0, s>>>(p);
+            break;
+        }
         default: k_split_operand<2><<<grid, 256, 0, s>>>(p); break;
     }
     return cudaGetLastError();
@@ -933,6 +1046,9 @@ cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA
     switch (kind_of(mode)) {
         case 0: return launch_tc_rows<0>(p, planesA, planesB, batch, s);
         case 1: return launch_tc_rows<1>(p, planesA, planesB, batch, s);
+        case 3:
+            if (!p.amax_a || !p.amax_b) return cudaErrorInvalidValue;
+            return launch_tc_rows<3>(p, planesA, planesB, batch, s);
         default: return launch_tc_rows<2>(p, planesA, planesB, batch, s);
     }
 }

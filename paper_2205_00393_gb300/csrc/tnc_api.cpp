@@ -164,6 +164,7 @@ struct tnc_net {
     int tc_row_bytes = 128;
     int tc_group_m = 1;
     int tc_pair = 0;             // untuned default: 128-byte rows on CTA pairs where M >= 256
+    int tc_prefetch = 0;         // L2 prefetch distance of the tensor-core producer, in stages
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
@@ -342,8 +343,15 @@ std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice);
 // Split-precision planes of one operand are capped (tc_plane_cap_log2, 2^32
 // bytes by default): a larger operand is processed in panels of its rows
 // (whole 128-row tiles, top row bits fixed).
-int64_t full_planes_bytes(int mode, int rb, int kb, int64_t batch) {
+// Plane data of one operand; split FP16x2 keeps the operand's scale words
+// (one uint32 per batch entry) after it.
+int64_t plane_data_bytes(int mode, int rb, int kb, int64_t batch) {
     return batch * (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode) << (rb + kb);
+}
+
+int64_t full_planes_bytes(int mode, int rb, int kb, int64_t batch) {
+    const int64_t scale_words = mode == TNC_SPLIT_FP16X2 ? (batch * 4 + 255) / 256 * 256 : 0;
+    return plane_data_bytes(mode, rb, kb, batch) + scale_words;
 }
 
 // Panel bits p (2^p panels) so that one panel's planes fit the cap.
@@ -633,6 +641,8 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
         for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.bk[j];
         sp.slice0 = g.slice0;
         sp.dst = pb;
+        if (mode == TNC_SPLIT_FP16X2)
+            sp.amax = reinterpret_cast<uint32_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, g.kb, b));
         CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
         CUDA_TRY(tnc::launch_split(sp, mode, b, s));
         CUDA_TRY(timed_end(net, s));
@@ -649,6 +659,9 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
                 for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.ak[j];
                 sp.slice0 = g.slice0;
                 sp.dst = pa;
+                if (mode == TNC_SPLIT_FP16X2)
+                    sp.amax =
+                        reinterpret_cast<uint32_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, g.kb, b));
                 CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
                 CUDA_TRY(tnc::launch_split(sp, mode, b, s));
                 CUDA_TRY(timed_end(net, s));
@@ -663,6 +676,13 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tp.err = net->d_err;
             tp.row_bytes = row_bytes == 256 ? 128 : row_bytes;
             tp.pair = row_bytes == 256 ? 1 : 0;
+            tp.prefetch = net->tc_prefetch;
+            if (mode == TNC_SPLIT_FP16X2) {
+                tp.amax_a = reinterpret_cast<const uint32_t*>(static_cast<const char*>(pa) +
+                                                              plane_data_bytes(mode, mbp, g.kb, b));
+                tp.amax_b = reinterpret_cast<const uint32_t*>(static_cast<const char*>(pb) +
+                                                              plane_data_bytes(mode, nbp, g.kb, b));
+            }
             tp.group_m = net->tc_group_m;
             tp.spin_limit = net->tc_spin_limit;
             tp.test_stall = net->tc_test_stall;
@@ -1504,7 +1524,7 @@ tnc_status tnc_workspace_bytes(tnc_net_t net, int64_t max_batch, size_t* bytes) 
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
     size_t b = 0;
-    for (int mode = TNC_FP32; mode <= TNC_SPLIT_BF16X2; ++mode)
+    for (int mode = TNC_FP32; mode <= TNC_SPLIT_FP16X2; ++mode)
         b = std::max(b, (size_t)plan_arena(net, max_batch, mode).peak);
     *bytes = b;
     return TNC_OK;
@@ -1522,8 +1542,7 @@ tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes) {
 tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double* out_c128, void* stream) {
     if (!net) return fail(TNC_E_INVALID, "NULL network");
     if (!out_c128) return fail(TNC_E_INVALID, "NULL output");
-    if (mode != TNC_FP32 && mode != TNC_SPLIT_TF32 && mode != TNC_SPLIT_BF16 && mode != TNC_SPLIT_BF16X2)
-        return fail(TNC_E_INVALID, "unknown mode");
+    if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
     const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
@@ -1716,6 +1735,9 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "tc_pair") {
         if (value != 0 && value != 1) return fail(TNC_E_INVALID, "tc_pair must be 0 or 1");
         net->tc_pair = (int)value;
+    } else if (k == "tc_prefetch") {
+        if (value < 0 || value > 64) return fail(TNC_E_INVALID, "tc_prefetch must be in [0, 64]");
+        net->tc_prefetch = (int)value;
     } else if (k == "tc_group_m") {
         if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");
         net->tc_group_m = (int)value;
@@ -1773,7 +1795,7 @@ tnc_status tnc_contract_backward(tnc_net_t net, int64_t lo, int64_t hi, int mode
                                  void* stream) {
     if (!net) return fail(TNC_E_INVALID, "NULL network");
     if (!grad_out_c128 || !grad_leaves_c64) return fail(TNC_E_INVALID, "NULL gradient buffer");
-    if (mode < TNC_FP32 || mode > TNC_SPLIT_BF16X2) return fail(TNC_E_INVALID, "unknown mode");
+    if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
     const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
@@ -1888,7 +1910,7 @@ tnc_status tnc_param_grads(tnc_net_t net, int n_params, const int* leaf_ids, con
 tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_lo, const int64_t* slice_hi,
                              int mode, double* const* outs_c128, int use_graph, void* stream) {
     if (n < 1 || !nets || !slice_lo || !slice_hi || !outs_c128) return fail(TNC_E_INVALID, "bad argument");
-    if (mode < TNC_FP32 || mode > TNC_SPLIT_BF16X2) return fail(TNC_E_INVALID, "unknown mode");
+    if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
     cudaStream_t s = (cudaStream_t)stream;
     std::ostringstream key;
     key << mode << ":" << use_graph << ":" << (uintptr_t)s;

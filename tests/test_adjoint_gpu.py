@@ -137,7 +137,7 @@ def test_backward_budget_too_small(lib):
     assert e.value.status == 2
 
 
-@pytest.mark.parametrize("mode", [2, 1])
+@pytest.mark.parametrize("mode", [2, 1, 4])
 def test_tensor_core_environments(lib, mode):
     """Environment contractions large enough for the tensor cores: split
     precision must agree with the FP32 environments, and F is linear in every

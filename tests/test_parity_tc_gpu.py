@@ -1,5 +1,6 @@
 """GPU parity of the split-precision tensor-core path (tcgen05) against the
-FP64 oracle. Split BF16 (3 parts, 6 products) and split TF32 (2 parts, 3
+FP64 oracle. Split BF16 (3 parts, 6 products), split TF32 (2 parts, 3
+products) and split FP16x2 (2 FP16 parts of the power-of-2-scaled operand, 3
 products) must match within 1e-4 relative per amplitude; the cheaper 2-part
 BF16 variant is reported and held to 1e-3."""
 
@@ -14,7 +15,7 @@ from ._util import floored_rel_err
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 1e-4, 2: 1e-4, 3: 1e-3}
+TOL = {1: 1e-4, 2: 1e-4, 3: 1e-3, 4: 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +49,7 @@ def _three_leaf(seed, mb, nb, kb, permuted):
                          tuple(m_ids + o_ids), [-1, -1, -1])
 
 
-@pytest.mark.parametrize("mode", [2, 1, 3])
+@pytest.mark.parametrize("mode", [2, 1, 3, 4])
 @pytest.mark.parametrize("mb,nb,kb,permuted", [(7, 7, 6, False), (8, 9, 7, True), (9, 8, 10, False), (8, 7, 5, True)])
 def test_tc_node_vs_oracle(lib, mode, mb, nb, kb, permuted):
     from paper_2205_00393_gb300 import Network
@@ -69,7 +70,7 @@ def test_tc_node_vs_oracle(lib, mode, mb, nb, kb, permuted):
     assert floored_rel_err(fp32, ref, 0) <= 1e-5
 
 
-@pytest.mark.parametrize("mode", [2, 1])
+@pytest.mark.parametrize("mode", [2, 1, 4])
 def test_c2_one_slice_split(lib, mode):
     from paper_2205_00393_gb300 import Network
     c = grid_rqc(5, 6, 14, 2, n_open=6)
@@ -121,7 +122,7 @@ def _tc_kinds(net, mode):
     return out, {r["kind"] for r in recs}
 
 
-@pytest.mark.parametrize("mode", [2, 1, 3])
+@pytest.mark.parametrize("mode", [2, 1, 3, 4])
 @pytest.mark.parametrize("mb,nb,kb,permuted", [(8, 8, 6, True), (9, 8, 10, False), (10, 9, 12, True)])
 def test_cta_pair_vs_single_cta(lib, mode, mb, nb, kb, permuted):
     """256x128 tiles on CTA pairs (2-SM MMA, kind 5) against 128x128 tiles on
@@ -177,3 +178,31 @@ def test_cta_pair_batched_slices(lib, mode):
     net.set_option("tc_pair", 0)
     single = net.contract(lo, hi, mode).cpu().numpy()
     assert float(np.max(np.abs(got - single)) / np.max(np.abs(single))) <= 1e-6
+
+
+@pytest.mark.parametrize("scale_a,scale_b", [(-70, 50), (60, -90), (0, 0)])
+def test_fp16x2_operand_scaling(lib, scale_a, scale_b):
+    """Split FP16x2 scales each operand by 2^e so that its largest component
+    lands in [2^13, 2^14): operands of magnitude 2^-70 .. 2^60 (far outside
+    FP16's range) are contracted to the same relative accuracy, and an
+    all-zero operand gives exactly zero."""
+    from paper_2205_00393_gb300 import Network
+    net_ref = _three_leaf(77, 9, 8, 10, True)
+    ts = list(net_ref.tensors)
+    ts[0] = (ts[0] * np.float32(2.0 ** scale_a)).astype(np.complex64)
+    ts[1] = (ts[1] * np.float32(2.0 ** scale_b)).astype(np.complex64)
+    net_ref = net_ref.with_tensors(ts)
+    net = Network.from_tn(net_ref)
+    path = [(0, 1), (2, 3)]
+    net.set_path(path)
+    got = net.contract(0, 1, 4).cpu().numpy()
+    net.check_device()
+    ref = tn.contract(net_ref, path)
+    err = floored_rel_err(got, ref, 0)
+    print("fp16x2 scales 2^%d, 2^%d: err %.3e" % (scale_a, scale_b, err))
+    assert err <= TOL[4]
+    ts[1] = np.zeros_like(ts[1])
+    net.set_tensor_data(1, ts[1])
+    zero = net.contract(0, 1, 4).cpu().numpy()
+    net.check_device()
+    assert np.array_equal(zero, np.zeros_like(zero))
