@@ -42,7 +42,7 @@ TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 *
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
-              4: "k_split_operand", 5: "k_cgemm_tc2", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
+              4: "k_split_operand", 5: "k_cgemm_tc2", 6: "k_cgemm_tc_mc", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
 
 
 def workload_name():
@@ -162,7 +162,7 @@ def kernel_breakdown(recs):
         d = by_kind.setdefault(r["kind"], {"ms": 0.0, "cmacs": 0.0, "launches": 0})
         d["ms"] += r["ms"]
         d["launches"] += 1
-        if r["kind"] in (0, 1, 2, 3, 5):
+        if r["kind"] in (0, 1, 2, 3, 5, 6):
             d["cmacs"] += r["cmacs"]
     return by_kind
 
@@ -173,7 +173,7 @@ def roofline_of(by_kind, mode, peaks, peak_src, sustained):
     d = by_kind[dom]
     share = d["ms"] / sum(v["ms"] for v in by_kind.values())
     sec = d["ms"] / 1e3
-    if dom in (3, 5):
+    if dom in (3, 5, 6):
         bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
         peak = bf16 * (TF32_OVER_BF16 if mode == "tf32" else 1.0)
         achieved = d["cmacs"] * TENSOR_FLOPS_PER_CMAC[mode] / sec / 1e12
@@ -262,8 +262,8 @@ def apply_options(net, args):
         net.set_option("tc_group_m", args.tc_group_m)
     if args.tc_pair is not None:
         net.set_option("tc_pair", args.tc_pair)
-    if args.tc_prefetch is not None:
-        net.set_option("tc_prefetch", args.tc_prefetch)
+    if args.tc_multicast is not None:
+        net.set_option("tc_multicast", args.tc_multicast)
 
 
 def single_node(args):
@@ -296,10 +296,10 @@ def single_node(args):
     net.check_device()
     recs, n_launches = net.last_timings()
     net.set_timing(False)
-    by_kind = kernel_breakdown([r for r in recs if r["node"] in (3, -1) and r["kind"] in (3, 4, 0, 5)])
+    by_kind = kernel_breakdown([r for r in recs if r["node"] in (3, -1) and r["kind"] in (3, 4, 0, 5, 6)])
     peaks, peak_src = load_peaks()
     line = {"single_node": [mb, nb, kb], "mode": args.mode, "tc_row_bytes": args.tc_row_bytes, "tc_group_m": args.tc_group_m,
-            "tc_pair": args.tc_pair, "tc_prefetch": args.tc_prefetch, "steps": args.steps,
+            "tc_pair": args.tc_pair, "tc_multicast": args.tc_multicast, "steps": args.steps,
             "kernel_ms_per_call": {KIND_NAMES[k]: v["ms"] / args.steps for k, v in by_kind.items()},
             "roofline": roofline_of(by_kind, args.mode, peaks, peak_src, sustained=False),
             "gpu_launches": n_launches}
@@ -498,7 +498,7 @@ def backward_bench(args):
     recs, n_launches = net.last_timings()
     net.set_timing(False)
     by_kind = kernel_breakdown(recs)
-    cmacs = sum(v["cmacs"] for k, v in by_kind.items() if k in (0, 3, 5))
+    cmacs = sum(v["cmacs"] for k, v in by_kind.items() if k in (0, 3, 5, 6))
     stats = net.stats()
     line = {"metric": "adjoint pass (forward + environments of all fSim leaves), effective complex TFLOPS",
             "value": 8 * cmacs / T / 1e12, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
@@ -520,13 +520,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnc", choices=["tnc", "reference"])
     ap.add_argument("--mode", default=None, choices=sorted(MODES),
-                    help="arithmetic of the contractions (default bf16; fp32 for --grad42)")
+                    help="arithmetic of the contractions (default fp16x2; bf16 for the single-node, "
+                         "backward and many-circuit modes; fp32 for --grad42)")
+    ap.add_argument("--compare-modes", default="bf16",
+                    help="comma-separated split modes also timed on the same slices in the default run "
+                         "(reported under split_modes; empty to skip)")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
-    ap.add_argument("--tc-prefetch", type=int, default=None,
-                    help="L2 prefetch distance (stages) of the tensor-core producer (library default 0)")
+    ap.add_argument("--tc-multicast", type=int, default=None, choices=(0, 1),
+                    help="tensor-core GEMMs on 2-CTA clusters sharing the A tile by multicast (library default 0)")
     ap.add_argument("--tc-pair", type=int, default=None, choices=(0, 1),
                     help="tensor-core GEMMs on CTA pairs (2-SM MMA) where eligible (library default 1)")
     ap.add_argument("--grad42", action="store_true",
@@ -541,7 +545,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.mode is None:
-        args.mode = "fp32" if args.grad42 else "bf16"
+        if args.grad42:
+            args.mode = "fp32"
+        elif args.single_node or args.backward or args.many or args.impl == "reference":
+            args.mode = "bf16"
+        else:
+            args.mode = "fp16x2"
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -697,6 +706,40 @@ def main():
             f32_flops *= world
         line["fp32_value"] = f32_flops / Tf / 1e12
         line["speedup_vs_fp32"] = line["value"] / line["fp32_value"]
+    others = [m for m in args.compare_modes.split(",") if m and m != args.mode and m != "fp32"]
+    if others:
+        # other split modes on the same slices: value, dominant-kernel roofline, error below
+        line["split_modes"] = {}
+        for m in others:
+            mo = MODES[m]
+            if not args.no_autotune:
+                net.autotune(mo, 0)
+            for i in range(args.warmup):
+                lo, hi = slice_range(i)
+                net.contract(lo, hi, mo, out=out)
+            torch.cuda.synchronize()
+            barrier()
+            net.set_timing(True)
+            ev0.record(stream)
+            m_flops = 0
+            for i in range(args.steps):
+                lo, hi = slice_range(args.warmup + i)
+                net.contract(lo, hi, mo, out=out)
+                m_flops += node_flops(stats, hi - lo)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            Tm = ev0.elapsed_time(ev1) / 1e3
+            m_recs, _ = net.last_timings()
+            net.set_timing(False)
+            if world > 1:
+                t = torch.tensor([Tm], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                Tm = float(t.item())
+                m_flops *= world
+            line["split_modes"][m] = {
+                "value": m_flops / Tm / 1e12, "ms_per_step": 1e3 * Tm / args.steps,
+                "s_per_1024_slices": Tm / n_sl_tot * 1024 * (world if world > 1 else 1),
+                "roofline": roofline_of(kernel_breakdown(m_recs), m, peaks, peak_src, sustained=True)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         path_py = [tuple(p) for p in path]
         macs, dt, ref0 = run_oracle_sample(ref_net, path_py, S)
@@ -704,9 +747,18 @@ def main():
                                 "kind": "oracle",
                                 "sample": "one full slice (slice 0) of the workload, NumPy complex128 "
                                           "tensordot per node, %.1f s" % dt}
-        got = net.contract(0, 1, mode, out=out).cpu().numpy()
         rms = float(np.sqrt(np.mean(np.abs(ref0) ** 2)))
-        line["rel_err_vs_oracle"] = float(np.max(np.abs(got - ref0) / np.maximum(np.abs(ref0), rms)))
+
+        def errs(mo):
+            got = net.contract(0, 1, mo, out=out).cpu().numpy()
+            d = np.abs(got - ref0)
+            return (float(np.max(d / np.maximum(np.abs(ref0), rms))),
+                    float(np.max(d / np.maximum(np.abs(ref0), 0.1 * rms))))
+        line["rel_err_vs_oracle"], line["rel_err_vs_oracle_floor_0.1rms"] = errs(mode)
+        for m in line.get("split_modes", {}):
+            e1, e2 = errs(MODES[m])
+            line["split_modes"][m]["rel_err_vs_oracle"] = e1
+            line["split_modes"][m]["rel_err_vs_oracle_floor_0.1rms"] = e2
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -90,10 +90,10 @@ struct TcGemmParams {
     int group_m;     // tile rasterisation: row tiles per group (1 = row-major)
     uint32_t spin_limit;  // polls before a bounded wait gives up
     int test_stall;       // tests only: the producer issues no loads, so waits run out
-    int pair;             // 1: 256x128 tiles on CTA pairs (2-SM MMA) where M >= 256 and rows are 128 B
+    int pair;             // 128-byte rows only: 1 = 256x128 tiles on CTA pairs (2-SM MMA) where M >= 256;
+                          // 2 = clusters of two CTAs sharing their A tile by multicast where N >= 256
     const uint32_t* amax_a;  // split FP16x2: the operands' scale words (SplitParams::amax), else null
     const uint32_t* amax_b;
-    int prefetch;            // > 0: the producer also prefetches the tiles of stage it + prefetch into L2
 };
 
 int tc_plane_count(int mode);
@@ -102,8 +102,10 @@ int tc_min_kb(int mode);
 cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s);
 cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
                             int batch, cudaStream_t s);
-// whether launch_cgemm_tc runs this contraction on CTA pairs (2-SM MMA)
+// whether launch_cgemm_tc runs this contraction on CTA pairs (2-SM MMA), or
+// on 2-CTA clusters with the A tile multicast
 bool tc_uses_pair(const TcGemmParams& p);
+bool tc_uses_multicast(const TcGemmParams& p);
 
 // Adjoint pass. Root environment seed: E_z[sum_j bit_j(r) ostride[j]] = grad[r].
 struct SeedParams {

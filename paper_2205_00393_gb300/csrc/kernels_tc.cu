@@ -112,14 +112,6 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// L2 prefetch of one tensor-map box (a hint: no completion, no shared memory).
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
-    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-                 : "memory");
-}
-
 // Shared-memory matrix descriptor: K-major, ROWB-byte swizzle (layout type
 // 2 = 128B, 4 = 64B), 8-row groups 8*ROWB bytes apart, descriptor version 1.
 template <int ROWB>
@@ -185,6 +177,8 @@ __constant__ int kPairs2[3][2] = {{0, 1}, {1, 0}, {0, 0}};
 // across chunks round to nearest.
 constexpr int KC_ELEMS = 256;
 constexpr int EPI_WARPS = 8;   // warps 0-7: epilogue (warp w: TMEM lanes 32*(w%4), columns 64*(w/4))
+constexpr int EPI_LDW = 66;    // float2 per row of a warp's staged 32 x 64 output block (2 of padding)
+static_assert(EPI_WARPS * 32 * EPI_LDW * 8 <= SMEM_PIPE, "staged epilogue fits the pipeline ring");
 constexpr int PRODUCER_WARP = 8, MMA_WARP = 9, NTHREADS = 320;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -205,11 +199,90 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int KIND, int ROWB>
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of `saddr` (a shared::cta address) in CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
+    return d;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+// Non-suspending test: a waiter suspended in try_wait is not necessarily woken
+// by an arrive from the other CTA, so barriers with remote arrivals are polled.
+__device__ __forceinline__ bool mbar_try_acq_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        "selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a barrier that the other CTA arrives on.
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                  uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_try_acq_cluster(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+// stop both CTAs of the pair and record a timeout
+__device__ __forceinline__ void raise_abort_pair(volatile int* abort_local, uint32_t peer_abort, int* err) {
+    *abort_local = 1;
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1) : "memory");
+    atomicExch(err, kErrTimeout);
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Multicast TMA load: the box lands at the same shared-memory offset in every
+// CTA of `mask`, each completing its own barrier at offset `bar`.
+__device__ __forceinline__ void tma_load_4d_mc(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                               uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+// arrive once on the barrier at this offset in every CTA of `mask` when this
+// CTA's MMAs issued so far complete
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(mask)
+        : "memory");
+}
+
+// MC = 2: launched as clusters of two CTAs with the same row tile and adjacent
+// column tiles. Each CTA loads half of the A tile's rows and multicasts them to
+// both (tmA's box is then 64 rows of one part), so the pair reads A from L2
+// once; B stays per CTA. Each CTA's MMA commit arrives on both CTAs' empty
+// barriers, so no stage is overwritten while either CTA still reads it.
+template <int KIND, int ROWB, int MC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ TcGemmParams p) {
     using C_ = Cfg<KIND, ROWB>;
+    static_assert(MC == 1 || (MC == 2 && ROWB == 128), "A multicast needs 128-byte rows");
     constexpr int PART_TILE_BYTES = C_::PART_TILE;
     constexpr int STAGE_A = C_::PARTS * PART_TILE_BYTES;
     constexpr int STAGE_BYTES = 2 * STAGE_A;
@@ -222,13 +295,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     const int64_t N = 1ll << p.nb, K = 1ll << p.kb;
-    // grouped rasterisation: consecutive CTAs cover GROUP_M row tiles x all column tiles
-    const int64_t tiles_n = N / TN, tiles_m = (1ll << p.mb) / TM;
+    // grouped rasterisation: consecutive CTAs (clusters) cover GROUP_M row tiles x all column tiles
+    const uint32_t rank = MC == 2 ? cluster_rank() : 0u;
+    const int64_t tiles_n = N / (MC * TN), tiles_m = (1ll << p.mb) / TM;
     const int64_t per_group = (int64_t)GROUP_M * tiles_n;
-    const int64_t grp = blockIdx.x / per_group, in_grp = blockIdx.x % per_group;
+    const int64_t cta = blockIdx.x / MC;
+    const int64_t grp = cta / per_group, in_grp = cta % per_group;
     const int64_t gm = (tiles_m - grp * GROUP_M) < GROUP_M ? (tiles_m - grp * GROUP_M) : GROUP_M;
     const int m0 = (int)((grp * GROUP_M + in_grp % gm) * TM);
-    const int n0 = (int)((in_grp / gm) * TN);
+    const int n0 = (int)((in_grp / gm) * MC * TN) + (int)rank * TN;
     const int z = blockIdx.z;
     const int nkb = (int)(K / C_::BK);
     const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;  // k-blocks per chunk
@@ -238,7 +313,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < C_::STAGES; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), MC);
         }
         for (int t = 0; t < 3; ++t) {
             mbar_init(smem_u32(&tfull[t]), 1);
@@ -256,11 +331,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    if constexpr (MC == 2) cluster_sync_all();  // both CTAs' barriers exist before any multicast
+    else __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
     volatile int* abort_flag = &abort_sh;
     const uint32_t spin = p.spin_limit ? p.spin_limit : kSpinLimit;
+    const uint32_t peer_abort = MC == 2 ? map_rank(smem_u32(&abort_sh), rank ^ 1u) : 0u;
 
     if (warp == PRODUCER_WARP && lane == 0) {
         // ---------------- TMA producer: stages in (chunk, product, k-block) order
@@ -269,8 +346,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int s = it % C_::STAGES;
             const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
             if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag, spin)) {
-                abort_sh = 1;
-                atomicExch(p.err, kErrTimeout);
+                if constexpr (MC == 2) raise_abort_pair(abort_flag, peer_abort, p.err);
+                else {
+                    abort_sh = 1;
+                    atomicExch(p.err, kErrTimeout);
+                }
                 break;
             }
             const int c = it / (3 * kpc), r = it % (3 * kpc);
@@ -278,15 +358,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
             const uint32_t fb = smem_u32(&full_bar[s]);
             mbar_expect_tx(fb, STAGE_BYTES);
-            tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, z, fb);
+            if constexpr (MC == 2) {  // this CTA's 64 rows of every A part, to both CTAs
+#pragma unroll
+                for (int q = 0; q < C_::PARTS; ++q)
+                    tma_load_4d_mc(sa + q * PART_TILE_BYTES + rank * (PART_TILE_BYTES / 2), &tmA, kb * C_::BK,
+                                   m0 + (int)rank * (TM / 2), t * C_::PARTS + q, z, fb, (uint16_t)3);
+            } else {
+                tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, z, fb);
+            }
             tma_load_4d(sa + STAGE_A, &tmB, kb * C_::BK, n0, t * C_::PARTS, z, fb);
             issued = it + 1;
-            if (p.prefetch > 0 && it + p.prefetch < n_it) {  // the tiles of a later stage into L2
-                const int ip = it + p.prefetch;
-                const int cp = ip / (3 * kpc), rp = ip % (3 * kpc);
-                const int tp = rp / kpc, kbp = cp * kpc + rp % kpc;
-                tma_prefetch_4d(&tmA, kbp * C_::BK, m0, tp * C_::PARTS, z);
-                tma_prefetch_4d(&tmB, kbp * C_::BK, n0, tp * C_::PARTS, z);
+        }
+        if constexpr (MC == 2) {
+            if (!*abort_flag && issued == n_it) {
+                // tail: the other CTA's last commits arrive on this CTA's empty
+                // barriers; wait until they have, so none lands after this CTA exits
+                int first = n_it - C_::STAGES < 0 ? 0 : n_it - C_::STAGES;
+                for (int it = first; it < n_it; ++it) {
+                    const int s = it % C_::STAGES;
+                    const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&empty_bar[s]), ph, abort_flag, spin)) break;
+                }
             }
         }
         if (*abort_flag) {
@@ -308,15 +400,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
             const int c = it / (3 * kpc), r = it % (3 * kpc);
             const int t = r / kpc, kbi = r % kpc;
-            if (kbi == 0 && c > 0 &&
-                !mbar_wait(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag, spin)) {
-                abort_sh = 1;
-                atomicExch(p.err, kErrTimeout);
-                break;
-            }
-            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin)) {
-                abort_sh = 1;
-                atomicExch(p.err, kErrTimeout);
+            if ((kbi == 0 && c > 0 && !mbar_wait(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag, spin)) ||
+                !mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin)) {
+                if constexpr (MC == 2) raise_abort_pair(abort_flag, peer_abort, p.err);
+                else {
+                    abort_sh = 1;
+                    atomicExch(p.err, kErrTimeout);
+                }
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -335,7 +425,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             any = true;
-            mma_commit(smem_u32(&empty_bar[s]));
+            if constexpr (MC == 2) mma_commit_mc(smem_u32(&empty_bar[s]), (uint16_t)3);
+            else mma_commit(smem_u32(&empty_bar[s]));
             if (kbi == kpc - 1) mma_commit(smem_u32(&tfull[t]));
         }
         if (*abort_flag && any) {
@@ -390,14 +481,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (!ok) {
             if (lane == 0 && !abort_sh) {
-                abort_sh = 1;
-                atomicExch(p.err, kErrTimeout);
+                if constexpr (MC == 2) raise_abort_pair(abort_flag, peer_abort, p.err);
+                else {
+                    abort_sh = 1;
+                    atomicExch(p.err, kErrTimeout);
+                }
             }
         } else {
-            const int row = 32 * g + lane;
-            const int64_t ld = p.c_ld ? p.c_ld : N;
-            float4* dst = reinterpret_cast<float4*>(p.C + (int64_t)z * p.c_batch_stride +
-                                                    (int64_t)(m0 + row) * ld + n0 + 64 * h);
             if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
                 const float sa = pow2f(-fp16_scale_exp(p.amax_a[z])), sb = pow2f(-fp16_scale_exp(p.amax_b[z]));
 #pragma unroll
@@ -406,12 +496,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     ci[j] = ci[j] * sa * sb;
                 }
             }
+            // Stage the warp's 32 x 64 complex block in shared memory (every MMA that
+            // read the pipeline ring has completed), then write whole 512-byte rows
+            // with coalesced 16-byte stores.
+            float2* stg = reinterpret_cast<float2*>(smem) + (size_t)warp * 32 * EPI_LDW;
 #pragma unroll
-            for (int j = 0; j < 64; j += 2) dst[j / 2] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
+            for (int j = 0; j < 64; j += 2)
+                reinterpret_cast<float4*>(stg + lane * EPI_LDW + j)[0] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
+            __syncwarp();
+            const int64_t ld = p.c_ld ? p.c_ld : N;
+            float2* cbase = p.C + (int64_t)z * p.c_batch_stride + (int64_t)(m0 + 32 * g) * ld + n0 + 64 * h;
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r)
+                reinterpret_cast<float4*>(cbase + (int64_t)r * ld)[lane] =
+                    reinterpret_cast<const float4*>(stg + r * EPI_LDW)[lane];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    __syncwarp();
+    if constexpr (MC == 2) cluster_sync_all();  // no CTA leaves while the other may still signal it
+    else __syncthreads();
     if (warp == MMA_WARP) {
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -449,57 +553,6 @@ template <int KIND> struct Cfg2 {
     static constexpr int STAGES = SMEM_PIPE2 / STAGE_BYTES;
 };
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// shared::cluster address of `saddr` (a shared::cta address) in CTA `rank`
-__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
-    uint32_t d;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
-    return d;
-}
-
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-
-// Non-suspending test: a waiter suspended in try_wait is not necessarily woken
-// by an arrive from the other CTA, so barriers with remote arrivals are polled.
-__device__ __forceinline__ bool mbar_try_acq_cluster(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\n"
-        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        "selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on a barrier that the other CTA arrives on.
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                                  uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i) {
-        if (mbar_try_acq_cluster(bar, parity)) return true;
-        if ((i & 255) == 255 && *abort_flag) return false;
-    }
-    return false;
-}
-
-// stop both CTAs of the pair and record a timeout
-__device__ __forceinline__ void raise_abort_pair(volatile int* abort_local, uint32_t peer_abort, int* err) {
-    *abort_local = 1;
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1) : "memory");
-    atomicExch(err, kErrTimeout);
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
-}
 
 template <int KIND>
 __device__ __forceinline__ void mma2(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -743,10 +796,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         if (!ok) {
             if (lane == 0 && !abort_sh) raise_abort_pair(abort_flag, peer_abort, p.err);
         } else {
-            const int row = 32 * g + lane;
-            const int64_t ld = p.c_ld ? p.c_ld : N;
-            float4* dst = reinterpret_cast<float4*>(p.C + (int64_t)z * p.c_batch_stride +
-                                                    (int64_t)(m0 + row) * ld + n0 + 64 * h);
             if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
                 const float sa = pow2f(-fp16_scale_exp(p.amax_a[z])), sb = pow2f(-fp16_scale_exp(p.amax_b[z]));
 #pragma unroll
@@ -755,8 +804,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     ci[j] = ci[j] * sa * sb;
                 }
             }
+            // Stage the warp's 32 x 64 complex block in shared memory (every MMA that
+            // read the pipeline ring has completed), then write whole 512-byte rows
+            // with coalesced 16-byte stores.
+            float2* stg = reinterpret_cast<float2*>(smem) + (size_t)warp * 32 * EPI_LDW;
 #pragma unroll
-            for (int j = 0; j < 64; j += 2) dst[j / 2] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
+            for (int j = 0; j < 64; j += 2)
+                reinterpret_cast<float4*>(stg + lane * EPI_LDW + j)[0] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
+            __syncwarp();
+            const int64_t ld = p.c_ld ? p.c_ld : N;
+            float2* cbase = p.C + (int64_t)z * p.c_batch_stride + (int64_t)(m0 + 32 * g) * ld + n0 + 64 * h;
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r)
+                reinterpret_cast<float4*>(cbase + (int64_t)r * ld)[lane] =
+                    reinterpret_cast<const float4*>(stg + r * EPI_LDW)[lane];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -874,34 +935,46 @@ __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ S
 
 // Split FP16x2: max of |Re| and |Im| over the operand of each batch entry (the
 // split kernel's tiles and gather), as float bits (non-negative floats order
-// like their bits). amax must be zeroed first.
-__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ SplitParams p) {
+// like their bits). Each block sweeps tiles with a grid stride, reduces in
+// shared memory and issues one atomic. amax must be zeroed first.
+constexpr int ABSMAX_BLOCKS = 152 * 4;
+
+__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ SplitParams p, int64_t n_tiles) {
     __shared__ int64_t roff[64], koff[64];
+    __shared__ uint32_t wmax[8];
     const int64_t K = 1ll << p.kb;
     const int SK = K >= 64 ? 64 : (int)K;
     const int SR = SPLIT_TILE / SK;
     const int64_t tiles_k = K / SK;
-    const int64_t r0 = (blockIdx.x / tiles_k) * SR, k0 = (blockIdx.x % tiles_k) * SK;
     const int z = blockIdx.z;
     const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, p.slice0 + z);
     const int tid = threadIdx.x;
-    if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
-    else if (tid >= 64 && tid < 64 + SK) koff[tid - 64] = bits_offset(k0 + tid - 64, p.ks, p.kb, 0);
-    __syncthreads();
     const bool kfast = p.kb > 0 && p.ks[0] == 1;
     uint32_t m = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t r0 = (tile / tiles_k) * SR, k0 = (tile % tiles_k) * SK;
+        __syncthreads();  // the previous tile's offsets are no longer read
+        if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
+        else if (tid >= 64 && tid < 64 + SK) koff[tid - 64] = bits_offset(k0 + tid - 64, p.ks, p.kb, 0);
+        __syncthreads();
 #pragma unroll
-    for (int i = 0; i < SPLIT_TILE / 256; ++i) {
-        int e = tid + i * 256;
-        int rr, kk;
-        if (kfast) { kk = e % SK; rr = e / SK; }
-        else { rr = e % SR; kk = e / SR; }
-        const float2 v = src[roff[rr] + koff[kk]];
-        const uint32_t a = __float_as_uint(fabsf(v.x)), b = __float_as_uint(fabsf(v.y));
-        m = max(m, max(a, b));
+        for (int i = 0; i < SPLIT_TILE / 256; ++i) {
+            int e = tid + i * 256;
+            int rr, kk;
+            if (kfast) { kk = e % SK; rr = e / SK; }
+            else { rr = e % SR; kk = e / SR; }
+            const float2 v = src[roff[rr] + koff[kk]];
+            m = max(m, max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))));
+        }
     }
     m = __reduce_max_sync(0xffffffffu, m);
-    if ((tid & 31) == 0) atomicMax(p.amax + z, m);
+    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    __syncthreads();
+    if (tid < 32) {
+        m = tid < 8 ? wmax[tid] : 0u;
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (tid == 0) atomicMax(p.amax + z, m);
+    }
 }
 
 // ------------------------------------------------------------ host helpers
@@ -925,7 +998,8 @@ EncodeFn encoder() {
 
 // 4D map over planes [batch][3*PARTS][rows][K]; box = (BK, box_rows, PARTS, 1).
 template <int KIND, int ROWB>
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int batch, int box_rows = 128) {
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int batch, int box_rows = 128,
+              int box_parts = Cfg<KIND, ROWB>::PARTS) {
     using C_ = Cfg<KIND, ROWB>;
     EncodeFn enc = encoder();
     if (!enc) return false;
@@ -933,7 +1007,7 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int b
     cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Q, (cuuint64_t)batch};
     cuuint64_t strides[3] = {(cuuint64_t)(K * C_::ELEM), (cuuint64_t)(rows * K * C_::ELEM),
                              (cuuint64_t)(Q * rows * K * C_::ELEM)};
-    cuuint32_t box[4] = {(cuuint32_t)C_::BK, (cuuint32_t)box_rows, (cuuint32_t)C_::PARTS, 1u};  // BK * ELEM = ROWB bytes
+    cuuint32_t box[4] = {(cuuint32_t)C_::BK, (cuuint32_t)box_rows, (cuuint32_t)box_parts, 1u};  // BK * ELEM = ROWB bytes
     cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = KIND == 1   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : KIND == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -946,27 +1020,44 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int b
     return r == CUDA_SUCCESS;
 }
 
-template <int KIND, int ROWB>
+template <int KIND, int ROWB, int MC>
 cudaError_t launch_tc_impl(const TcGemmParams& p, const void* planesA, const void* planesB, int batch,
                            cudaStream_t s) {
     using C_ = Cfg<KIND, ROWB>;
     const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
-    if (K % C_::BK) return cudaErrorInvalidValue;
+    if (K % C_::BK || N % (MC * TN)) return cudaErrorInvalidValue;
     CUtensorMap ta, tb;
-    if (!make_map<KIND, ROWB>(&ta, planesA, M, K, batch) || !make_map<KIND, ROWB>(&tb, planesB, N, K, batch))
-        return cudaErrorInvalidValue;
+    const bool maps = MC == 2 ? make_map<KIND, ROWB>(&ta, planesA, M, K, batch, TM / 2, 1)
+                              : make_map<KIND, ROWB>(&ta, planesA, M, K, batch);
+    if (!maps || !make_map<KIND, ROWB>(&tb, planesB, N, K, batch)) return cudaErrorInvalidValue;
     const int smem = C_::STAGES * C_::STAGE_BYTES + 1024;
     static_assert(C_::STAGES >= 2 && C_::STAGES * C_::STAGE_BYTES + 1024 <= 227 * 1024, "shared memory");
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_cgemm_tc<KIND, ROWB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(k_cgemm_tc<KIND, ROWB, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t tiles = (M / TM) * (N / TN);
-    k_cgemm_tc<KIND, ROWB><<<dim3((unsigned)tiles, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
-    return cudaGetLastError();
+    if constexpr (MC == 1) {
+        k_cgemm_tc<KIND, ROWB, 1><<<dim3((unsigned)tiles, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)tiles, 1, batch);
+        cfg.blockDim = dim3(NTHREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = MC;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_cgemm_tc<KIND, ROWB, MC>, ta, tb, p);
+    }
 }
 
 template <int KIND>
@@ -997,15 +1088,21 @@ cudaError_t launch_tc_rows(const TcGemmParams& p, const void* pa, const void* pb
     // 128-byte rows need K to span whole 128-byte k-blocks
     const int64_t K = 1ll << p.kb;
     if (tc_uses_pair(p)) return launch_tc2_impl<KIND>(p, pa, pb, batch, s);
-    if (p.row_bytes == 128 && K % Cfg<KIND, 128>::BK == 0) return launch_tc_impl<KIND, 128>(p, pa, pb, batch, s);
-    return launch_tc_impl<KIND, 64>(p, pa, pb, batch, s);
+    if (tc_uses_multicast(p)) return launch_tc_impl<KIND, 128, 2>(p, pa, pb, batch, s);
+    if (p.row_bytes == 128 && K % Cfg<KIND, 128>::BK == 0) return launch_tc_impl<KIND, 128, 1>(p, pa, pb, batch, s);
+    return launch_tc_impl<KIND, 64, 1>(p, pa, pb, batch, s);
 }
 
 }  // namespace
 
 // CTA pairs need 256-row tiles and K >= 64 (whole 128-byte k-blocks in every mode)
 bool tc_uses_pair(const TcGemmParams& p) {
-    return p.pair && p.row_bytes == 128 && p.mb >= 8 && p.kb >= 6;
+    return p.pair == 1 && p.row_bytes == 128 && p.mb >= 8 && p.kb >= 6;
+}
+
+// A multicast over a 2-CTA cluster needs an even number of column tiles
+bool tc_uses_multicast(const TcGemmParams& p) {
+    return p.pair == 2 && p.row_bytes == 128 && p.nb >= 8 && p.kb >= 6;
 }
 
 // tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts),
@@ -1030,7 +1127,8 @@ cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t
             if (!p.amax) return cudaErrorInvalidValue;
             cudaError_t e = cudaMemsetAsync(p.amax, 0, sizeof(uint32_t) * (size_t)batch, s);
             if (e != cudaSuccess) return e;
-            k_absmax<<<grid, 256, 0, s>>>(p);
+            const unsigned ab = (unsigned)(blocks < ABSMAX_BLOCKS ? blocks : ABSMAX_BLOCKS);
+            k_absmax<<<dim3(ab, 1, batch), 256, 0, s>>>(p, blocks);
             k_split_operand<3><<<grid, 256, 0, s>>>(p);
             break;
         }

@@ -50,7 +50,7 @@ constexpr int64_t kAlign = 256;
 int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Kernel chosen for a contraction node.
-enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_TC2 = 5 };
+enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_TC2 = 5, K_TCMC = 6 };
 
 // Tensor-core eligibility of a non-root node in a split mode: both output
 // sides span whole 128-wide tiles and K spans whole 64-wide k-blocks.
@@ -60,7 +60,8 @@ bool tc_node(int mode, int mb, int nb, int kb, bool is_root) {
 
 // Autotuned kernel choice per (mode, log2 M, log2 N, log2 K): 0 = FP32 CUDA
 // cores, 64 / 128 = tensor cores with that row width, 256 = tensor cores with
-// 128-byte rows on CTA pairs (2-SM MMA, 256x128 tiles). Filled by
+// 128-byte rows on CTA pairs (2-SM MMA, 256x128 tiles), 512 = 128-byte rows on
+// 2-CTA clusters that multicast their shared A tile. Filled by
 // tnc_autotune; shared by every network of the process.
 std::map<std::tuple<int, int, int, int>, int>& tune_table() {
     static std::map<std::tuple<int, int, int, int>, int> t;
@@ -164,7 +165,7 @@ struct tnc_net {
     int tc_row_bytes = 128;
     int tc_group_m = 1;
     int tc_pair = 0;             // untuned default: 128-byte rows on CTA pairs where M >= 256
-    int tc_prefetch = 0;         // L2 prefetch distance of the tensor-core producer, in stages
+    int tc_multicast = 0;        // untuned default: 128-byte rows on A-multicast clusters where N >= 256
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
@@ -212,6 +213,7 @@ int shape_choice(const tnc_net* net, int mode, int mb, int nb, int kb, bool is_r
     if (net->force_choice >= 0) return net->force_choice;
     auto it = tune_table().find(std::make_tuple(mode, mb, nb, kb));
     if (it != tune_table().end()) return it->second;
+    if (net->tc_row_bytes == 128 && net->tc_multicast) return 512;
     return net->tc_row_bytes == 128 && net->tc_pair ? 256 : net->tc_row_bytes;
 }
 
@@ -674,9 +676,8 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tp.c_batch_stride = g.c_batch_stride;
             tp.c_ld = N;
             tp.err = net->d_err;
-            tp.row_bytes = row_bytes == 256 ? 128 : row_bytes;
-            tp.pair = row_bytes == 256 ? 1 : 0;
-            tp.prefetch = net->tc_prefetch;
+            tp.row_bytes = row_bytes >= 256 ? 128 : row_bytes;
+            tp.pair = row_bytes == 256 ? 1 : (row_bytes == 512 ? 2 : 0);
             if (mode == TNC_SPLIT_FP16X2) {
                 tp.amax_a = reinterpret_cast<const uint32_t*>(static_cast<const char*>(pa) +
                                                               plane_data_bytes(mode, mbp, g.kb, b));
@@ -686,7 +687,7 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tp.group_m = net->tc_group_m;
             tp.spin_limit = net->tc_spin_limit;
             tp.test_stall = net->tc_test_stall;
-            CUDA_TRY(timed_begin(net, node, tnc::tc_uses_pair(tp) ? K_TC2 : K_TC, b, s,
+            CUDA_TRY(timed_begin(net, node, tnc::tc_uses_pair(tp) ? K_TC2 : (tnc::tc_uses_multicast(tp) ? K_TCMC : K_TC), b, s,
                                  std::ldexp(1.0, mbp + nbp + g.kb) * b));
             CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
             CUDA_TRY(timed_end(net, s));
@@ -1654,8 +1655,8 @@ tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
     const int R = 1 << net->plan.obits;
     double* out = nullptr;
     CUDA_TRY(cudaMalloc(&out, (size_t)R * 16));
-    constexpr int NV = 4;
-    const int variants[NV] = {0, 256, 128, 64};
+    constexpr int NV = 5;
+    const int variants[NV] = {0, 512, 256, 128, 64};
     std::map<int, double> t[NV];  // per node: milliseconds of all its launches
     const bool timing = net->timing;
     net->tuning = true;
@@ -1735,9 +1736,9 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "tc_pair") {
         if (value != 0 && value != 1) return fail(TNC_E_INVALID, "tc_pair must be 0 or 1");
         net->tc_pair = (int)value;
-    } else if (k == "tc_prefetch") {
-        if (value < 0 || value > 64) return fail(TNC_E_INVALID, "tc_prefetch must be in [0, 64]");
-        net->tc_prefetch = (int)value;
+    } else if (k == "tc_multicast") {
+        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "tc_multicast must be 0 or 1");
+        net->tc_multicast = (int)value;
     } else if (k == "tc_group_m") {
         if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");
         net->tc_group_m = (int)value;
