@@ -76,6 +76,8 @@ def kernel_traffic(kind_name, mode, cmacs_per_launch):
             rec = json.load(f).get(kind_name)
     except (OSError, ValueError):
         return None
+    if rec and "mode" not in rec:  # one record per mode
+        rec = rec.get(mode)
     if not rec or rec.get("mode") != mode:
         return None
     src = os.path.join(ROOT, rec["source"])
