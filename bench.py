@@ -386,6 +386,62 @@ def many_bench(args):
     return 0
 
 
+def c53_bench(args):
+    """53-qubit lattice (6x9 grid minus one site), 20 cycles (seed 3), one
+    amplitude, sliced to 2^30-element intermediates: a fixed subset of slices
+    [0, n) (1024 by default) in the split mode, timed with CUDA events, in
+    batches of --slices-per-step; then the first two slices again in split
+    precision and on the FP32 CUDA-core path, whose sums are compared (the
+    oracle cannot run at this size)."""
+    import torch
+    from tnc_inputs import circuit_to_network, lattice_53q_rqc
+    from paper_2205_00393_gb300 import Network, tune_table
+    torch.cuda.set_device(0)
+    c = lattice_53q_rqc(20, 3)
+    net = Network.from_tn(circuit_to_network(c).as_complex64())
+    net.set_path(net.greedy_path())
+    net.set_slices(net.find_slices(30, 7))
+    apply_options(net, args)
+    mode = MODES[args.mode]
+    B = args.slices_per_step
+    n = args.c53_slices
+    if not args.no_autotune:
+        net.autotune(mode, 0)
+    ws = torch.empty(net.workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    net.set_workspace(ws)
+    stats = net.stats()
+    out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
+    acc = torch.zeros(net.n_out, dtype=torch.complex128, device="cuda")
+    net.contract(n, n + B, mode, out=out)  # warm-up on slices outside the timed subset
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for lo in range(0, n, B):
+            net.contract(lo, min(lo + B, n), mode, out=out)
+            acc += out
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    net.check_device()
+    T = ev0.elapsed_time(ev1) / 1e3
+    flops = node_flops(stats, n)
+    split2 = net.contract(0, 2, mode, out=out).cpu().numpy()[0]
+    t0 = time.perf_counter()
+    fp32 = net.contract(0, 2, 0, out=out).cpu().numpy()[0]
+    t_fp32 = time.perf_counter() - t0
+    line = {"metric": "53-qubit lattice, 20 cycles: sliced contraction of a fixed slice subset",
+            "mode": args.mode, "value": flops / T / 1e12, "unit": UNIT,
+            "s_per_1024_slices": T / n * 1024, "slices": n, "seconds": T,
+            "n_sliced": len(net.sliced), "eq3_overhead": stats["overhead"], "max_log2_size": stats["max_log2_size"],
+            "workspace_gb": ws.numel() / 1e9, "partial_amplitude": [float(acc[0].real), float(acc[0].imag)],
+            "rel_err_vs_fp32_path_2_slices": float(abs(split2 - fp32) / abs(fp32)),
+            "fp32_path_s_per_slice": t_fp32 / 2, "clocks": clk.summary(),
+            "tuned_shapes": [e for e in tune_table() if e[0] == mode]}
+    print(json.dumps(line))
+    return 0
+
+
 def grad42_bench(args):
     """Gradient configuration: 42-qubit 6x7 grid, 12 cycles (seed 5), one
     amplitude, sliced to 2^30-element intermediates; d amp / d(theta, phi) of
@@ -422,22 +478,27 @@ def grad42_bench(args):
     flat = rng.choice(params.numel(), 16, replace=False)
     which = [(int(f) // 2, int(f) % 2) for f in flat]
     p0 = params.detach().numpy().copy()
-    h = 1e-3
-    fd = []
-    for (k, j) in which:
-        vals = []
-        for sgn in (1, -1):
-            p = p0.copy()
-            p[k, j] += sgn * h
-            with torch.no_grad():
-                vals.append(float(amp(torch.from_numpy(p)).real.sum()))
-        fd.append((vals[0] - vals[1]) / (2 * h))
-    fd = np.array(fd)
-    amp.set_params(p0)  # the loop above leaves the last parameter perturbed
     got = np.array([g[k, j] for (k, j) in which])
-    rms = float(np.sqrt(np.mean(fd ** 2)))
-    err = float(np.max(np.abs(got - fd) / np.maximum(np.abs(fd), rms)))
-    err_norm = float(np.linalg.norm(got - fd) / np.linalg.norm(fd))
+
+    def central_fd(h):
+        fd = []
+        for (k, j) in which:
+            vals = []
+            for sgn in (1, -1):
+                p = p0.copy()
+                p[k, j] += sgn * h
+                with torch.no_grad():
+                    vals.append(float(amp(torch.from_numpy(p)).real.sum()))
+            fd.append((vals[0] - vals[1]) / (2 * h))
+        amp.set_params(p0)  # the loop leaves the last parameter perturbed
+        fd = np.array(fd)
+        rms = float(np.sqrt(np.mean(fd ** 2)))
+        return (float(np.max(np.abs(got - fd) / np.maximum(np.abs(fd), rms))),
+                float(np.linalg.norm(got - fd) / np.linalg.norm(fd)))
+    err, err_norm = central_fd(1e-3)
+    # the witness's own noise: rounding of the forward divided by 2h falls as 1/h
+    # until the truncation error (h^2 / 6 relative) takes over
+    fd_by_h = {"%g" % h: dict(zip(("max_rel", "normwise"), central_fd(h))) for h in args.fd_extra_h}
     # second witness: the amplitude is linear in every gate matrix, so
     # (amp(G + dG) - amp(G - dG)) / 2 is the exact derivative along dG
     from tnc_inputs import gates as G
@@ -460,6 +521,7 @@ def grad42_bench(args):
             "n_sliced": len(amp.net.sliced), "forward_s": t1 - t0, "backward_s": t2 - t1,
             "max_rel_err_vs_fd_h1e-3": err, "normwise_rel_err_vs_fd_h1e-3": err_norm, "fd_params": 16,
             "max_rel_err_vs_gate_perturbation": err_lin, "normwise_rel_err_vs_gate_perturbation": err_lin_norm,
+            "fd_other_h": fd_by_h,
             "backward_keep_every": st.get("backward_keep_every"),
             "backward_workspace_gb": st.get("backward_workspace", 0) / 1e9, "budget_gb": 80 * 1.073741824,
             "amplitude_partial": [float(a.detach().real.sum()), float(a.detach().imag.sum())]}
@@ -518,7 +580,7 @@ def backward_bench(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnc", choices=["tnc", "reference"])
     ap.add_argument("--mode", default=None, choices=sorted(MODES),
@@ -535,6 +597,11 @@ def main():
                     help="tensor-core GEMMs on 2-CTA clusters sharing the A tile by multicast (library default 0)")
     ap.add_argument("--tc-pair", type=int, default=None, choices=(0, 1),
                     help="tensor-core GEMMs on CTA pairs (2-SM MMA) where eligible (library default 1)")
+    ap.add_argument("--c53", action="store_true",
+                    help="53-qubit lattice, 20 cycles, t = 30: time a fixed subset of slices")
+    ap.add_argument("--c53-slices", type=int, default=1024)
+    ap.add_argument("--fd-extra-h", type=float, nargs="*", default=[],
+                    help="--grad42: further central-difference steps to report besides h = 1e-3")
     ap.add_argument("--grad42", action="store_true",
                     help="42-qubit gradient configuration (adjoint vs finite differences) instead")
     ap.add_argument("--many", action="store_true",
@@ -567,6 +634,8 @@ def main():
         return many_bench(args)
     if args.grad42:
         return grad42_bench(args)
+    if args.c53:
+        return c53_bench(args)
 
     import torch
     import torch.distributed as dist
@@ -593,9 +662,10 @@ def main():
     stream = torch.cuda.current_stream()
     out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
 
-    def slice_range(step):
-        lo = ((step * world + rank) * B) % n_slices
-        return lo, min(lo + B, n_slices)
+    from paper_2205_00393_gb300.shard import step_range
+
+    def slice_range(step):  # disjoint slice blocks per rank (weak scaling, no data-path collective)
+        return step_range(step, world, rank, B, n_slices)
 
     def barrier():
         if world > 1:

@@ -77,7 +77,7 @@ struct SplitParams {
     int64_t rs[kMaxBits], ks[kMaxBits];
     int64_t slice0;
     void* dst;
-    uint32_t* amax;  // split FP16x2: per batch entry, bits of max |Re|, |Im| (written by launch_split)
+    const uint32_t* amax;  // split FP16x2: per batch entry, bits of max |Re|, |Im| (from launch_absmax)
 };
 
 struct TcGemmParams {
@@ -100,6 +100,10 @@ int tc_plane_count(int mode);
 int tc_elem_bytes(int mode);
 int tc_min_kb(int mode);
 cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s);
+// Split FP16x2 scale words: amax[z] = bits of max |Re|, |Im| over the 2^bits
+// elements of the tensor behind `src` (its free, contracted and sliced modes)
+// at src.ptr + z * src.batch_stride.
+cudaError_t launch_absmax(const Operand& src, int bits, int batch, uint32_t* amax, cudaStream_t s);
 cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
                             int batch, cudaStream_t s);
 // whether launch_cgemm_tc runs this contraction on CTA pairs (2-SM MMA), or

@@ -851,129 +851,138 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
-constexpr int SPLIT_TILE = 2048;  // elements per split tile: 32 rows x 64 k, or 64 rows x 32 k
+constexpr int SPLIT_TILE = 2048;  // elements per split tile: SR rows x SK k
+// SK: 256 k when k is the operand's unit-stride mode (reads of 2 KB and plane
+// writes of 512 B per row), else 64 (32 when K = 32) so that a gather whose
+// unit stride lies along the rows stays coalesced too.
+__host__ __device__ inline int split_tile_k(int kb, bool kfast) {
+    const int K = 1 << (kb < 9 ? kb : 9);
+    return kfast ? (K < 256 ? K : 256) : (K < 64 ? K : 64);
+}
+// shared-memory slot of tile element (rr, kk): one padding slot every 8 k keeps
+// the write phase's 8-wide groups on distinct banks
+constexpr int SPLIT_SMEM = 2368;  // >= SR * (SK + SK / 8 + 1) for every SK above
 
 // planes: out[((z * (3*PARTS) + q) * R + r) * K + k], q = t * PARTS + part
 template <int KIND>
 __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ SplitParams p) {
     using C_ = Cfg<KIND, 64>;
-    __shared__ float2 tile[SPLIT_TILE + 64];
-    __shared__ int64_t roff[64], koff[64];
+    __shared__ float2 tile[SPLIT_SMEM];
+    __shared__ int64_t roff[64], koff[256];
     const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
-    const int SK = K >= 64 ? 64 : (int)K;
+    const bool kfast = p.kb > 0 && p.ks[0] == 1;
+    const int SK = split_tile_k(p.kb, kfast);
     const int SR = SPLIT_TILE / SK;
-    const int LD = SK + 1;
+    const int LD = SK + SK / 8 + 1;
     const int64_t tiles_k = K / SK;
     const int64_t r0 = (blockIdx.x / tiles_k) * SR, k0 = (blockIdx.x % tiles_k) * SK;
     const int z = blockIdx.z;
     const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, p.slice0 + z);
     const int tid = threadIdx.x;
     if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
-    else if (tid >= 64 && tid < 64 + SK) koff[tid - 64] = bits_offset(k0 + tid - 64, p.ks, p.kb, 0);
+    if (tid < SK) koff[tid] = bits_offset(k0 + tid, p.ks, p.kb, 0);
     __syncthreads();
-    const bool kfast = p.kb > 0 && p.ks[0] == 1;
 #pragma unroll
     for (int i = 0; i < SPLIT_TILE / 256; ++i) {
         int e = tid + i * 256;
         int rr, kk;
         if (kfast) { kk = e % SK; rr = e / SK; }
         else { rr = e % SR; kk = e / SR; }
-        tile[rr * LD + kk] = src[roff[rr] + koff[kk]];
+        tile[rr * LD + kk + (kk >> 3)] = src[roff[rr] + koff[kk]];
     }
     __syncthreads();
     constexpr int Q = 3 * C_::PARTS;
     const int64_t plane = R * K;
     uint8_t* out = reinterpret_cast<uint8_t*>(p.dst) + (int64_t)z * Q * plane * C_::ELEM;
+    // one thread per 8 consecutive k of one row (SR rows x SK/8 groups = 256):
+    // every part of every real matrix leaves as one 16-byte (TF32: 32-byte) store
+    const int gpr = SK / 8;
+    const int rr = tid / gpr, g8 = tid % gpr;
+    float v[3][8];
+    const float sc = KIND == 3 ? pow2f(fp16_scale_exp(p.amax[z])) : 1.f;  // FP16x2 operand scale (exact)
 #pragma unroll
-    for (int i = 0; i < (SPLIT_TILE / 2) / 256; ++i) {
-        int e = tid + i * 256;
-        int kp = e % (SK / 2), rr = e / (SK / 2);
-        float2 x0 = tile[rr * LD + 2 * kp], x1 = tile[rr * LD + 2 * kp + 1];
-        if constexpr (KIND == 3) {  // operand scale 2^e (exact)
-            const float sc = pow2f(fp16_scale_exp(p.amax[z]));
-            x0.x *= sc;
-            x0.y *= sc;
-            x1.x *= sc;
-            x1.y *= sc;
+    for (int j = 0; j < 8; ++j) {
+        float2 x = tile[rr * LD + 9 * g8 + j];  // element (rr, 8 g8 + j)
+        if constexpr (KIND == 3) {
+            x.x *= sc;
+            x.y *= sc;
         }
-        float v0[3] = {x0.x, x0.y, x0.x + x0.y};
-        float v1[3] = {x1.x, x1.y, x1.x + x1.y};
-        const int64_t idx = (r0 + rr) * K + k0 + 2 * kp;
+        v[0][j] = x.x;
+        v[1][j] = x.y;
+        v[2][j] = x.x + x.y;
+    }
+    const int64_t idx = (r0 + rr) * K + k0 + 8 * g8;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            if constexpr (KIND == 3) {
-                float a = v0[t], b = v1[t];
+    for (int t = 0; t < 3; ++t) {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    __half2 pr = __halves2half2(__float2half_rn(a), __float2half_rn(b));
-                    reinterpret_cast<__half2*>(out + ((t * 2 + q) * plane + idx) * 2)[0] = pr;
-                    a -= __low2float(pr);
-                    b -= __high2float(pr);
+        for (int q = 0; q < C_::PARTS; ++q) {
+            if constexpr (KIND == 1) {
+                float hi[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    hi[j] = tf32_round(v[t][j]);
+                    v[t][j] -= hi[j];
                 }
-            } else if constexpr (KIND != 1) {
-                float a = v0[t], b = v1[t];
-#pragma unroll
-                for (int q = 0; q < C_::PARTS; ++q) {
-                    __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-                    __nv_bfloat162 pr;
-                    pr.x = ha;
-                    pr.y = hb;
-                    reinterpret_cast<__nv_bfloat162*>(out + ((t * C_::PARTS + q) * plane + idx) * 2)[0] = pr;
-                    a -= __bfloat162float(ha);
-                    b -= __bfloat162float(hb);
-                }
+                float4* dst = reinterpret_cast<float4*>(out + ((t * 2 + q) * plane + idx) * 4);
+                dst[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                dst[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
             } else {
-                float a = v0[t], b = v1[t];
-                float a0 = tf32_round(a), b0 = tf32_round(b);
-                float a1 = tf32_round(a - a0), b1 = tf32_round(b - b0);
-                reinterpret_cast<float2*>(out + ((t * 2 + 0) * plane + idx) * 4)[0] = make_float2(a0, b0);
-                reinterpret_cast<float2*>(out + ((t * 2 + 1) * plane + idx) * 4)[0] = make_float2(a1, b1);
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if constexpr (KIND == 3) {
+                        const __half2 h = __floats2half2_rn(v[t][2 * j], v[t][2 * j + 1]);
+                        v[t][2 * j] -= __low2float(h);
+                        v[t][2 * j + 1] -= __high2float(h);
+                        w[j] = *reinterpret_cast<const uint32_t*>(&h);
+                    } else {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(v[t][2 * j], v[t][2 * j + 1]);
+                        v[t][2 * j] -= __low2float(h);
+                        v[t][2 * j + 1] -= __high2float(h);
+                        w[j] = *reinterpret_cast<const uint32_t*>(&h);
+                    }
+                }
+                reinterpret_cast<uint4*>(out + ((t * C_::PARTS + q) * plane + idx) * 2)[0] =
+                    make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
     }
 }
 
-// Split FP16x2: max of |Re| and |Im| over the operand of each batch entry (the
-// split kernel's tiles and gather), as float bits (non-negative floats order
-// like their bits). Each block sweeps tiles with a grid stride, reduces in
-// shared memory and issues one atomic. amax must be zeroed first.
+// Split FP16x2: max of |Re| and |Im| over the whole tensor behind an operand,
+// per batch entry, as float bits (non-negative floats order like their bits).
+// An operand covers every element of its tensor (free, contracted and sliced
+// binary modes together), so the max is order-free and a linear scan; for a
+// slice or a row panel of the tensor it is an upper bound, which is all the
+// scale needs. One atomic per block; amax must be zeroed first.
 constexpr int ABSMAX_BLOCKS = 152 * 4;
 
-__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ SplitParams p, int64_t n_tiles) {
-    __shared__ int64_t roff[64], koff[64];
+__global__ void __launch_bounds__(256) k_absmax(const float2* __restrict__ base, int64_t batch_stride, int64_t n,
+                                                uint32_t* amax) {
     __shared__ uint32_t wmax[8];
-    const int64_t K = 1ll << p.kb;
-    const int SK = K >= 64 ? 64 : (int)K;
-    const int SR = SPLIT_TILE / SK;
-    const int64_t tiles_k = K / SK;
     const int z = blockIdx.z;
-    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, p.slice0 + z);
-    const int tid = threadIdx.x;
-    const bool kfast = p.kb > 0 && p.ks[0] == 1;
+    const float2* src = base + (int64_t)z * batch_stride;
     uint32_t m = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int64_t r0 = (tile / tiles_k) * SR, k0 = (tile % tiles_k) * SK;
-        __syncthreads();  // the previous tile's offsets are no longer read
-        if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
-        else if (tid >= 64 && tid < 64 + SK) koff[tid - 64] = bits_offset(k0 + tid - 64, p.ks, p.kb, 0);
-        __syncthreads();
+    const int64_t step = (int64_t)gridDim.x * 256;
+    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    for (; i + 3 * step < n; i += 4 * step) {  // four loads in flight per thread
+        float2 v[4];
 #pragma unroll
-        for (int i = 0; i < SPLIT_TILE / 256; ++i) {
-            int e = tid + i * 256;
-            int rr, kk;
-            if (kfast) { kk = e % SK; rr = e / SK; }
-            else { rr = e % SR; kk = e / SR; }
-            const float2 v = src[roff[rr] + koff[kk]];
-            m = max(m, max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))));
-        }
+        for (int u = 0; u < 4; ++u) v[u] = src[i + u * step];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m = max(m, max(__float_as_uint(fabsf(v[u].x)), __float_as_uint(fabsf(v[u].y))));
+    }
+    for (; i < n; i += step) {
+        const float2 v = src[i];
+        m = max(m, max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))));
     }
     m = __reduce_max_sync(0xffffffffu, m);
-    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
-    if (tid < 32) {
-        m = tid < 8 ? wmax[tid] : 0u;
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < 8 ? wmax[threadIdx.x] : 0u;
         m = __reduce_max_sync(0xffffffffu, m);
-        if (tid == 0) atomicMax(p.amax + z, m);
+        if (threadIdx.x == 0) atomicMax(amax + z, m);
     }
 }
 
@@ -1116,24 +1125,30 @@ int tc_min_kb(int) { return 5; }
 cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s) {
     const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
     if (K < 32 || batch < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
-    const int64_t SK = K >= 64 ? 64 : K, SR = SPLIT_TILE / SK;
+    const int64_t SK = split_tile_k(p.kb, p.kb > 0 && p.ks[0] == 1), SR = SPLIT_TILE / SK;
     if (R < SR) return cudaErrorInvalidConfiguration;
     const int64_t blocks = (R / SR) * (K / SK);
     const dim3 grid((unsigned)blocks, 1, batch);
     switch (kind_of(mode)) {
         case 0: k_split_operand<0><<<grid, 256, 0, s>>>(p); break;
         case 1: k_split_operand<1><<<grid, 256, 0, s>>>(p); break;
-        case 3: {
-            if (!p.amax) return cudaErrorInvalidValue;
-            cudaError_t e = cudaMemsetAsync(p.amax, 0, sizeof(uint32_t) * (size_t)batch, s);
-            if (e != cudaSuccess) return e;
-            const unsigned ab = (unsigned)(blocks < ABSMAX_BLOCKS ? blocks : ABSMAX_BLOCKS);
-            k_absmax<<<dim3(ab, 1, batch), 256, 0, s>>>(p, blocks);
+        case 3:
+            if (!p.amax) return cudaErrorInvalidValue;  // launch_absmax ran before
             k_split_operand<3><<<grid, 256, 0, s>>>(p);
             break;
-        }
         default: k_split_operand<2><<<grid, 256, 0, s>>>(p); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const Operand& src, int bits, int batch, uint32_t* amax, cudaStream_t s) {
+    if (!amax || bits < 0 || bits > 40 || batch < 1 || batch > 65535) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(uint32_t) * (size_t)batch, s);
+    if (e != cudaSuccess) return e;
+    const int64_t n = 1ll << bits;
+    const int64_t want = (n + 2047) / 2048;
+    const unsigned blocks = (unsigned)(want < ABSMAX_BLOCKS ? (want < 1 ? 1 : want) : ABSMAX_BLOCKS);
+    k_absmax<<<dim3(blocks, 1, batch), 256, 0, s>>>(src.ptr, src.batch_stride, n, amax);
     return cudaGetLastError();
 }
 

@@ -631,6 +631,30 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
     const int pA = panel_bits(net, mode, g.mb, g.kb, b), pB = panel_bits(net, mode, g.nb, g.kb, b);
     const int mbp = g.mb - pA, nbp = g.nb - pB;
     const int64_t N = 1ll << g.nb;
+    // split FP16x2: one scale word per operand and batch entry, kept after the
+    // (panel-sized) plane data and computed once from the whole tensor
+    uint32_t* amax_a = nullptr;
+    uint32_t* amax_b = nullptr;
+    if (mode == TNC_SPLIT_FP16X2) {
+        // the linear scan needs each operand to be a dense block of 2^bits
+        // elements: distinct power-of-two strides that add up to 2^bits - 1
+        auto dense = [](const int64_t* r, int nr, const int64_t* k, int nk, const tnc::Operand& o) {
+            int64_t sum = 0, bits = 0;
+            for (int j = 0; j < nr; ++j) sum += r[j], bits |= r[j];
+            for (int j = 0; j < nk; ++j) sum += k[j], bits |= k[j];
+            for (int j = 0; j < o.n_sl; ++j) sum += o.sl_stride[j], bits |= o.sl_stride[j];
+            const int64_t n = (int64_t)1 << (nr + nk + o.n_sl);
+            return sum == n - 1 && bits == n - 1;
+        };
+        if (!dense(g.am, g.mb, g.ak, g.kb, g.A) || !dense(g.bn, g.nb, g.bk, g.kb, g.B))
+            return fail(TNC_E_STATE, "split FP16x2: an operand is not a dense tensor");
+        amax_a = reinterpret_cast<uint32_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, g.kb, b));
+        amax_b = reinterpret_cast<uint32_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, g.kb, b));
+        CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
+        CUDA_TRY(tnc::launch_absmax(g.A, g.mb + g.kb + g.A.n_sl, b, amax_a, s));
+        CUDA_TRY(tnc::launch_absmax(g.B, g.nb + g.kb + g.B.n_sl, b, amax_b, s));
+        CUDA_TRY(timed_end(net, s));
+    }
     for (int64_t qb = 0; qb < (1ll << pB); ++qb) {
         tnc::Operand B = g.B;
         for (int j = 0; j < pB; ++j)
@@ -643,8 +667,7 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
         for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.bk[j];
         sp.slice0 = g.slice0;
         sp.dst = pb;
-        if (mode == TNC_SPLIT_FP16X2)
-            sp.amax = reinterpret_cast<uint32_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, g.kb, b));
+        if (mode == TNC_SPLIT_FP16X2) sp.amax = amax_b;
         CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
         CUDA_TRY(tnc::launch_split(sp, mode, b, s));
         CUDA_TRY(timed_end(net, s));
@@ -661,9 +684,7 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
                 for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.ak[j];
                 sp.slice0 = g.slice0;
                 sp.dst = pa;
-                if (mode == TNC_SPLIT_FP16X2)
-                    sp.amax =
-                        reinterpret_cast<uint32_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, g.kb, b));
+                if (mode == TNC_SPLIT_FP16X2) sp.amax = amax_a;
                 CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
                 CUDA_TRY(tnc::launch_split(sp, mode, b, s));
                 CUDA_TRY(timed_end(net, s));
@@ -678,12 +699,8 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tp.err = net->d_err;
             tp.row_bytes = row_bytes >= 256 ? 128 : row_bytes;
             tp.pair = row_bytes == 256 ? 1 : (row_bytes == 512 ? 2 : 0);
-            if (mode == TNC_SPLIT_FP16X2) {
-                tp.amax_a = reinterpret_cast<const uint32_t*>(static_cast<const char*>(pa) +
-                                                              plane_data_bytes(mode, mbp, g.kb, b));
-                tp.amax_b = reinterpret_cast<const uint32_t*>(static_cast<const char*>(pb) +
-                                                              plane_data_bytes(mode, nbp, g.kb, b));
-            }
+            tp.amax_a = amax_a;
+            tp.amax_b = amax_b;
             tp.group_m = net->tc_group_m;
             tp.spin_limit = net->tc_spin_limit;
             tp.test_stall = net->tc_test_stall;

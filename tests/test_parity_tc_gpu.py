@@ -89,7 +89,7 @@ def test_c2_one_slice_split(lib, mode):
     assert err <= TOL[mode]
 
 
-@pytest.mark.parametrize("mode", [2, 1])
+@pytest.mark.parametrize("mode", [2, 1, 4])
 def test_panelled_planes_identical(lib, mode):
     """With the split-plane cap lowered to 64 KB the tensor-core contraction
     runs in row panels of A and B (4 x 2 here); every output tile is computed
