@@ -42,7 +42,7 @@ TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 *
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
-              4: "k_split_operand", 5: "k_cgemm_tc2", 6: "k_cgemm_tc_mc", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
+              4: "k_split_operand", 5: "k_cgemm_tc2", 6: "k_cgemm_tc_mc", 7: "k_ksplit_reduce", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
 
 
 def workload_name():
@@ -425,6 +425,13 @@ def c53_bench(args):
         torch.cuda.synchronize()
     net.check_device()
     T = ev0.elapsed_time(ev1) / 1e3
+    # per-launch breakdown on one more call (outside the timed subset)
+    net.set_timing(True)
+    net.contract(n, n + B, mode, out=out)
+    torch.cuda.synchronize()
+    recs, _ = net.last_timings()
+    net.set_timing(False)
+    by_kind = kernel_breakdown(recs)
     flops = node_flops(stats, n)
     split2 = net.contract(0, 2, mode, out=out).cpu().numpy()[0]
     t0 = time.perf_counter()
@@ -437,6 +444,8 @@ def c53_bench(args):
             "workspace_gb": ws.numel() / 1e9, "partial_amplitude": [float(acc[0].real), float(acc[0].imag)],
             "rel_err_vs_fp32_path_2_slices": float(abs(split2 - fp32) / abs(fp32)),
             "fp32_path_s_per_slice": t_fp32 / 2, "clocks": clk.summary(),
+            "kernel_time_ms_one_call": {KIND_NAMES.get(k, str(k)): v["ms"] for k, v in by_kind.items()},
+            "top_nodes_one_call": top_nodes(recs, stats, 10),
             "tuned_shapes": [e for e in tune_table() if e[0] == mode]}
     print(json.dumps(line))
     return 0

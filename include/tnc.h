@@ -263,7 +263,7 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable);
  * launch the node's tensor id, kernel kind (0 FP32 GEMM, 1 FP64 root reduction,
  * 2 GEMM root + FP64 slice sum, 3 tensor-core GEMM, 4 operand split,
  * 5 tensor-core GEMM on CTA pairs, 6 tensor-core GEMM on A-multicast clusters,
- * -1 leaf slice sum), slice batch, complex multiply-accumulates of the
+ * 7 reduction of a tensor-core GEMM's K-split partials, -1 leaf slice sum), slice batch, complex multiply-accumulates of the
  * launch (all its nodes and slices) and milliseconds; a grouped launch of
  * several nodes of one tree level reports node -1. Any output array may be NULL. *n_out receives the number
  * of records (TNC_E_INVALID if it exceeds cap); *n_launches (may be NULL) the

@@ -94,6 +94,9 @@ struct TcGemmParams {
                           // 2 = clusters of two CTAs sharing their A tile by multicast where N >= 256
     const uint32_t* amax_a;  // split FP16x2: the operands' scale words (SplitParams::amax), else null
     const uint32_t* amax_b;
+    int ksplit_bits;         // > 0: K is split over 2^ksplit_bits CTAs (grid y); each writes its FP32
+    float2* partial;         //   partial tile to partial[(split * batch + z) * M * N + m * N + n]
+    int accumulate;          // 1 (no K split): add the result into C instead of overwriting it
 };
 
 int tc_plane_count(int mode);
@@ -110,6 +113,10 @@ cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA
 // on 2-CTA clusters with the A tile multicast
 bool tc_uses_pair(const TcGemmParams& p);
 bool tc_uses_multicast(const TcGemmParams& p);
+// C[z][m][n] (+)= sum over s < 2^ksplit_bits, in order, of partial[s][z][m][n] (an FP64 sum
+// rounded once); C rows c_ld apart, batch entries c_batch_stride apart.
+cudaError_t launch_ksplit_reduce(const float2* partial, int ksplit_bits, int batch, int mb, int nb, float2* C,
+                                 int64_t c_batch_stride, int64_t c_ld, int accumulate, cudaStream_t s);
 
 // Adjoint pass. Root environment seed: E_z[sum_j bit_j(r) ostride[j]] = grad[r].
 struct SeedParams {

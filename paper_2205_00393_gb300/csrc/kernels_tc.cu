@@ -305,7 +305,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int m0 = (int)((grp * GROUP_M + in_grp % gm) * TM);
     const int n0 = (int)((in_grp / gm) * MC * TN) + (int)rank * TN;
     const int z = blockIdx.z;
-    const int nkb = (int)(K / C_::BK);
+    const int nkb = (int)((K >> p.ksplit_bits) / C_::BK);  // k-blocks of this CTA's K split
+    const int kb_off = (int)blockIdx.y * nkb;
     const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;  // k-blocks per chunk
     const int nchunks = nkb / kpc;
     const int n_it = nchunks * 3 * kpc;
@@ -361,12 +362,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if constexpr (MC == 2) {  // this CTA's 64 rows of every A part, to both CTAs
 #pragma unroll
                 for (int q = 0; q < C_::PARTS; ++q)
-                    tma_load_4d_mc(sa + q * PART_TILE_BYTES + rank * (PART_TILE_BYTES / 2), &tmA, kb * C_::BK,
-                                   m0 + (int)rank * (TM / 2), t * C_::PARTS + q, z, fb, (uint16_t)3);
+                    tma_load_4d_mc(sa + q * PART_TILE_BYTES + rank * (PART_TILE_BYTES / 2), &tmA,
+                                   (kb + kb_off) * C_::BK, m0 + (int)rank * (TM / 2), t * C_::PARTS + q, z, fb,
+                                   (uint16_t)3);
             } else {
-                tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, z, fb);
+                tma_load_4d(sa, &tmA, (kb + kb_off) * C_::BK, m0, t * C_::PARTS, z, fb);
             }
-            tma_load_4d(sa + STAGE_A, &tmB, kb * C_::BK, n0, t * C_::PARTS, z, fb);
+            tma_load_4d(sa + STAGE_A, &tmB, (kb + kb_off) * C_::BK, n0, t * C_::PARTS, z, fb);
             issued = it + 1;
         }
         if constexpr (MC == 2) {
@@ -504,12 +506,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int j = 0; j < 64; j += 2)
                 reinterpret_cast<float4*>(stg + lane * EPI_LDW + j)[0] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
             __syncwarp();
-            const int64_t ld = p.c_ld ? p.c_ld : N;
-            float2* cbase = p.C + (int64_t)z * p.c_batch_stride + (int64_t)(m0 + 32 * g) * ld + n0 + 64 * h;
+            const int64_t ld = p.ksplit_bits ? N : (p.c_ld ? p.c_ld : N);
+            float2* cb = p.ksplit_bits
+                             ? p.partial + ((int64_t)blockIdx.y * gridDim.z + z) * ((int64_t)N << p.mb)
+                             : p.C + (int64_t)z * p.c_batch_stride;
+            float2* cbase = cb + (int64_t)(m0 + 32 * g) * ld + n0 + 64 * h;
+            if (p.accumulate) {
 #pragma unroll 4
-            for (int r = 0; r < 32; ++r)
-                reinterpret_cast<float4*>(cbase + (int64_t)r * ld)[lane] =
-                    reinterpret_cast<const float4*>(stg + r * EPI_LDW)[lane];
+                for (int r = 0; r < 32; ++r) {
+                    float4* dst = reinterpret_cast<float4*>(cbase + (int64_t)r * ld) + lane;
+                    const float4 v = reinterpret_cast<const float4*>(stg + r * EPI_LDW)[lane];
+                    const float4 o = *dst;
+                    *dst = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+                }
+            } else {
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r)
+                    reinterpret_cast<float4*>(cbase + (int64_t)r * ld)[lane] =
+                        reinterpret_cast<const float4*>(stg + r * EPI_LDW)[lane];
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -986,6 +1001,34 @@ __global__ void __launch_bounds__(256) k_absmax(const float2* __restrict__ base,
     }
 }
 
+// ------------------------------------------------------------ K-split reduction
+// C[z][m][n] (+)= sum over splits, in order, of partial[split][z][m][n]: FP64
+// sums rounded once, two complex elements per thread step.
+__global__ void __launch_bounds__(256) k_ksplit_reduce(const float4* __restrict__ partial, int nsplit, int batch,
+                                                       int64_t mn2, int nb, float2* C, int64_t c_batch_stride,
+                                                       int64_t c_ld, int accumulate) {
+    const int z = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < mn2; i += (int64_t)gridDim.x * 256) {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int sp = 0; sp < nsplit; ++sp) {
+            const float4 v = partial[((int64_t)sp * batch + z) * mn2 + i];
+            a0 += v.x;
+            a1 += v.y;
+            a2 += v.z;
+            a3 += v.w;
+        }
+        const int64_t e = 2 * i;  // first of the two complex elements
+        const int64_t m = e >> nb, n = e & ((1ll << nb) - 1);
+        float4* dst = reinterpret_cast<float4*>(C + (int64_t)z * c_batch_stride + m * c_ld + n);
+        float4 r = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+        if (accumulate) {
+            const float4 o = *dst;
+            r = make_float4(o.x + r.x, o.y + r.y, o.z + r.z, o.w + r.w);
+        }
+        *dst = r;
+    }
+}
+
 // ------------------------------------------------------------ host helpers
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1049,8 +1092,9 @@ cudaError_t launch_tc_impl(const TcGemmParams& p, const void* planesA, const voi
         attr_set = true;
     }
     const int64_t tiles = (M / TM) * (N / TN);
+    if ((K >> p.ksplit_bits) < C_::BK || (p.ksplit_bits && (!p.partial || p.accumulate))) return cudaErrorInvalidValue;
     if constexpr (MC == 1) {
-        k_cgemm_tc<KIND, ROWB, 1><<<dim3((unsigned)tiles, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
+        k_cgemm_tc<KIND, ROWB, 1><<<dim3((unsigned)tiles, 1u << p.ksplit_bits, batch), NTHREADS, smem, s>>>(ta, tb, p);
         return cudaGetLastError();
     } else {
         cudaLaunchConfig_t cfg = {};
@@ -1106,12 +1150,12 @@ cudaError_t launch_tc_rows(const TcGemmParams& p, const void* pa, const void* pb
 
 // CTA pairs need 256-row tiles and K >= 64 (whole 128-byte k-blocks in every mode)
 bool tc_uses_pair(const TcGemmParams& p) {
-    return p.pair == 1 && p.row_bytes == 128 && p.mb >= 8 && p.kb >= 6;
+    return p.pair == 1 && p.row_bytes == 128 && p.mb >= 8 && p.kb >= 6 && !p.ksplit_bits && !p.accumulate;
 }
 
 // A multicast over a 2-CTA cluster needs an even number of column tiles
 bool tc_uses_multicast(const TcGemmParams& p) {
-    return p.pair == 2 && p.row_bytes == 128 && p.nb >= 8 && p.kb >= 6;
+    return p.pair == 2 && p.row_bytes == 128 && p.nb >= 8 && p.kb >= 6 && !p.ksplit_bits && !p.accumulate;
 }
 
 // tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts),
@@ -1138,6 +1182,17 @@ cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t
             break;
         default: k_split_operand<2><<<grid, 256, 0, s>>>(p); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ksplit_reduce(const float2* partial, int ksplit_bits, int batch, int mb, int nb, float2* C,
+                                 int64_t c_batch_stride, int64_t c_ld, int accumulate, cudaStream_t s) {
+    if (!partial || !C || ksplit_bits < 1 || batch < 1 || batch > 65535 || nb < 1) return cudaErrorInvalidValue;
+    const int64_t mn2 = (1ll << (mb + nb)) / 2;  // float4 steps of two complex elements
+    const int64_t want = (mn2 + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    k_ksplit_reduce<<<dim3(blocks, batch), 256, 0, s>>>(reinterpret_cast<const float4*>(partial), 1 << ksplit_bits,
+                                                        batch, mn2, nb, C, c_batch_stride, c_ld, accumulate);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,9 @@ constexpr int64_t kAlign = 256;
 int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Kernel chosen for a contraction node.
-enum NodeKind { K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_TC2 = 5, K_TCMC = 6 };
+enum NodeKind {
+    K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_TC2 = 5, K_TCMC = 6, K_KRED = 7
+};
 
 // Tensor-core eligibility of a non-root node in a split mode: both output
 // sides span whole 128-wide tiles and K spans whole 64-wide k-blocks.
@@ -356,16 +358,45 @@ int64_t full_planes_bytes(int mode, int rb, int kb, int64_t batch) {
     return plane_data_bytes(mode, rb, kb, batch) + scale_words;
 }
 
-// Panel bits p (2^p panels) so that one panel's planes fit the cap.
-int panel_bits(const tnc_net* net, int mode, int rb, int kb, int64_t batch) {
+// How one tensor-core contraction is cut up:
+//  - planes of one operand are capped (tc_plane_cap_log2): when K is the
+//    largest dimension the contraction runs as 2^pK sequential K panels (each
+//    launch keeps every output tile and adds into C after the first);
+//    otherwise the top row bits of A (pA) and of B (pB) are fixed in panels;
+//  - with fewer than four waves of output tiles (152 SMs), K is also split
+//    across 2^ks CTAs of one launch (at least 4096 K per split) whose FP32
+//    partials a reduction adds in a fixed order.
+// The workspace holds, per operand, the planes of one panel (plus the split
+// FP16x2 scale words), and for A also the partials of one launch.
+struct TcCut {
+    int pA = 0, pB = 0, pK = 0, ks = 0;
+    int64_t a_bytes = 0, b_bytes = 0, partial_off = 0;
+};
+
+TcCut tc_cut(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch) {
     const int64_t cap = (int64_t)1 << net_plane_cap_log2(net);
-    int p = 0;
-    while (p < rb - 7 && full_planes_bytes(mode, rb - p, kb, batch) > cap) ++p;
-    return p;
+    TcCut c;
+    auto fits = [&](int rb, int k) { return full_planes_bytes(mode, rb, k, batch) <= cap; };
+    if (kb > mb && kb > nb) {
+        while (kb - c.pK > 6 && !(fits(mb, kb - c.pK) && fits(nb, kb - c.pK))) ++c.pK;
+    }
+    while (c.pA < mb - 7 && !fits(mb - c.pA, kb - c.pK)) ++c.pA;
+    while (c.pB < nb - 7 && !fits(nb - c.pB, kb - c.pK)) ++c.pB;
+    const int64_t tiles = batch << ((mb - c.pA - 7) + (nb - c.pB - 7));
+    while (c.ks < 6 && (tiles << c.ks) < 4 * 152 && kb - c.pK - c.ks > 12) ++c.ks;
+    c.partial_off = full_planes_bytes(mode, mb - c.pA, kb - c.pK, batch);
+    const int64_t partials = c.ks ? (batch << (c.ks + (mb - c.pA) + (nb - c.pB))) * 8 : 0;
+    c.a_bytes = c.partial_off + partials;
+    c.b_bytes = full_planes_bytes(mode, nb - c.pB, kb - c.pK, batch);
+    return c;
 }
 
-int64_t planes_bytes(const tnc_net* net, int mode, int rb, int kb, int64_t batch) {
-    return full_planes_bytes(mode, rb - panel_bits(net, mode, rb, kb, batch), kb, batch);
+int64_t tc_bytes_a(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch) {
+    return tc_cut(net, mode, mb, nb, kb, batch).a_bytes;
+}
+
+int64_t tc_bytes_b(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch) {
+    return tc_cut(net, mode, mb, nb, kb, batch).b_bytes;
 }
 
 // First-fit simulation of the workspace for a batch of `nb` slices.
@@ -393,8 +424,8 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
     auto release = [&](int64_t off) { used.erase(off); };
     auto tc_planes = [&](const NodePlan& np, int64_t b) {
         const size_t i = np.v - net->n_leaves;
-        ar.planes_a[i] = alloc(planes_bytes(net, mode, np.mb, np.kb, b));
-        ar.planes_b[i] = alloc(planes_bytes(net, mode, np.nb, np.kb, b));
+        ar.planes_a[i] = alloc(tc_bytes_a(net, mode, np.mb, np.nb, np.kb, b));
+        ar.planes_b[i] = alloc(tc_bytes_b(net, mode, np.mb, np.nb, np.kb, b));
     };
     auto tc_release = [&](const NodePlan& np) {
         const size_t i = np.v - net->n_leaves;
@@ -623,14 +654,16 @@ tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, in
                      cudaStream_t s);
 
 // Split + tensor-core GEMM for the contraction described by g (operands,
-// per-bit strides, output); planes are workspace temporaries of the sizes
-// planes_bytes() gives for (mb, kb) and (nb, kb).
+// per-bit strides, output), cut up as tc_cut() says; pa and pb are workspace
+// temporaries of tc_bytes_a() and tc_bytes_b() bytes.
 tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, int mode, void* pa, void* pb,
                                  int node, cudaStream_t s, int row_bytes) {
-    // panels: fix the top pA bits of m (A rows) and pB bits of n (B rows)
-    const int pA = panel_bits(net, mode, g.mb, g.kb, b), pB = panel_bits(net, mode, g.nb, g.kb, b);
-    const int mbp = g.mb - pA, nbp = g.nb - pB;
+    const TcCut cut = tc_cut(net, mode, g.mb, g.nb, g.kb, b);
+    const int pA = cut.pA, pB = cut.pB, pK = cut.pK;
+    const int mbp = g.mb - pA, nbp = g.nb - pB, kbp = g.kb - pK;
     const int64_t N = 1ll << g.nb;
+    if (cut.ks || pK) row_bytes = row_bytes >= 256 ? 128 : row_bytes;  // K splits: single-CTA tiles
+    float2* partial = cut.ks ? reinterpret_cast<float2*>(static_cast<char*>(pa) + cut.partial_off) : nullptr;
     // split FP16x2: one scale word per operand and batch entry, kept after the
     // (panel-sized) plane data and computed once from the whole tensor
     uint32_t* amax_a = nullptr;
@@ -648,66 +681,77 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
         };
         if (!dense(g.am, g.mb, g.ak, g.kb, g.A) || !dense(g.bn, g.nb, g.bk, g.kb, g.B))
             return fail(TNC_E_STATE, "split FP16x2: an operand is not a dense tensor");
-        amax_a = reinterpret_cast<uint32_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, g.kb, b));
-        amax_b = reinterpret_cast<uint32_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, g.kb, b));
+        amax_a = reinterpret_cast<uint32_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, kbp, b));
+        amax_b = reinterpret_cast<uint32_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, kbp, b));
         CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
         CUDA_TRY(tnc::launch_absmax(g.A, g.mb + g.kb + g.A.n_sl, b, amax_a, s));
         CUDA_TRY(tnc::launch_absmax(g.B, g.nb + g.kb + g.B.n_sl, b, amax_b, s));
         CUDA_TRY(timed_end(net, s));
     }
-    for (int64_t qb = 0; qb < (1ll << pB); ++qb) {
-        tnc::Operand B = g.B;
-        for (int j = 0; j < pB; ++j)
-            if ((qb >> j) & 1) B.ptr += g.bn[nbp + j];
+    auto split = [&](const tnc::Operand& src, int rb, const int64_t* rs, const int64_t* ks, void* dst,
+                     uint32_t* amax) -> tnc_status {
         tnc::SplitParams sp{};
-        sp.src = B;
-        sp.rb = nbp;
-        sp.kb = g.kb;
-        for (int j = 0; j < nbp; ++j) sp.rs[j] = g.bn[j];
-        for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.bk[j];
+        sp.src = src;
+        sp.rb = rb;
+        sp.kb = kbp;
+        for (int j = 0; j < rb; ++j) sp.rs[j] = rs[j];
+        for (int j = 0; j < kbp; ++j) sp.ks[j] = ks[j];
         sp.slice0 = g.slice0;
-        sp.dst = pb;
-        if (mode == TNC_SPLIT_FP16X2) sp.amax = amax_b;
+        sp.dst = dst;
+        sp.amax = amax;
         CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
         CUDA_TRY(tnc::launch_split(sp, mode, b, s));
         CUDA_TRY(timed_end(net, s));
-        for (int64_t qa = 0; qa < (1ll << pA); ++qa) {
-            tnc::Operand A = g.A;
-            for (int j = 0; j < pA; ++j)
-                if ((qa >> j) & 1) A.ptr += g.am[mbp + j];
-            if (pB == 0 || qb == 0 || pA > 0) {
-                sp = tnc::SplitParams{};
-                sp.src = A;
-                sp.rb = mbp;
-                sp.kb = g.kb;
-                for (int j = 0; j < mbp; ++j) sp.rs[j] = g.am[j];
-                for (int j = 0; j < g.kb; ++j) sp.ks[j] = g.ak[j];
-                sp.slice0 = g.slice0;
-                sp.dst = pa;
-                if (mode == TNC_SPLIT_FP16X2) sp.amax = amax_a;
-                CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
-                CUDA_TRY(tnc::launch_split(sp, mode, b, s));
-                CUDA_TRY(timed_end(net, s));
+        return TNC_OK;
+    };
+    tnc_status st;
+    for (int64_t qk = 0; qk < (1ll << pK); ++qk) {  // K panels: the top pK bits of k fixed
+        tnc::Operand Ak = g.A, Bk = g.B;
+        for (int j = 0; j < pK; ++j)
+            if ((qk >> j) & 1) {
+                Ak.ptr += g.ak[kbp + j];
+                Bk.ptr += g.bk[kbp + j];
             }
-            tnc::TcGemmParams tp{};
-            tp.mb = mbp;
-            tp.nb = nbp;
-            tp.kb = g.kb;
-            tp.C = g.C + (qa << mbp) * N + (qb << nbp);
-            tp.c_batch_stride = g.c_batch_stride;
-            tp.c_ld = N;
-            tp.err = net->d_err;
-            tp.row_bytes = row_bytes >= 256 ? 128 : row_bytes;
-            tp.pair = row_bytes == 256 ? 1 : (row_bytes == 512 ? 2 : 0);
-            tp.amax_a = amax_a;
-            tp.amax_b = amax_b;
-            tp.group_m = net->tc_group_m;
-            tp.spin_limit = net->tc_spin_limit;
-            tp.test_stall = net->tc_test_stall;
-            CUDA_TRY(timed_begin(net, node, tnc::tc_uses_pair(tp) ? K_TC2 : (tnc::tc_uses_multicast(tp) ? K_TCMC : K_TC), b, s,
-                                 std::ldexp(1.0, mbp + nbp + g.kb) * b));
-            CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
-            CUDA_TRY(timed_end(net, s));
+        for (int64_t qb = 0; qb < (1ll << pB); ++qb) {  // row panels of B: top pB bits of n fixed
+            tnc::Operand B = Bk;
+            for (int j = 0; j < pB; ++j)
+                if ((qb >> j) & 1) B.ptr += g.bn[nbp + j];
+            if ((st = split(B, nbp, g.bn, g.bk, pb, amax_b)) != TNC_OK) return st;
+            for (int64_t qa = 0; qa < (1ll << pA); ++qa) {  // row panels of A: top pA bits of m fixed
+                tnc::Operand A = Ak;
+                for (int j = 0; j < pA; ++j)
+                    if ((qa >> j) & 1) A.ptr += g.am[mbp + j];
+                if (pB == 0 || qb == 0 || pA > 0)  // else the A planes of this K panel are still in place
+                    if ((st = split(A, mbp, g.am, g.ak, pa, amax_a)) != TNC_OK) return st;
+                tnc::TcGemmParams tp{};
+                tp.mb = mbp;
+                tp.nb = nbp;
+                tp.kb = kbp;
+                tp.C = g.C + (qa << mbp) * N + (qb << nbp);
+                tp.c_batch_stride = g.c_batch_stride;
+                tp.c_ld = N;
+                tp.err = net->d_err;
+                tp.row_bytes = row_bytes >= 256 ? 128 : row_bytes;
+                tp.pair = row_bytes == 256 ? 1 : (row_bytes == 512 ? 2 : 0);
+                tp.amax_a = amax_a;
+                tp.amax_b = amax_b;
+                tp.group_m = net->tc_group_m;
+                tp.spin_limit = net->tc_spin_limit;
+                tp.test_stall = net->tc_test_stall;
+                tp.ksplit_bits = cut.ks;
+                tp.partial = partial;
+                tp.accumulate = (!cut.ks && qk > 0) ? 1 : 0;
+                CUDA_TRY(timed_begin(net, node, tnc::tc_uses_pair(tp) ? K_TC2 : (tnc::tc_uses_multicast(tp) ? K_TCMC : K_TC),
+                                     b, s, std::ldexp(1.0, mbp + nbp + kbp) * b));
+                CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
+                CUDA_TRY(timed_end(net, s));
+                if (cut.ks) {  // add the K splits' partials into C, in split order
+                    CUDA_TRY(timed_begin(net, node, K_KRED, b, s, 0.0));
+                    CUDA_TRY(tnc::launch_ksplit_reduce(partial, cut.ks, b, mbp, nbp, tp.C, g.c_batch_stride, N,
+                                                       qk > 0 ? 1 : 0, s));
+                    CUDA_TRY(timed_end(net, s));
+                }
+            }
         }
     }
     return TNC_OK;
@@ -822,8 +866,8 @@ tnc_status env_child(Backward& bw, const NodePlan& np, int c, int64_t b, int64_t
     const bool tc = env_choice != 0;
     int64_t pa = -1, pb = -1;
     if (tc) {  // split-precision planes (allocated in the sizing pass too)
-        pa = bw.A.alloc(planes_bytes(bw.net, bw.mode, gmb, gkb, b));
-        pb = bw.A.alloc(planes_bytes(bw.net, bw.mode, gnb, gkb, b));
+        pa = bw.A.alloc(tc_bytes_a(bw.net, bw.mode, gmb, gnb, gkb, b));
+        pb = bw.A.alloc(tc_bytes_b(bw.net, bw.mode, gmb, gnb, gkb, b));
     }
     if (!bw.exec) {
         if (tc) {
@@ -983,8 +1027,8 @@ tnc_status fwd_node(Backward& bw, const NodePlan& np, int64_t b, int64_t slice0)
     const bool tc = shape_choice(net, bw.mode, np.mb, np.nb, np.kb, np.is_root) != 0;
     const size_t i = np.v - net->n_leaves;
     if (tc) {
-        bw.fwd.planes_a[i] = bw.A.alloc(planes_bytes(net, bw.mode, np.mb, np.kb, per ? b : 1));
-        bw.fwd.planes_b[i] = bw.A.alloc(planes_bytes(net, bw.mode, np.nb, np.kb, per ? b : 1));
+        bw.fwd.planes_a[i] = bw.A.alloc(tc_bytes_a(net, bw.mode, np.mb, np.nb, np.kb, per ? b : 1));
+        bw.fwd.planes_b[i] = bw.A.alloc(tc_bytes_b(net, bw.mode, np.mb, np.nb, np.kb, per ? b : 1));
     }
     if (bw.exec) {
         tnc::GemmParams g = gemm_params(net, bw.fwd, bw.ws, np, b);
