@@ -223,8 +223,10 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  fits the budget
  *  "tc_plane_cap_log2" 16..40 (default 32): split-precision operand planes of
  *                  one contraction are limited to 2^value bytes per operand;
- *                  larger operands are processed in panels of whole 128-row
- *                  tiles (results unchanged, workspace smaller)
+ *                  larger operands are processed in panels: of K when K is
+ *                  the largest dimension (each panel's launch adds into the
+ *                  output), else of whole 128-row tiles (results unchanged up
+ *                  to the order of the K sum; workspace smaller)
  *  "cache_invariants" 0 (default) or 1: keep the slice-invariant tensors that
  *                  feed per-slice contractions in the workspace between calls
  *                  and skip their recomputation while the plan, leaf data,
