@@ -208,10 +208,75 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_f32_group(const GemmParams* __re
     gemm_tile(params[lo], b - tile_off[lo], blockIdx.z, slice0, sm);
 }
 
+// Sum over this thread's k in [k_lo, k_hi) (k = k_lo + lane, + lanes, ...) of
+// A[k] B[k] for the final contraction. When the block's K range holds whole
+// rows of lanes, k = lanes * j + lane: the low bits are the lane (one offset
+// per thread) and the offsets of j's bits come from shared-memory tables ta,
+// tb, one per 8-bit group (K <= 2^40); products are summed in FP32 over runs
+// of 16 j and the runs in FP64. Called by every thread of the block.
+__device__ void root_dot(const GemmParams& p, const float2* A, const float2* B, int64_t k_lo, int64_t k_hi,
+                         int lane, int lanes, int64_t (*root_ta)[256], int64_t (*root_tb)[256], double& re,
+                         double& im) {
+    const int64_t kc = k_hi - k_lo;
+    int lb = 0;
+    while ((1 << lb) < lanes) ++lb;
+    if (kc >= lanes) {
+        // k = lanes * j + lane: the low lb bits are the lane (one offset per
+        // thread); the offsets of j's bits come from shared-memory tables, one
+        // per 8-bit group. Products are summed in FP32 over runs of 16 j and
+        // the runs in FP64.
+        const int jb = p.kb - lb, ng = (jb + 7) / 8;
+        for (int idx = threadIdx.x; idx < ng * 256; idx += 256) {
+            const int g = idx >> 8, e = idx & 255;
+            int64_t oa = 0, ob = 0;
+            for (int t = 0; t < 8; ++t) {
+                const int bit = lb + 8 * g + t;
+                if (bit < p.kb && ((e >> t) & 1)) {
+                    oa += p.ak[bit];
+                    ob += p.bk[bit];
+                }
+            }
+            root_ta[g][e] = oa;
+            root_tb[g][e] = ob;
+        }
+        __syncthreads();
+        const float2* Al = A + bits_offset(lane, p.ak, lb, 0);
+        const float2* Bl = B + bits_offset(lane, p.bk, lb, 0);
+        const int64_t j_lo = k_lo >> lb, j_hi = k_hi >> lb;
+        for (int64_t j0 = j_lo; j0 < j_hi; j0 += 16) {
+            const int64_t je = j0 + 16 < j_hi ? j0 + 16 : j_hi;
+            float sr = 0.f, si = 0.f;
+            for (int64_t j = j0; j < je; ++j) {
+                int64_t oa = 0, ob = 0;
+                for (int g = 0; g < ng; ++g) {
+                    const int e = (int)((j >> (8 * g)) & 255);
+                    oa += root_ta[g][e];
+                    ob += root_tb[g][e];
+                }
+                const float2 a = Al[oa], b = Bl[ob];
+                sr = fmaf(a.x, b.x, sr);
+                sr = fmaf(-a.y, b.y, sr);
+                si = fmaf(a.x, b.y, si);
+                si = fmaf(a.y, b.x, si);
+            }
+            re += sr;
+            im += si;
+        }
+    } else {
+        for (int64_t k = k_lo + lane; k < k_hi; k += lanes) {
+            float2 a = A[bits_offset(k, p.ak, p.kb, 0)];
+            float2 b = B[bits_offset(k, p.bk, p.kb, 0)];
+            re += (double)a.x * b.x - (double)a.y * b.y;
+            im += (double)a.x * b.y + (double)a.y * b.x;
+        }
+    }
+}
+
 // FP64 partial sums of a contraction with R = M*N <= 64 outputs.
 __global__ void __launch_bounds__(256) k_root_partials(const __grid_constant__ RootParams rp,
                                                        double2* __restrict__ partials) {
     __shared__ double2 red[256];
+    __shared__ int64_t root_ta[5][256], root_tb[5][256];  // offsets of 8-bit groups of j (K <= 2^40)
     const GemmParams& p = rp.g;
     const int R = 1 << (p.mb + p.nb);
     const int lanes = 256 / R;
@@ -225,12 +290,7 @@ __global__ void __launch_bounds__(256) k_root_partials(const __grid_constant__ R
     const int64_t kc = K / rp.chunks;
     const int64_t k_lo = blockIdx.x * kc, k_hi = k_lo + kc;
     double re = 0.0, im = 0.0;
-    for (int64_t k = k_lo + lane; k < k_hi; k += lanes) {
-        float2 a = A[bits_offset(k, p.ak, p.kb, 0)];
-        float2 b = B[bits_offset(k, p.bk, p.kb, 0)];
-        re += (double)a.x * b.x - (double)a.y * b.y;
-        im += (double)a.x * b.y + (double)a.y * b.x;
-    }
+    root_dot(p, A, B, k_lo, k_hi, lane, lanes, root_ta, root_tb, re, im);
     red[threadIdx.x] = make_double2(re, im);
     __syncthreads();
     for (int st = lanes / 2; st > 0; st >>= 1) {
@@ -317,6 +377,7 @@ __global__ void __launch_bounds__(256) k_root_partials_multi(const RootParams* _
                                                              const int64_t* __restrict__ rs0,
                                                              const int* __restrict__ rb) {
     __shared__ double2 red[256];
+    __shared__ int64_t root_ta[5][256], root_tb[5][256];
     const int64_t x = blockIdx.x;
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -340,12 +401,7 @@ __global__ void __launch_bounds__(256) k_root_partials_multi(const RootParams* _
     const int64_t kc = K / rp.chunks;
     const int64_t k_lo = chunk * kc, k_hi = k_lo + kc;
     double re = 0.0, im = 0.0;
-    for (int64_t k = k_lo + lane; k < k_hi; k += lanes) {
-        float2 a = A[bits_offset(k, p.ak, p.kb, 0)];
-        float2 bb = B[bits_offset(k, p.bk, p.kb, 0)];
-        re += (double)a.x * bb.x - (double)a.y * bb.y;
-        im += (double)a.x * bb.y + (double)a.y * bb.x;
-    }
+    root_dot(p, A, B, k_lo, k_hi, lane, lanes, root_ta, root_tb, re, im);
     red[threadIdx.x] = make_double2(re, im);
     __syncthreads();
     for (int st = lanes / 2; st > 0; st >>= 1) {
