@@ -344,11 +344,9 @@ int64_t tensor_bytes(const Plan& P, int v) { return (int64_t)8 << P.layout[v].si
 
 std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice);
 
-// Split-precision planes of one operand are capped (tc_plane_cap_log2, 2^32
-// bytes by default): a larger operand is processed in panels of its rows
-// (whole 128-row tiles, top row bits fixed).
-// Plane data of one operand; split FP16x2 keeps the operand's scale words
-// (one uint32 per batch entry) after it.
+// Plane data of one operand (rows x K, every plane, every batch entry); split
+// FP16x2 keeps the operand's scale words (one uint32 per batch entry) after
+// it. How a contraction whose planes exceed the cap is cut up: tc_cut below.
 int64_t plane_data_bytes(int mode, int rb, int kb, int64_t batch) {
     return batch * (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode) << (rb + kb);
 }
