@@ -619,9 +619,13 @@ def main():
                     help="time the adjoint pass (leaf environments of all fSim gates) instead")
     ap.add_argument("--single-node", default=None,
                     help="MB,NB,KB: time one isolated contraction node (log2 sizes) instead")
-    ap.add_argument("--slices-per-step", type=int, default=2)
+    ap.add_argument("--slices-per-step", type=int, default=None,
+                    help="slices per tnc_contract call (default 4 for the 30-qubit line, 2 for the other modes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.slices_per_step is None:
+        plain = not (args.grad42 or args.c53 or args.many or args.backward or args.single_node)
+        args.slices_per_step = 4 if plain else 2
     if args.mode is None:
         if args.grad42:
             args.mode = "fp32"
