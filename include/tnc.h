@@ -198,7 +198,10 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
                              int mode, double* const* outs_c128, int use_graph, void* stream);
 
 /* JSON statistics of the current plan: Eq. 1 cost, Eq. 3 cost, Eq. 2
- * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace. */
+ * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace, and
+ * "tc_cuts": per split mode, [node index, A row-panel bits, B row-panel bits,
+ * K-panel bits, K-split bits] of every tensor-core-eligible contraction for
+ * the last batch size ("tc_cut_batch"). */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 
 /* Tuning options of the tensor-core GEMM (no effect on results):

@@ -2082,6 +2082,25 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
             first = false;
         }
         o << "]";
+        // how each tensor-core-eligible contraction is cut up in the split
+        // modes, for the last batch size (1 before any call)
+        const int64_t cb = net->last_batch > 0 ? net->last_batch : 1;
+        o << ",\"tc_cut_batch\":" << cb << ",\"tc_cuts\":{";
+        const int cut_modes[4] = {TNC_SPLIT_TF32, TNC_SPLIT_BF16, TNC_SPLIT_BF16X2, TNC_SPLIT_FP16X2};
+        for (int mi = 0; mi < 4; ++mi) {
+            const int mode = cut_modes[mi];
+            o << (mi ? "," : "") << "\"" << mode << "\":[";
+            bool f2 = true;
+            for (size_t i = 0; i < net->plan.nodes.size(); ++i) {
+                const NodePlan& np = net->plan.nodes[i];
+                if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) continue;
+                const TcCut c = tc_cut(net, mode, np.mb, np.nb, np.kb, np.per_slice ? cb : 1);
+                o << (f2 ? "" : ",") << "[" << i << "," << c.pA << "," << c.pB << "," << c.pK << "," << c.ks << "]";
+                f2 = false;
+            }
+            o << "]";
+        }
+        o << "}";
     } else {
         o << ",\"plan_error\":\"" << perr << "\"";
     }

@@ -136,3 +136,47 @@ def test_eq3_wide_costs(libtnc):
     st = net.stats()
     assert int(st["eq3"]) == tree.eq3(S1) and tree.eq3(S1) > 2 ** 100
     assert int(st["eq1"]) == tree.eq1()
+
+
+def test_tensor_core_cuts_on_the_53_qubit_plan():
+    """tnc_stats reports how every tensor-core-eligible contraction is cut up
+    (host logic, no GPU): K panels only for K-dominant contractions whose
+    planes exceed the cap, each row or K panel within the cap unless it is
+    already a single 128-row tile (or 64 of K), and K splits only while the
+    output tiles fill fewer than four waves of 152 SMs, keeping at least 4096
+    of K per split. On the 53-qubit lattice both K-dominant nodes run in K
+    panels, and the one with few output tiles also splits K."""
+    from tnc_inputs import circuit_to_network, lattice_53q_rqc
+    from paper_2205_00393_gb300 import Network
+    net = Network.from_tn(circuit_to_network(lattice_53q_rqc(20, 3)).as_complex64())
+    net.set_path(net.greedy_path())
+    net.set_slices(net.find_slices(30, 7))
+    st = net.stats()
+    b = st["tc_cut_batch"]
+    cap = 1 << 32
+    planes = {"1": (6, 4), "2": (9, 2), "3": (6, 2), "4": (6, 2)}  # (planes, bytes per element)
+    seen = {}
+    for mode, cuts in st["tc_cuts"].items():
+        n_pl, elem = planes[mode]
+        for i, pA, pB, pK, ks in cuts:
+            mb, nb, kb = st["nodes"][i][:3]
+            per = st["nodes"][i][3]
+            bb = b if per else 1
+
+            def fits(rb, k):
+                return bb * n_pl * elem * (1 << (rb + k)) + (256 if mode == "4" else 0) <= cap
+            if pK:
+                assert kb > max(mb, nb)
+                assert fits(mb, kb - pK) and fits(nb, kb - pK) or kb - pK == 6
+                assert not (fits(mb, kb - pK + 1) and fits(nb, kb - pK + 1))
+            assert fits(mb - pA, kb - pK) or mb - pA == 7
+            assert fits(nb - pB, kb - pK) or nb - pB == 7
+            tiles = bb << ((mb - pA - 7) + (nb - pB - 7))
+            if ks:
+                assert (tiles << (ks - 1)) < 4 * 152 and kb - pK - ks >= 12
+            else:
+                assert tiles >= 4 * 152 or kb - pK <= 12
+            seen[(mode, mb, nb, kb)] = (pA, pB, pK, ks)
+    for mode in ("1", "2", "4"):
+        assert seen[(mode, 12, 12, 18)][2] > 0
+        assert seen[(mode, 11, 10, 19)][2] > 0 and seen[(mode, 11, 10, 19)][3] > 0
