@@ -97,6 +97,8 @@ struct TcGemmParams {
     int ksplit_bits;         // > 0: K is split over 2^ksplit_bits CTAs (grid y); each writes its FP32
     float2* partial;         //   partial tile to partial[(split * batch + z) * M * N + m * N + n]
     int accumulate;          // 1 (no K split): add the result into C instead of overwriting it
+    int a_shared, b_shared;  // 1: the operand is the same for every batch entry; its planes and scale
+                             //   word exist once (batch entry 0)
 };
 
 int tc_plane_count(int mode);

@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int m0 = (int)((grp * GROUP_M + in_grp % gm) * TM);
     const int n0 = (int)((in_grp / gm) * MC * TN) + (int)rank * TN;
     const int z = blockIdx.z;
+    const int za = p.a_shared ? 0 : z, zb = p.b_shared ? 0 : z;  // batch entry of each operand's planes
     const int nkb = (int)((K >> p.ksplit_bits) / C_::BK);  // k-blocks of this CTA's K split
     const int kb_off = (int)blockIdx.y * nkb;
     const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;  // k-blocks per chunk
@@ -363,12 +364,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int q = 0; q < C_::PARTS; ++q)
                     tma_load_4d_mc(sa + q * PART_TILE_BYTES + rank * (PART_TILE_BYTES / 2), &tmA,
-                                   (kb + kb_off) * C_::BK, m0 + (int)rank * (TM / 2), t * C_::PARTS + q, z, fb,
+                                   (kb + kb_off) * C_::BK, m0 + (int)rank * (TM / 2), t * C_::PARTS + q, za, fb,
                                    (uint16_t)3);
             } else {
-                tma_load_4d(sa, &tmA, (kb + kb_off) * C_::BK, m0, t * C_::PARTS, z, fb);
+                tma_load_4d(sa, &tmA, (kb + kb_off) * C_::BK, m0, t * C_::PARTS, za, fb);
             }
-            tma_load_4d(sa + STAGE_A, &tmB, (kb + kb_off) * C_::BK, n0, t * C_::PARTS, z, fb);
+            tma_load_4d(sa + STAGE_A, &tmB, (kb + kb_off) * C_::BK, n0, t * C_::PARTS, zb, fb);
             issued = it + 1;
         }
         if constexpr (MC == 2) {
@@ -491,7 +492,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         } else {
             if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
-                const float sa = pow2f(-fp16_scale_exp(p.amax_a[z])), sb = pow2f(-fp16_scale_exp(p.amax_b[z]));
+                const float sa = pow2f(-fp16_scale_exp(p.amax_a[p.a_shared ? 0 : z])),
+                            sb = pow2f(-fp16_scale_exp(p.amax_b[p.b_shared ? 0 : z]));
 #pragma unroll
                 for (int j = 0; j < 64; ++j) {
                     cr[j] = cr[j] * sa * sb;
@@ -684,8 +686,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             const uint32_t sa = smem_u32(smem + s * C_::STAGE_BYTES);
             const uint32_t fb = smem_u32(&full_bar[s]);
             mbar_expect_tx(fb, C_::STAGE_BYTES);
-            tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, z, fb);
-            tma_load_4d(sa + C_::STAGE_A, &tmB, kb * C_::BK, nb0, t * C_::PARTS, z, fb);
+            tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, p.a_shared ? 0 : z, fb);
+            tma_load_4d(sa + C_::STAGE_A, &tmB, kb * C_::BK, nb0, t * C_::PARTS, p.b_shared ? 0 : z, fb);
             issued = it + 1;
         }
         if (*abort_flag || issued < n_it) {
@@ -812,7 +814,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             if (lane == 0 && !abort_sh) raise_abort_pair(abort_flag, peer_abort, p.err);
         } else {
             if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
-                const float sa = pow2f(-fp16_scale_exp(p.amax_a[z])), sb = pow2f(-fp16_scale_exp(p.amax_b[z]));
+                const float sa = pow2f(-fp16_scale_exp(p.amax_a[p.a_shared ? 0 : z])),
+                            sb = pow2f(-fp16_scale_exp(p.amax_b[p.b_shared ? 0 : z]));
 #pragma unroll
                 for (int j = 0; j < 64; ++j) {
                     cr[j] = cr[j] * sa * sb;

@@ -660,6 +660,11 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
     const int pA = cut.pA, pB = cut.pB, pK = cut.pK;
     const int mbp = g.mb - pA, nbp = g.nb - pB, kbp = g.kb - pK;
     const int64_t N = 1ll << g.nb;
+    // an operand that is the same for every slice of the batch (no sliced
+    // modes, no batch stride) is split and scanned once
+    const bool a_shared = b > 1 && g.A.batch_stride == 0 && g.A.n_sl == 0;
+    const bool b_shared = b > 1 && g.B.batch_stride == 0 && g.B.n_sl == 0;
+    const int nza = a_shared ? 1 : b, nzb = b_shared ? 1 : b;
     if (cut.ks || pK) row_bytes = row_bytes >= 256 ? 128 : row_bytes;  // K splits: single-CTA tiles
     float2* partial = cut.ks ? reinterpret_cast<float2*>(static_cast<char*>(pa) + cut.partial_off) : nullptr;
     // split FP16x2: one scale word per operand and batch entry, kept after the
@@ -682,12 +687,12 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
         amax_a = reinterpret_cast<uint32_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, kbp, b));
         amax_b = reinterpret_cast<uint32_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, kbp, b));
         CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
-        CUDA_TRY(tnc::launch_absmax(g.A, g.mb + g.kb + g.A.n_sl, b, amax_a, s));
-        CUDA_TRY(tnc::launch_absmax(g.B, g.nb + g.kb + g.B.n_sl, b, amax_b, s));
+        CUDA_TRY(tnc::launch_absmax(g.A, g.mb + g.kb + g.A.n_sl, nza, amax_a, s));
+        CUDA_TRY(tnc::launch_absmax(g.B, g.nb + g.kb + g.B.n_sl, nzb, amax_b, s));
         CUDA_TRY(timed_end(net, s));
     }
     auto split = [&](const tnc::Operand& src, int rb, const int64_t* rs, const int64_t* ks, void* dst,
-                     uint32_t* amax) -> tnc_status {
+                     uint32_t* amax, int nz) -> tnc_status {
         tnc::SplitParams sp{};
         sp.src = src;
         sp.rb = rb;
@@ -697,8 +702,8 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
         sp.slice0 = g.slice0;
         sp.dst = dst;
         sp.amax = amax;
-        CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
-        CUDA_TRY(tnc::launch_split(sp, mode, b, s));
+        CUDA_TRY(timed_begin(net, node, K_SPLIT, nz, s, 0.0));
+        CUDA_TRY(tnc::launch_split(sp, mode, nz, s));
         CUDA_TRY(timed_end(net, s));
         return TNC_OK;
     };
@@ -714,13 +719,13 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tnc::Operand B = Bk;
             for (int j = 0; j < pB; ++j)
                 if ((qb >> j) & 1) B.ptr += g.bn[nbp + j];
-            if ((st = split(B, nbp, g.bn, g.bk, pb, amax_b)) != TNC_OK) return st;
+            if ((st = split(B, nbp, g.bn, g.bk, pb, amax_b, nzb)) != TNC_OK) return st;
             for (int64_t qa = 0; qa < (1ll << pA); ++qa) {  // row panels of A: top pA bits of m fixed
                 tnc::Operand A = Ak;
                 for (int j = 0; j < pA; ++j)
                     if ((qa >> j) & 1) A.ptr += g.am[mbp + j];
                 if (pB == 0 || qb == 0 || pA > 0)  // else the A planes of this K panel are still in place
-                    if ((st = split(A, mbp, g.am, g.ak, pa, amax_a)) != TNC_OK) return st;
+                    if ((st = split(A, mbp, g.am, g.ak, pa, amax_a, nza)) != TNC_OK) return st;
                 tnc::TcGemmParams tp{};
                 tp.mb = mbp;
                 tp.nb = nbp;
@@ -739,6 +744,8 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
                 tp.ksplit_bits = cut.ks;
                 tp.partial = partial;
                 tp.accumulate = (!cut.ks && qk > 0) ? 1 : 0;
+                tp.a_shared = a_shared ? 1 : 0;
+                tp.b_shared = b_shared ? 1 : 0;
                 CUDA_TRY(timed_begin(net, node, tnc::tc_uses_pair(tp) ? K_TC2 : (tnc::tc_uses_multicast(tp) ? K_TCMC : K_TC),
                                      b, s, std::ldexp(1.0, mbp + nbp + kbp) * b));
                 CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));

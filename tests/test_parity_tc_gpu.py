@@ -275,3 +275,33 @@ def test_k_panels_and_k_splits(lib, mode, mb, nb, kb, cap, sliced):
     print("mode %d (%d,%d,%d) cap 2^%d: err %.3e, vs uncut %.3e" % (mode, mb, nb, kb, cap, err, d))
     assert err <= TOL[mode]
     assert d <= 1e-6
+
+
+@pytest.mark.parametrize("mode", [4, 2, 1])
+def test_slice_invariant_operand_split_once(lib, mode):
+    """In the 30-qubit plan the (2^14, 2^10, 2^12) contraction's A operand
+    holds no sliced index: in a batch of slices it is split (and, in FP16x2,
+    scanned for its scale) once and every batch entry reads that copy. A
+    4-slice call matches the sum of four single-slice calls (where nothing
+    is shared) to FP64 summation order."""
+    from paper_2205_00393_gb300 import Network
+    c = grid_rqc(5, 6, 14, 2, n_open=6)
+    ref_net = circuit_to_network(c).as_complex64()
+    net = Network.from_tn(ref_net)
+    path = net.greedy_path()
+    net.set_path(path)
+    S = net.find_slices(27, 7)
+    net.set_slices(S)
+    Sset = set(S)
+    per = [any(i in Sset for i in idx) for idx in ref_net.indices]
+    for (a, b) in path:
+        per.append(per[a] or per[b])
+    nodes = net.stats()["nodes"]
+    shared = [i for i, (a, b) in enumerate(path) if nodes[i][:3] == [14, 10, 12] and not per[a] and per[b]]
+    assert shared, "expected a tensor-core node with a slice-invariant A operand"
+    batched = net.contract(8, 12, mode).cpu().numpy()
+    single = sum(net.contract(s, s + 1, mode).cpu().numpy() for s in range(8, 12))
+    net.check_device()
+    d = float(np.max(np.abs(batched - single)) / np.max(np.abs(single)))
+    print("mode %d batched vs single-slice calls %.3e" % (mode, d))
+    assert d <= 1e-10
