@@ -180,3 +180,25 @@ def test_tensor_core_cuts_on_the_53_qubit_plan():
     for mode in ("1", "2", "4"):
         assert seen[(mode, 12, 12, 18)][2] > 0
         assert seen[(mode, 11, 10, 19)][2] > 0 and seen[(mode, 11, 10, 19)][3] > 0
+
+
+def test_option_validation():
+    """tnc_set_option accepts each documented key within its range and
+    rejects unknown keys and out-of-range values with TNC_E_INVALID (host
+    logic, no GPU)."""
+    from paper_2205_00393_gb300 import Network, TNCError
+    t = np.ones((2, 2), dtype=np.complex64)
+    net = Network([t, t], [(0, 1), (1, 2)], [2, 2, 2], [0, 2])
+    good = {"tc_row_bytes": [64, 128], "tc_group_m": [1, 64], "tc_pair": [0, 1], "tc_multicast": [0, 1],
+            "tc_plane_cap_log2": [16, 40], "backward_keep_every": [0, 64], "cache_invariants": [0, 1],
+            "tc_spin_limit": [0, 1 << 20], "tc_test_stall": [0]}
+    bad = {"tc_row_bytes": [32, 256], "tc_group_m": [0, 65], "tc_pair": [2, -1], "tc_multicast": [2],
+           "tc_plane_cap_log2": [15, 41], "backward_keep_every": [-1, 65], "tc_spin_limit": [-1], "no_such_key": [1]}
+    for k, vals in good.items():
+        for v in vals:
+            net.set_option(k, v)
+    for k, vals in bad.items():
+        for v in vals:
+            with pytest.raises(TNCError) as e:
+                net.set_option(k, v)
+            assert e.value.status == 1, (k, v)
