@@ -42,7 +42,7 @@ TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 *
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
-              4: "k_split_operand", 5: "k_cgemm_tc2", 6: "k_cgemm_tc_mc", 7: "k_ksplit_reduce", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
+              4: "k_split_operand", 7: "k_ksplit_reduce", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
 
 
 def workload_name():
@@ -164,7 +164,7 @@ def kernel_breakdown(recs):
         d = by_kind.setdefault(r["kind"], {"ms": 0.0, "cmacs": 0.0, "launches": 0})
         d["ms"] += r["ms"]
         d["launches"] += 1
-        if r["kind"] in (0, 1, 2, 3, 5, 6):
+        if r["kind"] in (0, 1, 2, 3):
             d["cmacs"] += r["cmacs"]
     return by_kind
 
@@ -175,7 +175,7 @@ def roofline_of(by_kind, mode, peaks, peak_src, sustained):
     d = by_kind[dom]
     share = d["ms"] / sum(v["ms"] for v in by_kind.values())
     sec = d["ms"] / 1e3
-    if dom in (3, 5, 6):
+    if dom == 3:
         bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
         peak = bf16 * (TF32_OVER_BF16 if mode == "tf32" else 1.0)
         achieved = d["cmacs"] * TENSOR_FLOPS_PER_CMAC[mode] / sec / 1e12
@@ -262,10 +262,6 @@ def apply_options(net, args):
         net.set_option("tc_row_bytes", args.tc_row_bytes)
     if args.tc_group_m:
         net.set_option("tc_group_m", args.tc_group_m)
-    if args.tc_pair is not None:
-        net.set_option("tc_pair", args.tc_pair)
-    if args.tc_multicast is not None:
-        net.set_option("tc_multicast", args.tc_multicast)
 
 
 def single_node(args):
@@ -298,10 +294,10 @@ def single_node(args):
     net.check_device()
     recs, n_launches = net.last_timings()
     net.set_timing(False)
-    by_kind = kernel_breakdown([r for r in recs if r["node"] in (3, -1) and r["kind"] in (3, 4, 0, 5, 6)])
+    by_kind = kernel_breakdown([r for r in recs if r["node"] in (3, -1) and r["kind"] in (3, 4, 0)])
     peaks, peak_src = load_peaks()
     line = {"single_node": [mb, nb, kb], "mode": args.mode, "tc_row_bytes": args.tc_row_bytes, "tc_group_m": args.tc_group_m,
-            "tc_pair": args.tc_pair, "tc_multicast": args.tc_multicast, "steps": args.steps,
+            "steps": args.steps,
             "kernel_ms_per_call": {KIND_NAMES[k]: v["ms"] / args.steps for k, v in by_kind.items()},
             "roofline": roofline_of(by_kind, args.mode, peaks, peak_src, sustained=False),
             "gpu_launches": n_launches}
@@ -571,7 +567,7 @@ def backward_bench(args):
     recs, n_launches = net.last_timings()
     net.set_timing(False)
     by_kind = kernel_breakdown(recs)
-    cmacs = sum(v["cmacs"] for k, v in by_kind.items() if k in (0, 3, 5, 6))
+    cmacs = sum(v["cmacs"] for k, v in by_kind.items() if k in (0, 3))
     stats = net.stats()
     line = {"metric": "adjoint pass (forward + environments of all fSim leaves), effective complex TFLOPS",
             "value": 8 * cmacs / T / 1e12, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
@@ -602,10 +598,6 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
-    ap.add_argument("--tc-multicast", type=int, default=None, choices=(0, 1),
-                    help="tensor-core GEMMs on 2-CTA clusters sharing the A tile by multicast (library default 0)")
-    ap.add_argument("--tc-pair", type=int, default=None, choices=(0, 1),
-                    help="tensor-core GEMMs on CTA pairs (2-SM MMA) where eligible (library default 1)")
     ap.add_argument("--c53", action="store_true",
                     help="53-qubit lattice, 20 cycles, t = 30: time a fixed subset of slices")
     ap.add_argument("--c53-slices", type=int, default=1024)

@@ -207,16 +207,6 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 /* Tuning options of the tensor-core GEMM (no effect on results):
  *  "tc_row_bytes"  64 or 128 (default 128): bytes of K per tile row and
  *                  pipeline stage, also the shared-memory swizzle width
- *  "tc_pair"       0 or 1 (default 0): with 128-byte rows and no tuning-table
- *                  entry for the shape, contractions with M >= 256 and K >= 64
- *                  run on CTA pairs (a cluster of two CTAs issuing 2-SM MMAs
- *                  on 256x128 output tiles, each CTA holding half of the
- *                  tile's B operand)
- *  "tc_multicast"  0 or 1 (default 0): with 128-byte rows and no tuning-table
- *                  entry for the shape, contractions with N >= 256 and K >= 64
- *                  run on clusters of two CTAs with the same row tile and
- *                  adjacent column tiles; each loads half of the shared A tile
- *                  and multicasts it to both (takes precedence over tc_pair)
  *  "tc_group_m"    1..64 (default 1): output row tiles per rasterisation
  *                  group (consecutive CTAs sweep all column tiles of a group)
  *  "backward_keep_every" 0 (default) or 1..64: the adjoint pass keeps the
@@ -245,17 +235,18 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value);
 
 /* Autotuner: for every contraction of the current plan that the tensor
  * cores can take in `mode`, time one slice (`slice`) with that contraction on
- * the FP32 CUDA cores, on the tensor cores with 128-byte rows on A-multicast
- * clusters and on CTA pairs, and on single CTAs with 128- and 64-byte rows, and
- * record the fastest per (mode, log2 M, log2 N, log2 K) in a table shared by
- * all networks of the process (results are the same up to rounding either
- * way). Later contractions of any network follow the table. */
+ * the tensor cores with the network's default row width ("tc_row_bytes"), on
+ * the tensor cores with the other row width, and on the FP32 CUDA cores (one
+ * warm-up run, then the median of three timed runs each). A variant replaces
+ * the default only if it is at least 3% faster, so near-equal timings do not
+ * flip the choice. The choice is recorded per (mode, log2 M, log2 N, log2 K)
+ * in a table shared by all networks of the process (results are the same up
+ * to rounding either way). Later contractions of any network follow the
+ * table. */
 tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream);
 
 /* The tuning table as JSON: [[mode, log2 M, log2 N, log2 K, choice], ...]
- * with choice 0 = FP32 CUDA cores, 64 / 128 = tensor-core row width on single
- * CTAs, 256 = 128-byte rows on CTA pairs, 512 = 128-byte rows on A-multicast
- * clusters. */
+ * with choice 0 = FP32 CUDA cores, 64 / 128 = tensor-core row width. */
 tnc_status tnc_tune_table(char* json, size_t cap);
 
 /* Per-launch timing: when enabled, every kernel launch of tnc_contract is
@@ -267,7 +258,6 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable);
 /* Launch records since the last tnc_set_timing (waits for their events): per timed
  * launch the node's tensor id, kernel kind (0 FP32 GEMM, 1 FP64 root reduction,
  * 2 GEMM root + FP64 slice sum, 3 tensor-core GEMM, 4 operand split,
- * 5 tensor-core GEMM on CTA pairs, 6 tensor-core GEMM on A-multicast clusters,
  * 7 reduction of a tensor-core GEMM's K-split partials, -1 leaf slice sum), slice batch, complex multiply-accumulates of the
  * launch (all its nodes and slices) and milliseconds; a grouped launch of
  * several nodes of one tree level reports node -1. Any output array may be NULL. *n_out receives the number

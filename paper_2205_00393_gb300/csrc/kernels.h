@@ -90,8 +90,6 @@ struct TcGemmParams {
     int group_m;     // tile rasterisation: row tiles per group (1 = row-major)
     uint32_t spin_limit;  // polls before a bounded wait gives up
     int test_stall;       // tests only: the producer issues no loads, so waits run out
-    int pair;             // 128-byte rows only: 1 = 256x128 tiles on CTA pairs (2-SM MMA) where M >= 256;
-                          // 2 = clusters of two CTAs sharing their A tile by multicast where N >= 256
     const uint32_t* amax_a;  // split FP16x2: the operands' scale words (SplitParams::amax), else null
     const uint32_t* amax_b;
     int ksplit_bits;         // > 0: K is split over 2^ksplit_bits CTAs (grid y); each writes its FP32
@@ -111,10 +109,6 @@ cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t
 cudaError_t launch_absmax(const Operand& src, int bits, int batch, uint32_t* amax, cudaStream_t s);
 cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
                             int batch, cudaStream_t s);
-// whether launch_cgemm_tc runs this contraction on CTA pairs (2-SM MMA), or
-// on 2-CTA clusters with the A tile multicast
-bool tc_uses_pair(const TcGemmParams& p);
-bool tc_uses_multicast(const TcGemmParams& p);
 // C[z][m][n] (+)= sum over s < 2^ksplit_bits, in order, of partial[s][z][m][n] (an FP64 sum
 // rounded once); C rows c_ld apart, batch entries c_batch_stride apart.
 cudaError_t launch_ksplit_reduce(const float2* partial, int ksplit_bits, int batch, int mb, int nb, float2* C,

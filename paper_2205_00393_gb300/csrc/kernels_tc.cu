@@ -199,90 +199,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// shared::cluster address of `saddr` (a shared::cta address) in CTA `rank`
-__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
-    uint32_t d;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
-    return d;
-}
-
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-
-// Non-suspending test: a waiter suspended in try_wait is not necessarily woken
-// by an arrive from the other CTA, so barriers with remote arrivals are polled.
-__device__ __forceinline__ bool mbar_try_acq_cluster(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\n"
-        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        "selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on a barrier that the other CTA arrives on.
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                                  uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i) {
-        if (mbar_try_acq_cluster(bar, parity)) return true;
-        if ((i & 255) == 255 && *abort_flag) return false;
-    }
-    return false;
-}
-
-// stop both CTAs of the pair and record a timeout
-__device__ __forceinline__ void raise_abort_pair(volatile int* abort_local, uint32_t peer_abort, int* err) {
-    *abort_local = 1;
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1) : "memory");
-    atomicExch(err, kErrTimeout);
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
-}
-
-// Multicast TMA load: the box lands at the same shared-memory offset in every
-// CTA of `mask`, each completing its own barrier at offset `bar`.
-__device__ __forceinline__ void tma_load_4d_mc(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                               uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar), "h"(mask)
-        : "memory");
-}
-
-// arrive once on the barrier at this offset in every CTA of `mask` when this
-// CTA's MMAs issued so far complete
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            bar),
-        "h"(mask)
-        : "memory");
-}
-
-// MC = 2: launched as clusters of two CTAs with the same row tile and adjacent
-// column tiles. Each CTA loads half of the A tile's rows and multicasts them to
-// both (tmA's box is then 64 rows of one part), so the pair reads A from L2
-// once; B stays per CTA. Each CTA's MMA commit arrives on both CTAs' empty
-// barriers, so no stage is overwritten while either CTA still reads it.
-template <int KIND, int ROWB, int MC>
+template <int KIND, int ROWB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ TcGemmParams p) {
     using C_ = Cfg<KIND, ROWB>;
-    static_assert(MC == 1 || (MC == 2 && ROWB == 128), "A multicast needs 128-byte rows");
     constexpr int PART_TILE_BYTES = C_::PART_TILE;
     constexpr int STAGE_A = C_::PARTS * PART_TILE_BYTES;
     constexpr int STAGE_BYTES = 2 * STAGE_A;
@@ -295,15 +216,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     const int64_t N = 1ll << p.nb, K = 1ll << p.kb;
-    // grouped rasterisation: consecutive CTAs (clusters) cover GROUP_M row tiles x all column tiles
-    const uint32_t rank = MC == 2 ? cluster_rank() : 0u;
-    const int64_t tiles_n = N / (MC * TN), tiles_m = (1ll << p.mb) / TM;
+    // grouped rasterisation: consecutive CTAs cover GROUP_M row tiles x all column tiles
+    const int64_t tiles_n = N / TN, tiles_m = (1ll << p.mb) / TM;
     const int64_t per_group = (int64_t)GROUP_M * tiles_n;
-    const int64_t cta = blockIdx.x / MC;
+    const int64_t cta = blockIdx.x;
     const int64_t grp = cta / per_group, in_grp = cta % per_group;
     const int64_t gm = (tiles_m - grp * GROUP_M) < GROUP_M ? (tiles_m - grp * GROUP_M) : GROUP_M;
     const int m0 = (int)((grp * GROUP_M + in_grp % gm) * TM);
-    const int n0 = (int)((in_grp / gm) * MC * TN) + (int)rank * TN;
+    const int n0 = (int)((in_grp / gm) * TN);
     const int z = blockIdx.z;
     const int za = p.a_shared ? 0 : z, zb = p.b_shared ? 0 : z;  // batch entry of each operand's planes
     const int nkb = (int)((K >> p.ksplit_bits) / C_::BK);  // k-blocks of this CTA's K split
@@ -315,7 +235,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < C_::STAGES; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), MC);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         for (int t = 0; t < 3; ++t) {
             mbar_init(smem_u32(&tfull[t]), 1);
@@ -333,13 +253,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    if constexpr (MC == 2) cluster_sync_all();  // both CTAs' barriers exist before any multicast
-    else __syncthreads();
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
     volatile int* abort_flag = &abort_sh;
     const uint32_t spin = p.spin_limit ? p.spin_limit : kSpinLimit;
-    const uint32_t peer_abort = MC == 2 ? map_rank(smem_u32(&abort_sh), rank ^ 1u) : 0u;
 
     if (warp == PRODUCER_WARP && lane == 0) {
         // ---------------- TMA producer: stages in (chunk, product, k-block) order
@@ -348,11 +266,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int s = it % C_::STAGES;
             const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
             if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag, spin)) {
-                if constexpr (MC == 2) raise_abort_pair(abort_flag, peer_abort, p.err);
-                else {
-                    abort_sh = 1;
-                    atomicExch(p.err, kErrTimeout);
-                }
+                abort_sh = 1;
+                atomicExch(p.err, kErrTimeout);
                 break;
             }
             const int c = it / (3 * kpc), r = it % (3 * kpc);
@@ -360,29 +275,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
             const uint32_t fb = smem_u32(&full_bar[s]);
             mbar_expect_tx(fb, STAGE_BYTES);
-            if constexpr (MC == 2) {  // this CTA's 64 rows of every A part, to both CTAs
-#pragma unroll
-                for (int q = 0; q < C_::PARTS; ++q)
-                    tma_load_4d_mc(sa + q * PART_TILE_BYTES + rank * (PART_TILE_BYTES / 2), &tmA,
-                                   (kb + kb_off) * C_::BK, m0 + (int)rank * (TM / 2), t * C_::PARTS + q, za, fb,
-                                   (uint16_t)3);
-            } else {
-                tma_load_4d(sa, &tmA, (kb + kb_off) * C_::BK, m0, t * C_::PARTS, za, fb);
-            }
+            tma_load_4d(sa, &tmA, (kb + kb_off) * C_::BK, m0, t * C_::PARTS, za, fb);
             tma_load_4d(sa + STAGE_A, &tmB, (kb + kb_off) * C_::BK, n0, t * C_::PARTS, zb, fb);
             issued = it + 1;
-        }
-        if constexpr (MC == 2) {
-            if (!*abort_flag && issued == n_it) {
-                // tail: the other CTA's last commits arrive on this CTA's empty
-                // barriers; wait until they have, so none lands after this CTA exits
-                int first = n_it - C_::STAGES < 0 ? 0 : n_it - C_::STAGES;
-                for (int it = first; it < n_it; ++it) {
-                    const int s = it % C_::STAGES;
-                    const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-                    if (!mbar_wait(smem_u32(&empty_bar[s]), ph, abort_flag, spin)) break;
-                }
-            }
         }
         if (*abort_flag) {
             // drain: wait (bounded) for every load that may still be in flight
@@ -405,11 +300,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int t = r / kpc, kbi = r % kpc;
             if ((kbi == 0 && c > 0 && !mbar_wait(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag, spin)) ||
                 !mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin)) {
-                if constexpr (MC == 2) raise_abort_pair(abort_flag, peer_abort, p.err);
-                else {
-                    abort_sh = 1;
-                    atomicExch(p.err, kErrTimeout);
-                }
+                abort_sh = 1;
+                atomicExch(p.err, kErrTimeout);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -428,8 +320,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             any = true;
-            if constexpr (MC == 2) mma_commit_mc(smem_u32(&empty_bar[s]), (uint16_t)3);
-            else mma_commit(smem_u32(&empty_bar[s]));
+            mma_commit(smem_u32(&empty_bar[s]));
             if (kbi == kpc - 1) mma_commit(smem_u32(&tfull[t]));
         }
         if (*abort_flag && any) {
@@ -484,11 +375,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (!ok) {
             if (lane == 0 && !abort_sh) {
-                if constexpr (MC == 2) raise_abort_pair(abort_flag, peer_abort, p.err);
-                else {
-                    abort_sh = 1;
-                    atomicExch(p.err, kErrTimeout);
-                }
+                abort_sh = 1;
+                atomicExch(p.err, kErrTimeout);
             }
         } else {
             if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
@@ -531,320 +419,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncwarp();
-    if constexpr (MC == 2) cluster_sync_all();  // no CTA leaves while the other may still signal it
-    else __syncthreads();
+    __syncthreads();
     if (warp == MMA_WARP) {
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
-    }
-}
-
-// ------------------------------------------------------------ CTA pair
-//
-// k_cgemm_tc2: the same contraction on 256x128 output tiles computed by a
-// cluster of two CTAs with 2-SM MMAs (tcgen05.mma.cta_group::2, M = 256).
-// Each CTA loads its own 128 rows of A and one half (64 rows) of the tile's
-// B rows; the tensor cores of both SMs read both halves of B, so an SM's
-// shared memory takes 72 KB of TMA writes and 144 KB of MMA operand reads
-// per stage instead of 96 + 192 KB. Roles:
-//   both CTAs  warp 8: TMA producer into its own ring, signalling its own
-//                      full barrier; warps 0-7: epilogue of its own 128 rows;
-//   leader     warp 9: MMA issuer; commits multicast to both CTAs' empty
-//                      and TMEM-full barriers;
-//   peer       warp 9: relay: when its own stage is full, arrives on the
-//                      leader's peer-full barrier for that stage.
-// Every CTA thus only waits on barriers its own loads or the leader's
-// commits complete; every wait is bounded, and a wait that gives up raises
-// the abort flag of both CTAs.
-
-constexpr int SMEM_PIPE2 = 216 * 1024;
-
-template <int KIND> struct Cfg2 {
-    using C1 = Cfg<KIND, 128>;
-    static constexpr int PARTS = C1::PARTS, NPAIRS = C1::NPAIRS, BK = C1::BK, KSTEPS = C1::KSTEPS;
-    static constexpr int A_PART = TM * 128;         // bytes of one A part tile: 128 rows x 128 B
-    static constexpr int B_PART = (TN / 2) * 128;   // one B part tile: this CTA's 64 rows
-    static constexpr int STAGE_A = PARTS * A_PART;
-    static constexpr int STAGE_BYTES = STAGE_A + PARTS * B_PART;
-    static constexpr int STAGES = SMEM_PIPE2 / STAGE_BYTES;
-};
-
-
-template <int KIND>
-__device__ __forceinline__ void mma2(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    if constexpr (KIND != 1) {
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc)
-            : "memory");
-    }
-}
-
-// arrive once on the barrier at this offset in both CTAs when the MMAs issued so far complete
-__device__ __forceinline__ void mma_commit2_both(uint32_t bar) {
-    const uint16_t mask = 3;
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            bar),
-        "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit2_local(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// Instruction descriptor of the 2-SM MMA: M = 256 (128 rows per CTA), N = 128.
-template <int KIND>
-__host__ __device__ constexpr uint32_t instr_desc2() {
-    return (1u << 4) | (ab_format<KIND>() << 7) | (ab_format<KIND>() << 10) |
-           ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
-}
-
-template <int KIND>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
-    k_cgemm_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                const __grid_constant__ TcGemmParams p) {
-    using C_ = Cfg2<KIND>;
-    const int GROUP_M = p.group_m < 1 ? 1 : p.group_m;
-    extern __shared__ __align__(1024) uint8_t dsmem[];
-    __shared__ __align__(8) uint64_t full_bar[C_::STAGES], pfull_bar[C_::STAGES], empty_bar[C_::STAGES], tfull[3],
-        tfree[3], drain_bar;
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_rank();
-    const bool leader = rank == 0;
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
-    const int64_t N = 1ll << p.nb, K = 1ll << p.kb;
-    // grouped rasterisation over pair tiles (256 rows x 128 columns)
-    const int64_t tiles_n = N / TN, tiles_m = (1ll << p.mb) / (2 * TM);
-    const int64_t per_group = (int64_t)GROUP_M * tiles_n;
-    const int64_t pair = blockIdx.x >> 1;
-    const int64_t grp = pair / per_group, in_grp = pair % per_group;
-    const int64_t gm = (tiles_m - grp * GROUP_M) < GROUP_M ? (tiles_m - grp * GROUP_M) : GROUP_M;
-    const int m0 = (int)((grp * GROUP_M + in_grp % gm) * 2 * TM) + (int)rank * TM;  // this CTA's rows
-    const int n0 = (int)((in_grp / gm) * TN);
-    const int nb0 = n0 + (int)rank * (TN / 2);  // this CTA's half of the tile's B rows
-    const int z = blockIdx.z;
-    const int nkb = (int)(K / C_::BK);
-    const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;
-    const int nchunks = nkb / kpc;
-    const int n_it = nchunks * 3 * kpc;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C_::STAGES; ++s) {
-            mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&pfull_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), 1);
-        }
-        for (int t = 0; t < 3; ++t) {
-            mbar_init(smem_u32(&tfull[t]), 1);
-            mbar_init(smem_u32(&tfree[t]), 2 * EPI_WARPS);
-        }
-        mbar_init(smem_u32(&drain_bar), 1);
-        abort_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (warp == MMA_WARP) {
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"(512u)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    cluster_sync_all();  // both CTAs' barriers initialised and TMEM allocated
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;
-    volatile int* abort_flag = &abort_sh;
-    const uint32_t spin = p.spin_limit ? p.spin_limit : kSpinLimit;
-    const uint32_t peer_abort = map_rank(smem_u32(&abort_sh), rank ^ 1u);
-
-    if (warp == PRODUCER_WARP && lane == 0) {
-        // ---------------- TMA producer (both CTAs): own A rows and own half of B
-        int issued = 0;
-        for (int it = 0; it < n_it && !p.test_stall; ++it) {
-            const int s = it % C_::STAGES;
-            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag, spin)) {
-                raise_abort_pair(abort_flag, peer_abort, p.err);
-                break;
-            }
-            const int c = it / (3 * kpc), r = it % (3 * kpc);
-            const int t = r / kpc, kb = c * kpc + r % kpc;
-            const uint32_t sa = smem_u32(smem + s * C_::STAGE_BYTES);
-            const uint32_t fb = smem_u32(&full_bar[s]);
-            mbar_expect_tx(fb, C_::STAGE_BYTES);
-            tma_load_4d(sa, &tmA, kb * C_::BK, m0, t * C_::PARTS, p.a_shared ? 0 : z, fb);
-            tma_load_4d(sa + C_::STAGE_A, &tmB, kb * C_::BK, nb0, t * C_::PARTS, p.b_shared ? 0 : z, fb);
-            issued = it + 1;
-        }
-        if (*abort_flag || issued < n_it) {
-            // drain: wait (bounded) for this CTA's loads that may still be in flight
-            int first = issued - C_::STAGES < 0 ? 0 : issued - C_::STAGES;
-            for (int it = first; it < issued; ++it) {
-                const int s = it % C_::STAGES;
-                const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-                for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&full_bar[s]), ph); ++i) {
-                }
-            }
-        } else {
-            // tail: the leader's last commits arrive on this CTA's empty barriers;
-            // wait until they have, so none lands after this CTA exits (an abort
-            // ends the wait: the leader then drains its MMAs before the pair's
-            // final cluster barrier)
-            int first = n_it - C_::STAGES < 0 ? 0 : n_it - C_::STAGES;
-            for (int it = first; it < n_it; ++it) {
-                const int s = it % C_::STAGES;
-                const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-                if (!mbar_wait(smem_u32(&empty_bar[s]), ph, abort_flag, spin)) break;
-            }
-        }
-    } else if (warp == MMA_WARP && lane == 0 && !leader) {
-        // ---------------- relay (peer): own stage full -> leader's peer-full barrier
-        for (int it = 0; it < n_it && !*abort_flag; ++it) {
-            const int s = it % C_::STAGES;
-            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin)) {
-                raise_abort_pair(abort_flag, peer_abort, p.err);
-                break;
-            }
-            mbar_arrive_cluster(map_rank(smem_u32(&pfull_bar[s]), 0));
-        }
-    } else if (warp == MMA_WARP && lane == 0) {
-        // ---------------- MMA issuer (leader)
-        constexpr uint32_t idesc = instr_desc2<KIND>();
-        bool any = false;
-        for (int it = 0; it < n_it && !*abort_flag; ++it) {
-            const int s = it % C_::STAGES;
-            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-            const int c = it / (3 * kpc), r = it % (3 * kpc);
-            const int t = r / kpc, kbi = r % kpc;
-            if (kbi == 0 && c > 0 &&
-                !mbar_wait_cluster(smem_u32(&tfree[t]), (uint32_t)(c - 1) & 1u, abort_flag, spin)) {
-                raise_abort_pair(abort_flag, peer_abort, p.err);
-                break;
-            }
-            if (!mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin) ||
-                !mbar_wait_cluster(smem_u32(&pfull_bar[s]), ph, abort_flag, spin)) {
-                raise_abort_pair(abort_flag, peer_abort, p.err);
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(smem + s * C_::STAGE_BYTES);
-            const uint32_t sb = sa + C_::STAGE_A;
-            const uint32_t d = tmem + (uint32_t)(t * TN);
-#pragma unroll
-            for (int q = 0; q < C_::NPAIRS; ++q) {
-                const int pa = KIND == 0 ? kPairsBF16[q][0] : kPairs2[q][0];
-                const int pb = KIND == 0 ? kPairsBF16[q][1] : kPairs2[q][1];
-#pragma unroll
-                for (int j = 0; j < C_::KSTEPS; ++j) {
-                    const uint64_t ad = smem_desc<128>(sa + pa * C_::A_PART + j * 32);
-                    const uint64_t bd = smem_desc<128>(sb + pb * C_::B_PART + j * 32);
-                    mma2<KIND>(d, ad, bd, idesc, (kbi > 0 || q > 0 || j > 0) ? 1u : 0u);
-                }
-            }
-            any = true;
-            mma_commit2_both(smem_u32(&empty_bar[s]));
-            if (kbi == kpc - 1) mma_commit2_both(smem_u32(&tfull[t]));
-        }
-        if (*abort_flag && any) {
-            mma_commit2_local(smem_u32(&drain_bar));
-            for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&drain_bar), 0); ++i) {
-            }
-        }
-    } else if (warp < EPI_WARPS) {
-        // ---------------- epilogue (both CTAs): own 128 rows, chunk partials -> FP32 registers -> C
-        const int g = warp & 3, h = warp >> 2;
-        float cr[64], ci[64];
-#pragma unroll
-        for (int j = 0; j < 64; ++j) {
-            cr[j] = 0.f;
-            ci[j] = 0.f;
-        }
-        bool ok = true;
-        for (int c = 0; c < nchunks && ok; ++c) {
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                int w = 0;
-                if (lane == 0) w = mbar_wait(smem_u32(&tfull[t]), (uint32_t)c & 1u, abort_flag, spin) ? 1 : 0;
-                w = __shfl_sync(0xffffffffu, w, 0);
-                if (!w) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(t * TN + 64 * h + 32 * half), v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = 32 * half + j;
-                        if (t == 0) {
-                            cr[col] += v[j];
-                            ci[col] -= v[j];
-                        } else if (t == 1) {
-                            cr[col] -= v[j];
-                            ci[col] -= v[j];
-                        } else {
-                            ci[col] += v[j];
-                        }
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(map_rank(smem_u32(&tfree[t]), 0));
-            }
-        }
-        if (!ok) {
-            if (lane == 0 && !abort_sh) raise_abort_pair(abort_flag, peer_abort, p.err);
-        } else {
-            if constexpr (KIND == 3) {  // undo the operand scales 2^eA 2^eB (exact)
-                const float sa = pow2f(-fp16_scale_exp(p.amax_a[p.a_shared ? 0 : z])),
-                            sb = pow2f(-fp16_scale_exp(p.amax_b[p.b_shared ? 0 : z]));
-#pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    cr[j] = cr[j] * sa * sb;
-                    ci[j] = ci[j] * sa * sb;
-                }
-            }
-            // Stage the warp's 32 x 64 complex block in shared memory (every MMA that
-            // read the pipeline ring has completed), then write whole 512-byte rows
-            // with coalesced 16-byte stores.
-            float2* stg = reinterpret_cast<float2*>(smem) + (size_t)warp * 32 * EPI_LDW;
-#pragma unroll
-            for (int j = 0; j < 64; j += 2)
-                reinterpret_cast<float4*>(stg + lane * EPI_LDW + j)[0] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
-            __syncwarp();
-            const int64_t ld = p.c_ld ? p.c_ld : N;
-            float2* cbase = p.C + (int64_t)z * p.c_batch_stride + (int64_t)(m0 + 32 * g) * ld + n0 + 64 * h;
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r)
-                reinterpret_cast<float4*>(cbase + (int64_t)r * ld)[lane] =
-                    reinterpret_cast<const float4*>(stg + r * EPI_LDW)[lane];
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncwarp();
-    cluster_sync_all();  // no CTA leaves while the other may still signal it or use the pair's TMEM
-    if (warp == MMA_WARP) {
-        __syncwarp();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
     }
 }
 
@@ -1075,67 +654,26 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int b
     return r == CUDA_SUCCESS;
 }
 
-template <int KIND, int ROWB, int MC>
+template <int KIND, int ROWB>
 cudaError_t launch_tc_impl(const TcGemmParams& p, const void* planesA, const void* planesB, int batch,
                            cudaStream_t s) {
     using C_ = Cfg<KIND, ROWB>;
     const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
-    if (K % C_::BK || N % (MC * TN)) return cudaErrorInvalidValue;
+    if (K % C_::BK || N % TN) return cudaErrorInvalidValue;
     CUtensorMap ta, tb;
-    const bool maps = MC == 2 ? make_map<KIND, ROWB>(&ta, planesA, M, K, batch, TM / 2, 1)
-                              : make_map<KIND, ROWB>(&ta, planesA, M, K, batch);
-    if (!maps || !make_map<KIND, ROWB>(&tb, planesB, N, K, batch)) return cudaErrorInvalidValue;
-    const int smem = C_::STAGES * C_::STAGE_BYTES + 1024;
-    static_assert(C_::STAGES >= 2 && C_::STAGES * C_::STAGE_BYTES + 1024 <= 227 * 1024, "shared memory");
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_cgemm_tc<KIND, ROWB, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int64_t tiles = (M / TM) * (N / TN);
-    if ((K >> p.ksplit_bits) < C_::BK || (p.ksplit_bits && (!p.partial || p.accumulate))) return cudaErrorInvalidValue;
-    if constexpr (MC == 1) {
-        k_cgemm_tc<KIND, ROWB, 1><<<dim3((unsigned)tiles, 1u << p.ksplit_bits, batch), NTHREADS, smem, s>>>(ta, tb, p);
-        return cudaGetLastError();
-    } else {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)tiles, 1, batch);
-        cfg.blockDim = dim3(NTHREADS, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = MC;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_cgemm_tc<KIND, ROWB, MC>, ta, tb, p);
-    }
-}
-
-template <int KIND>
-cudaError_t launch_tc2_impl(const TcGemmParams& p, const void* planesA, const void* planesB, int batch,
-                            cudaStream_t s) {
-    using C_ = Cfg2<KIND>;
-    const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
-    if (K % C_::BK || M % (2 * TM) || N % TN) return cudaErrorInvalidValue;
-    CUtensorMap ta, tb;
-    if (!make_map<KIND, 128>(&ta, planesA, M, K, batch, TM) ||
-        !make_map<KIND, 128>(&tb, planesB, N, K, batch, TN / 2))
+    if (!make_map<KIND, ROWB>(&ta, planesA, M, K, batch) || !make_map<KIND, ROWB>(&tb, planesB, N, K, batch))
         return cudaErrorInvalidValue;
     const int smem = C_::STAGES * C_::STAGE_BYTES + 1024;
     static_assert(C_::STAGES >= 2 && C_::STAGES * C_::STAGE_BYTES + 1024 <= 227 * 1024, "shared memory");
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc2<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc<KIND, ROWB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int64_t ctas = 2 * (M / (2 * TM)) * (N / TN);  // two CTAs (one cluster) per 256x128 tile
-    k_cgemm_tc2<KIND><<<dim3((unsigned)ctas, 1, batch), NTHREADS, smem, s>>>(ta, tb, p);
+    const int64_t tiles = (M / TM) * (N / TN);
+    if ((K >> p.ksplit_bits) < C_::BK || (p.ksplit_bits && (!p.partial || p.accumulate))) return cudaErrorInvalidValue;
+    k_cgemm_tc<KIND, ROWB><<<dim3((unsigned)tiles, 1u << p.ksplit_bits, batch), NTHREADS, smem, s>>>(ta, tb, p);
     return cudaGetLastError();
 }
 
@@ -1143,23 +681,11 @@ template <int KIND>
 cudaError_t launch_tc_rows(const TcGemmParams& p, const void* pa, const void* pb, int batch, cudaStream_t s) {
     // 128-byte rows need K to span whole 128-byte k-blocks
     const int64_t K = 1ll << p.kb;
-    if (tc_uses_pair(p)) return launch_tc2_impl<KIND>(p, pa, pb, batch, s);
-    if (tc_uses_multicast(p)) return launch_tc_impl<KIND, 128, 2>(p, pa, pb, batch, s);
-    if (p.row_bytes == 128 && K % Cfg<KIND, 128>::BK == 0) return launch_tc_impl<KIND, 128, 1>(p, pa, pb, batch, s);
-    return launch_tc_impl<KIND, 64, 1>(p, pa, pb, batch, s);
+    if (p.row_bytes == 128 && K % Cfg<KIND, 128>::BK == 0) return launch_tc_impl<KIND, 128>(p, pa, pb, batch, s);
+    return launch_tc_impl<KIND, 64>(p, pa, pb, batch, s);
 }
 
 }  // namespace
-
-// CTA pairs need 256-row tiles and K >= 64 (whole 128-byte k-blocks in every mode)
-bool tc_uses_pair(const TcGemmParams& p) {
-    return p.pair == 1 && p.row_bytes == 128 && p.mb >= 8 && p.kb >= 6 && !p.ksplit_bits && !p.accumulate;
-}
-
-// A multicast over a 2-CTA cluster needs an even number of column tiles
-bool tc_uses_multicast(const TcGemmParams& p) {
-    return p.pair == 2 && p.row_bytes == 128 && p.nb >= 8 && p.kb >= 6 && !p.ksplit_bits && !p.accumulate;
-}
 
 // tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts),
 // 4 scaled FP16 (2 parts)

@@ -51,7 +51,7 @@ int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Kernel chosen for a contraction node.
 enum NodeKind {
-    K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_TC2 = 5, K_TCMC = 6, K_KRED = 7
+    K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_KRED = 7
 };
 
 // Tensor-core eligibility of a non-root node in a split mode: both output
@@ -61,9 +61,7 @@ bool tc_node(int mode, int mb, int nb, int kb, bool is_root) {
 }
 
 // Autotuned kernel choice per (mode, log2 M, log2 N, log2 K): 0 = FP32 CUDA
-// cores, 64 / 128 = tensor cores with that row width, 256 = tensor cores with
-// 128-byte rows on CTA pairs (2-SM MMA, 256x128 tiles), 512 = 128-byte rows on
-// 2-CTA clusters that multicast their shared A tile. Filled by
+// cores, 64 / 128 = tensor cores with that row width. Filled by
 // tnc_autotune; shared by every network of the process.
 std::map<std::tuple<int, int, int, int>, int>& tune_table() {
     static std::map<std::tuple<int, int, int, int>, int> t;
@@ -166,8 +164,6 @@ struct tnc_net {
     // tensor-core tile options (tnc_set_option)
     int tc_row_bytes = 128;
     int tc_group_m = 1;
-    int tc_pair = 0;             // untuned default: 128-byte rows on CTA pairs where M >= 256
-    int tc_multicast = 0;        // untuned default: 128-byte rows on A-multicast clusters where N >= 256
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
@@ -215,8 +211,7 @@ int shape_choice(const tnc_net* net, int mode, int mb, int nb, int kb, bool is_r
     if (net->force_choice >= 0) return net->force_choice;
     auto it = tune_table().find(std::make_tuple(mode, mb, nb, kb));
     if (it != tune_table().end()) return it->second;
-    if (net->tc_row_bytes == 128 && net->tc_multicast) return 512;
-    return net->tc_row_bytes == 128 && net->tc_pair ? 256 : net->tc_row_bytes;
+    return net->tc_row_bytes;
 }
 
 // ------------------------------------------------------------- planning ----
@@ -665,7 +660,6 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
     const bool a_shared = b > 1 && g.A.batch_stride == 0 && g.A.n_sl == 0;
     const bool b_shared = b > 1 && g.B.batch_stride == 0 && g.B.n_sl == 0;
     const int nza = a_shared ? 1 : b, nzb = b_shared ? 1 : b;
-    if (cut.ks || pK) row_bytes = row_bytes >= 256 ? 128 : row_bytes;  // K splits: single-CTA tiles
     float2* partial = cut.ks ? reinterpret_cast<float2*>(static_cast<char*>(pa) + cut.partial_off) : nullptr;
     // split FP16x2: one scale word per operand and batch entry, kept after the
     // (panel-sized) plane data and computed once from the whole tensor
@@ -734,8 +728,7 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
                 tp.c_batch_stride = g.c_batch_stride;
                 tp.c_ld = N;
                 tp.err = net->d_err;
-                tp.row_bytes = row_bytes >= 256 ? 128 : row_bytes;
-                tp.pair = row_bytes == 256 ? 1 : (row_bytes == 512 ? 2 : 0);
+                tp.row_bytes = row_bytes;
                 tp.amax_a = amax_a;
                 tp.amax_b = amax_b;
                 tp.group_m = net->tc_group_m;
@@ -746,8 +739,7 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
                 tp.accumulate = (!cut.ks && qk > 0) ? 1 : 0;
                 tp.a_shared = a_shared ? 1 : 0;
                 tp.b_shared = b_shared ? 1 : 0;
-                CUDA_TRY(timed_begin(net, node, tnc::tc_uses_pair(tp) ? K_TC2 : (tnc::tc_uses_multicast(tp) ? K_TCMC : K_TC),
-                                     b, s, std::ldexp(1.0, mbp + nbp + kbp) * b));
+                CUDA_TRY(timed_begin(net, node, K_TC, b, s, std::ldexp(1.0, mbp + nbp + kbp) * b));
                 CUDA_TRY(tnc::launch_cgemm_tc(tp, mode, pa, pb, b, s));
                 CUDA_TRY(timed_end(net, s));
                 if (cut.ks) {  // add the K splits' partials into C, in split order
@@ -1721,24 +1713,26 @@ tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
     const int R = 1 << net->plan.obits;
     double* out = nullptr;
     CUDA_TRY(cudaMalloc(&out, (size_t)R * 16));
-    constexpr int NV = 5;
-    const int variants[NV] = {0, 512, 256, 128, 64};
-    std::map<int, double> t[NV];  // per node: milliseconds of all its launches
+    // variants: FP32 CUDA cores, tensor cores with 128- and 64-byte rows; the
+    // network's default row width is variant kDefault
+    constexpr int NV = 3, kReps = 3;
+    const int variants[NV] = {net->tc_row_bytes, net->tc_row_bytes == 128 ? 64 : 128, 0};
+    std::map<int, std::array<double, kReps>> t[NV];  // per node and timed repeat: ms of all its launches
     const bool timing = net->timing;
     net->tuning = true;
     for (int vi = 0; vi < NV && st == TNC_OK; ++vi) {
         net->force_choice = variants[vi];
-        for (int rep = 0; rep < 2 && st == TNC_OK; ++rep) {  // the first run warms up
+        for (int rep = 0; rep <= kReps && st == TNC_OK; ++rep) {  // run 0 warms up
             net->timing = true;
             net->timed.clear();
             st = tnc_contract(net, slice, slice + 1, mode, out, stream);
             if (st != TNC_OK) break;
             CUDA_TRY(cudaStreamSynchronize(s));
-            if (rep == 1)
+            if (rep > 0)
                 for (const auto& r : net->timed) {
                     float ms = 0.f;
                     CUDA_TRY(cudaEventElapsedTime(&ms, net->ev_pool[r.ev], net->ev_pool[r.ev + 1]));
-                    if (r.node >= net->n_leaves) t[vi][r.node] += ms;
+                    if (r.node >= net->n_leaves) t[vi][r.node][rep - 1] += ms;
                 }
         }
     }
@@ -1748,16 +1742,27 @@ tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
     net->timed.clear();
     cudaFree(out);
     if (st != TNC_OK) return st;
-    std::map<std::tuple<int, int, int, int>, std::array<double, NV>> by_shape;
+    // per shape: the sum over its nodes of each repeat, then the median repeat
+    std::map<std::tuple<int, int, int, int>, std::array<std::array<double, kReps>, NV>> by_shape;
     for (const NodePlan& np : net->plan.nodes) {
         if (!tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) continue;
         auto& acc = by_shape[std::make_tuple(mode, np.mb, np.nb, np.kb)];
-        for (int vi = 0; vi < NV; ++vi) acc[vi] += t[vi][np.v];
+        for (int vi = 0; vi < NV; ++vi)
+            for (int r = 0; r < kReps; ++r) acc[vi][r] += t[vi][np.v][r];
     }
+    // the default stays unless another variant is faster by kMargin: timings
+    // of near-equal variants differ by noise, and a choice should not flip on it
+    constexpr double kMargin = 0.03;
     for (auto& kv : by_shape) {
+        double med[NV];
+        for (int vi = 0; vi < NV; ++vi) {
+            std::array<double, kReps> v = kv.second[vi];
+            std::sort(v.begin(), v.end());
+            med[vi] = v[kReps / 2];
+        }
         int best = 0;
         for (int vi = 1; vi < NV; ++vi)
-            if (kv.second[vi] < kv.second[best]) best = vi;
+            if (med[vi] < (1.0 - kMargin) * med[0] && med[vi] < med[best]) best = vi;
         tune_table()[kv.first] = variants[best];
     }
     ++g_tune_version;
@@ -1799,12 +1804,6 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     if (k == "tc_row_bytes") {
         if (value != 64 && value != 128) return fail(TNC_E_INVALID, "tc_row_bytes must be 64 or 128");
         net->tc_row_bytes = (int)value;
-    } else if (k == "tc_pair") {
-        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "tc_pair must be 0 or 1");
-        net->tc_pair = (int)value;
-    } else if (k == "tc_multicast") {
-        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "tc_multicast must be 0 or 1");
-        net->tc_multicast = (int)value;
     } else if (k == "tc_group_m") {
         if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");
         net->tc_group_m = (int)value;

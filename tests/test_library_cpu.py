@@ -189,10 +189,10 @@ def test_option_validation():
     from paper_2205_00393_gb300 import Network, TNCError
     t = np.ones((2, 2), dtype=np.complex64)
     net = Network([t, t], [(0, 1), (1, 2)], [2, 2, 2], [0, 2])
-    good = {"tc_row_bytes": [64, 128], "tc_group_m": [1, 64], "tc_pair": [0, 1], "tc_multicast": [0, 1],
+    good = {"tc_row_bytes": [64, 128], "tc_group_m": [1, 64],
             "tc_plane_cap_log2": [16, 40], "backward_keep_every": [0, 64], "cache_invariants": [0, 1],
             "tc_spin_limit": [0, 1 << 20], "tc_test_stall": [0]}
-    bad = {"tc_row_bytes": [32, 256], "tc_group_m": [0, 65], "tc_pair": [2, -1], "tc_multicast": [2],
+    bad = {"tc_row_bytes": [32, 256], "tc_group_m": [0, 65], "tc_pair": [0, 1], "tc_multicast": [0, 1],
            "tc_plane_cap_log2": [15, 41], "backward_keep_every": [-1, 65], "tc_spin_limit": [-1], "no_such_key": [1]}
     for k, vals in good.items():
         for v in vals:

@@ -101,7 +101,6 @@ def test_panelled_planes_identical(lib, mode):
     net_ref = _three_leaf(21, 10, 9, 8, True)
     net = Network.from_tn(net_ref)
     net.set_path([(0, 1), (2, 3)])
-    net.set_option("tc_pair", 0)
     a = net.contract(0, 1, mode).cpu().numpy()
     seed = torch.ones(net.n_out, dtype=torch.complex128)
     ea = net.contract_backward(seed, 0, 1, mode).cpu().numpy()
@@ -113,75 +112,6 @@ def test_panelled_planes_identical(lib, mode):
     assert np.array_equal(a, b)
     assert float(np.max(np.abs(ea - eb)) / np.max(np.abs(ea))) <= 1e-6
     assert net.workspace_bytes(1) < w_full
-
-
-def _tc_kinds(net, mode):
-    net.set_timing(True)
-    out = net.contract(0, 1, mode).cpu().numpy()
-    recs, _ = net.last_timings()
-    net.set_timing(False)
-    return out, {r["kind"] for r in recs}
-
-
-@pytest.mark.parametrize("option,kind", [("tc_pair", 5), ("tc_multicast", 6)])
-@pytest.mark.parametrize("mode", [2, 1, 3, 4])
-@pytest.mark.parametrize("mb,nb,kb,permuted", [(8, 8, 6, True), (9, 8, 10, False), (10, 9, 12, True)])
-def test_cta_pair_vs_single_cta(lib, mode, mb, nb, kb, permuted, option, kind):
-    """Two-CTA variants against 128x128 tiles on single CTAs (kind 3) and the
-    FP64 oracle: 256x128 tiles on CTA pairs (2-SM MMA, kind 5), or clusters
-    of two CTAs sharing their A tile by multicast (kind 6). Both within the
-    mode's tolerance of the oracle and within 1e-6 of each other (each output
-    row accumulates the same MMA sequence either way)."""
-    from paper_2205_00393_gb300 import Network
-    net_ref = _three_leaf(300 + mb + nb + kb, mb, nb, kb, permuted)
-    net = Network.from_tn(net_ref)
-    net.set_path([(0, 1), (2, 3)])
-    M = net.stats()["nodes"][0][0]
-    net.set_option(option, 1)
-    pair, kinds_p = _tc_kinds(net, mode)
-    net.set_option(option, 0)
-    single, kinds_s = _tc_kinds(net, mode)
-    net.check_device()
-    assert kind in kinds_p and 3 not in kinds_p, kinds_p
-    assert 3 in kinds_s and kind not in kinds_s, kinds_s
-    ref = tn.contract(net_ref, path=[(0, 1), (2, 3)])
-    e_pair, e_single = floored_rel_err(pair, ref, 0), floored_rel_err(single, ref, 0)
-    d = float(np.max(np.abs(pair - single)) / np.max(np.abs(single)))
-    print("%s mode %d (%d,%d,%d) two-CTA %.3e single %.3e diff %.3e identical %s" % (
-        option, mode, mb, nb, kb, e_pair, e_single, d, np.array_equal(pair, single)))
-    assert M >= 8
-    assert e_pair <= TOL[mode] and e_single <= TOL[mode]
-    assert d <= 1e-6
-
-
-@pytest.mark.parametrize("option,kind", [("tc_pair", 5), ("tc_multicast", 6)])
-@pytest.mark.parametrize("mode", [2, 1])
-def test_cta_pair_batched_slices(lib, mode, option, kind):
-    """The CTA-pair kernel inside the executor: a 24-qubit workload whose
-    large contractions are tensor-core nodes, a batch of 4 slices in one
-    call, against the FP64 oracle slice by slice and against single-CTA
-    tiles."""
-    from paper_2205_00393_gb300 import Network
-    c = grid_rqc(4, 6, 12, 3, n_open=4)
-    ref_net = circuit_to_network(c).as_complex64()
-    net = Network.from_tn(ref_net)
-    path = net.greedy_path()
-    net.set_path(path)
-    S = net.find_slices(20, 7)
-    net.set_slices(S)
-    net.set_option(option, 1)
-    lo, hi = 1, 5
-    net.set_timing(True)
-    got = net.contract(lo, hi, mode).cpu().numpy()
-    recs, _ = net.last_timings()
-    net.set_timing(False)
-    net.check_device()
-    assert kind in {r["kind"] for r in recs}
-    ref = tn.contract(ref_net, path, S, slices=range(lo, hi))
-    assert floored_rel_err(got, ref, 24) <= TOL[mode]
-    net.set_option(option, 0)
-    single = net.contract(lo, hi, mode).cpu().numpy()
-    assert float(np.max(np.abs(got - single)) / np.max(np.abs(single))) <= 1e-6
 
 
 @pytest.mark.parametrize("scale_a,scale_b", [(-70, 50), (60, -90), (0, 0)])
