@@ -35,10 +35,11 @@ WORKLOAD = dict(rows=5, cols=6, cycles=14, seed=2, n_open=6, target_log2=27, sa_
 MODES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x2": 3, "fp16x2": 4}
 # FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# Tensor flops per complex multiply-accumulate of one node (3M: three real
-# products, each summed over the part pairs): BF16 3 parts -> 6 pairs,
-# TF32 2 parts -> 3 pairs, BF16 2 parts -> 3 pairs; 2 flops per real MAC.
-TENSOR_FLOPS_PER_CMAC = {"bf16": 3 * 6 * 2, "tf32": 3 * 3 * 2, "bf16x2": 3 * 3 * 2, "fp16x2": 3 * 3 * 2}
+# Tensor flops per complex multiply-accumulate of one node (four real
+# products Ar Br, Ai Bi, Ar Bi, Ai Br, each summed over the part pairs): BF16
+# 3 parts -> 6 pairs, TF32, BF16x2 and FP16x2 2 parts -> 3 pairs; 2 flops per
+# real MAC.
+TENSOR_FLOPS_PER_CMAC = {"bf16": 4 * 6 * 2, "tf32": 4 * 3 * 2, "bf16x2": 4 * 3 * 2, "fp16x2": 4 * 3 * 2}
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
@@ -184,7 +185,7 @@ def roofline_of(by_kind, mode, peaks, peak_src, sustained):
             " x nominal tf32/bf16 ratio 1.1/2.25" if mode == "tf32" else "")
         r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
              "frac": achieved / peak, "peak_source": src,
-             "algorithmic_flops": "%d*M*N*K tensor flops per node (3M, %s part pairs)" % (
+             "algorithmic_flops": "%d*M*N*K tensor flops per node (4 real products, %s part pairs)" % (
                  TENSOR_FLOPS_PER_CMAC[mode], mode)}
     else:
         achieved = d["cmacs"] * 8 / sec / 1e12
@@ -591,7 +592,7 @@ def main():
     ap.add_argument("--mode", default=None, choices=sorted(MODES),
                     help="arithmetic of the contractions (default fp16x2; bf16 for the single-node, "
                          "backward and many-circuit modes; fp32 for --grad42)")
-    ap.add_argument("--compare-modes", default="bf16",
+    ap.add_argument("--compare-modes", default="bf16,tf32",
                     help="comma-separated split modes also timed on the same slices in the default run "
                          "(reported under split_modes; empty to skip)")
     ap.add_argument("--no-fp32-compare", action="store_true")
@@ -742,6 +743,18 @@ def main():
     e2e = {"value": e2e_flops / Te / 1e12, "unit": UNIT, "h2d_bytes_per_step": leaf_bytes,
            "d2h_bytes_per_step": net.n_out * 16}
 
+    # ---- the sharded sum: slices [0, world * B) dealt to the ranks in blocks of B,
+    # partial sums added by one all-reduce; rank 0 checks the total against its
+    # own contraction of the same slices (untimed)
+    from paper_2205_00393_gb300.shard import sharded_sum
+    v_hi = min(world * B, n_slices)
+    total = sharded_sum(lambda a, b: net.contract(a, b, mode, out=out).clone(), 0, v_hi, B, world, rank)
+    shard_check = None
+    if rank == 0:
+        one = net.contract(0, v_hi, mode, out=out).cpu().numpy()
+        shard_check = {"slices": [0, v_hi], "ranks": world,
+                       "max_rel_diff_vs_one_rank": float(np.max(np.abs(total - one)) / np.max(np.abs(one)))}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
@@ -750,12 +763,14 @@ def main():
                   "bf16x2": "c64 via 2x bf16 split, fp32 accum",
                   "fp16x2": "c64 via 2x fp16 split of the 2^e-scaled operand, fp32 accum"}[args.mode],
         "data": "synthetic",
-        "s_per_1024_slices": T / n_sl_tot * 1024 * world if world > 1 else T / n_sl_tot * 1024,
+        "s_per_1024_slices": T / n_sl_tot * 1024,
+        "gpu_s_per_1024_slices": T * world / n_sl_tot * 1024,
         "config": {"workload": workload_name(), "mode": args.mode, "slices_per_step": B,
                    "n_slices": n_slices, "sliced": len(S), "eq3_overhead": stats["overhead"],
                    "l2": "working set > L2 (1 GiB intermediates), no flush",
                    "parallelism": "slices sharded over ranks" if world > 1 else "1 GPU"},
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launches,
+        "sharded_sum_check": shard_check,
         "kernel_time_ms": {KIND_NAMES[k]: v["ms"] for k, v in by_kind.items()},
         "top_nodes": top_nodes(recs, stats),
         "tuned_shapes": [e for e in tune_table() if e[0] == mode],
@@ -815,7 +830,7 @@ def main():
                 m_flops *= world
             line["split_modes"][m] = {
                 "value": m_flops / Tm / 1e12, "ms_per_step": 1e3 * Tm / args.steps,
-                "s_per_1024_slices": Tm / n_sl_tot * 1024 * (world if world > 1 else 1),
+                "s_per_1024_slices": Tm / n_sl_tot * 1024,
                 "roofline": roofline_of(kernel_breakdown(m_recs), m, peaks, peak_src, sustained=True)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         path_py = [tuple(p) for p in path]

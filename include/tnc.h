@@ -49,14 +49,18 @@ typedef enum {
 } tnc_status;
 
 /* Arithmetic used by the pairwise contractions. The slice sum and the final
- * amplitude reduction are always accumulated in FP64. */
+ * amplitude reduction are always accumulated in FP64. In the split modes each
+ * complex product takes four real products (Ar Br, Ai Bi, Ar Bi, Ai Br) on the
+ * tcgen05 tensor cores, each over the listed part pairs, with FP32
+ * accumulation. */
 typedef enum {
     TNC_FP32 = 0,        /* complex64 on FP32 CUDA cores (4 real FMAs per complex MAC)     */
-    TNC_SPLIT_TF32 = 1,  /* x = hi + lo in TF32, 3 products, tcgen05 kind::tf32, FP32 accum */
-    TNC_SPLIT_BF16 = 2,  /* x = x0 + x1 + x2 in BF16, 6 products, tcgen05 kind::f16, FP32   */
-    TNC_SPLIT_BF16X2 = 3, /* x = x0 + x1 in BF16, 3 products (cheaper, lower accuracy)      */
-    TNC_SPLIT_FP16X2 = 4  /* 2^e x = x0 + x1 in FP16, 3 products, kind::f16, FP32 accum; e per
-                             operand (and slice) puts max |Re|, |Im| in [2^13, 2^14)         */
+    TNC_SPLIT_TF32 = 1,  /* x = hi + lo in TF32, 3 part pairs, kind::tf32                  */
+    TNC_SPLIT_BF16 = 2,  /* x = x0 + x1 + x2 in BF16, 6 part pairs, kind::f16              */
+    TNC_SPLIT_BF16X2 = 3, /* x = x0 + x1 in BF16, 3 part pairs (cheaper, lower accuracy)   */
+    TNC_SPLIT_FP16X2 = 4  /* 2^e x = x0 + x1 in FP16, 3 part pairs, kind::f16; e per row of A,
+                             per column of B and per 256-wide chunk of K puts that chunk's
+                             max |Re|, |Im| in [2^14, 2^15); undone exactly per chunk      */
 } tnc_mode;
 
 /* Build a network (Sec. 2.1.1: G = (V, E, w)).
@@ -205,7 +209,7 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 
 /* Tuning options of the tensor-core GEMM (no effect on results):
- *  "tc_row_bytes"  64 or 128 (default 128): bytes of K per tile row and
+ *  "tc_row_bytes"  32 or 64 (default 64): bytes of K per tile row and
  *                  pipeline stage, also the shared-memory swizzle width
  *  "tc_group_m"    1..64 (default 1): output row tiles per rasterisation
  *                  group (consecutive CTAs sweep all column tiles of a group)
@@ -246,7 +250,7 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value);
 tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream);
 
 /* The tuning table as JSON: [[mode, log2 M, log2 N, log2 K, choice], ...]
- * with choice 0 = FP32 CUDA cores, 64 / 128 = tensor-core row width. */
+ * with choice 0 = FP32 CUDA cores, 32 / 64 = tensor-core row width. */
 tnc_status tnc_tune_table(char* json, size_t cap);
 
 /* Per-launch timing: when enabled, every kernel launch of tnc_contract is
@@ -287,7 +291,13 @@ tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, dou
  * TNC_NOALLOC_MAX_PARTIALS complex doubles (1 MiB) that every GPU loading
  * libtnc holds until the process exits. The first call on a device looks up
  * that array's device address (with the device current) and caches it; make
- * that first call before any stream capture. Every call on a device shares
+ * that first call before any stream capture. With CUDA's lazy module loading
+ * that first call is also when the driver loads this library's device code
+ * and the array onto the device, which the driver may back with device memory
+ * of its own; a caller that must not see any device allocation after set-up
+ * makes one call (e.g. with K = 1) during its own set-up. The cached address
+ * belongs to the device's primary context (the one the CUDA runtime uses): it
+ * is not valid in another driver context, nor after cudaDeviceReset. Every call on a device shares
  * the array, so calls whose work overlaps on the GPU (e.g. on two streams)
  * race; serialise them. Partial sums are fully rewritten by each call before
  * they are read. Errors: TNC_E_INVALID for NULL pointers or sizes beyond the

@@ -69,15 +69,15 @@ struct PermParams {
 
 // Operand split for the tensor-core path: the logical matrix X[R][K]
 // (R = M for A, N for B) with X(r, k) = src[r strides + k strides] is
-// written as K-major planes [batch][3 * parts][R][K] (Re, Im, Re+Im, each
-// split into parts).
+// written as K-major planes [batch][2 * parts][R][K] (the parts of Re, then
+// the parts of Im).
 struct SplitParams {
     Operand src;
     int rb, kb;
     int64_t rs[kMaxBits], ks[kMaxBits];
     int64_t slice0;
     void* dst;
-    const uint32_t* amax;  // split FP16x2: per batch entry, bits of max |Re|, |Im| (from launch_absmax)
+    int8_t* sexp;          // split FP16x2: scale exponents [batch][K / min(K, 256)][R] (written here)
 };
 
 struct TcGemmParams {
@@ -86,27 +86,25 @@ struct TcGemmParams {
     int64_t c_batch_stride;
     int64_t c_ld;    // elements between consecutive output rows (0 = 2^nb)
     int* err;        // device error word (4 = a bounded wait gave up)
-    int row_bytes;   // 64 or 128: bytes of K per tile row and stage (swizzle width)
+    int row_bytes;   // 32 or 64: bytes of K per tile row and stage (swizzle width)
     int group_m;     // tile rasterisation: row tiles per group (1 = row-major)
     uint32_t spin_limit;  // polls before a bounded wait gives up
     int test_stall;       // tests only: the producer issues no loads, so waits run out
-    const uint32_t* amax_a;  // split FP16x2: the operands' scale words (SplitParams::amax), else null
-    const uint32_t* amax_b;
+    const int8_t* sexp_a;    // split FP16x2: the operands' scale exponents (SplitParams::sexp), else null
+    const int8_t* sexp_b;
     int ksplit_bits;         // > 0: K is split over 2^ksplit_bits CTAs (grid y); each writes its FP32
     float2* partial;         //   partial tile to partial[(split * batch + z) * M * N + m * N + n]
     int accumulate;          // 1 (no K split): add the result into C instead of overwriting it
     int a_shared, b_shared;  // 1: the operand is the same for every batch entry; its planes and scale
-                             //   word exist once (batch entry 0)
+                             //   exponents exist once (batch entry 0)
 };
 
 int tc_plane_count(int mode);
 int tc_elem_bytes(int mode);
 int tc_min_kb(int mode);
+// split FP16x2: K chunks of 256 (one if K <= 256) that carry their own scale
+int tc_scale_chunks(int kb);
 cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s);
-// Split FP16x2 scale words: amax[z] = bits of max |Re|, |Im| over the 2^bits
-// elements of the tensor behind `src` (its free, contracted and sliced modes)
-// at src.ptr + z * src.batch_stride.
-cudaError_t launch_absmax(const Operand& src, int bits, int batch, uint32_t* amax, cudaStream_t s);
 cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
                             int batch, cudaStream_t s);
 // C[z][m][n] (+)= sum over s < 2^ksplit_bits, in order, of partial[s][z][m][n] (an FP64 sum

@@ -30,7 +30,9 @@ double2* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device. In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached. The cache holds addresses
+// in each device's primary context, the runtime's context; it is not valid
+// in other driver contexts or after cudaDeviceReset.
 cudaError_t scratch_for_current_device(double2** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -61,7 +61,7 @@ bool tc_node(int mode, int mb, int nb, int kb, bool is_root) {
 }
 
 // Autotuned kernel choice per (mode, log2 M, log2 N, log2 K): 0 = FP32 CUDA
-// cores, 64 / 128 = tensor cores with that row width. Filled by
+// cores, 32 / 64 = tensor cores with that row width. Filled by
 // tnc_autotune; shared by every network of the process.
 std::map<std::tuple<int, int, int, int>, int>& tune_table() {
     static std::map<std::tuple<int, int, int, int>, int> t;
@@ -162,7 +162,7 @@ struct tnc_net {
     int last_keep_every = 1;        // checkpoint spacing of the last backward pass
     size_t last_backward_bytes = 0;
     // tensor-core tile options (tnc_set_option)
-    int tc_row_bytes = 128;
+    int tc_row_bytes = 64;
     int tc_group_m = 1;
     uint32_t tc_spin_limit = 0;  // 0 = kernel default
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
@@ -340,15 +340,16 @@ int64_t tensor_bytes(const Plan& P, int v) { return (int64_t)8 << P.layout[v].si
 std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice);
 
 // Plane data of one operand (rows x K, every plane, every batch entry); split
-// FP16x2 keeps the operand's scale words (one uint32 per batch entry) after
-// it. How a contraction whose planes exceed the cap is cut up: tc_cut below.
+// FP16x2 keeps the operand's scale exponents (one byte per row and 256-wide K
+// chunk, per batch entry) after it, 256-byte aligned. How a contraction whose
+// planes exceed the cap is cut up: tc_cut below.
 int64_t plane_data_bytes(int mode, int rb, int kb, int64_t batch) {
-    return batch * (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode) << (rb + kb);
+    return align_up(batch * (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode) << (rb + kb));
 }
 
 int64_t full_planes_bytes(int mode, int rb, int kb, int64_t batch) {
-    const int64_t scale_words = mode == TNC_SPLIT_FP16X2 ? (batch * 4 + 255) / 256 * 256 : 0;
-    return plane_data_bytes(mode, rb, kb, batch) + scale_words;
+    const int64_t scales = mode == TNC_SPLIT_FP16X2 ? align_up((batch * tnc::tc_scale_chunks(kb)) << rb) : 0;
+    return plane_data_bytes(mode, rb, kb, batch) + scales;
 }
 
 // How one tensor-core contraction is cut up:
@@ -661,32 +662,16 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
     const bool b_shared = b > 1 && g.B.batch_stride == 0 && g.B.n_sl == 0;
     const int nza = a_shared ? 1 : b, nzb = b_shared ? 1 : b;
     float2* partial = cut.ks ? reinterpret_cast<float2*>(static_cast<char*>(pa) + cut.partial_off) : nullptr;
-    // split FP16x2: one scale word per operand and batch entry, kept after the
-    // (panel-sized) plane data and computed once from the whole tensor
-    uint32_t* amax_a = nullptr;
-    uint32_t* amax_b = nullptr;
+    // split FP16x2: scale exponents per row and 256-wide K chunk of each
+    // operand, written by the split after the (panel-sized) plane data
+    int8_t* sexp_a = nullptr;
+    int8_t* sexp_b = nullptr;
     if (mode == TNC_SPLIT_FP16X2) {
-        // the linear scan needs each operand to be a dense block of 2^bits
-        // elements: distinct power-of-two strides that add up to 2^bits - 1
-        auto dense = [](const int64_t* r, int nr, const int64_t* k, int nk, const tnc::Operand& o) {
-            int64_t sum = 0, bits = 0;
-            for (int j = 0; j < nr; ++j) sum += r[j], bits |= r[j];
-            for (int j = 0; j < nk; ++j) sum += k[j], bits |= k[j];
-            for (int j = 0; j < o.n_sl; ++j) sum += o.sl_stride[j], bits |= o.sl_stride[j];
-            const int64_t n = (int64_t)1 << (nr + nk + o.n_sl);
-            return sum == n - 1 && bits == n - 1;
-        };
-        if (!dense(g.am, g.mb, g.ak, g.kb, g.A) || !dense(g.bn, g.nb, g.bk, g.kb, g.B))
-            return fail(TNC_E_STATE, "split FP16x2: an operand is not a dense tensor");
-        amax_a = reinterpret_cast<uint32_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, kbp, b));
-        amax_b = reinterpret_cast<uint32_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, kbp, b));
-        CUDA_TRY(timed_begin(net, node, K_SPLIT, b, s, 0.0));
-        CUDA_TRY(tnc::launch_absmax(g.A, g.mb + g.kb + g.A.n_sl, nza, amax_a, s));
-        CUDA_TRY(tnc::launch_absmax(g.B, g.nb + g.kb + g.B.n_sl, nzb, amax_b, s));
-        CUDA_TRY(timed_end(net, s));
+        sexp_a = reinterpret_cast<int8_t*>(static_cast<char*>(pa) + plane_data_bytes(mode, mbp, kbp, b));
+        sexp_b = reinterpret_cast<int8_t*>(static_cast<char*>(pb) + plane_data_bytes(mode, nbp, kbp, b));
     }
     auto split = [&](const tnc::Operand& src, int rb, const int64_t* rs, const int64_t* ks, void* dst,
-                     uint32_t* amax, int nz) -> tnc_status {
+                     int8_t* sexp, int nz) -> tnc_status {
         tnc::SplitParams sp{};
         sp.src = src;
         sp.rb = rb;
@@ -695,7 +680,7 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
         for (int j = 0; j < kbp; ++j) sp.ks[j] = ks[j];
         sp.slice0 = g.slice0;
         sp.dst = dst;
-        sp.amax = amax;
+        sp.sexp = sexp;
         CUDA_TRY(timed_begin(net, node, K_SPLIT, nz, s, 0.0));
         CUDA_TRY(tnc::launch_split(sp, mode, nz, s));
         CUDA_TRY(timed_end(net, s));
@@ -713,13 +698,13 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
             tnc::Operand B = Bk;
             for (int j = 0; j < pB; ++j)
                 if ((qb >> j) & 1) B.ptr += g.bn[nbp + j];
-            if ((st = split(B, nbp, g.bn, g.bk, pb, amax_b, nzb)) != TNC_OK) return st;
+            if ((st = split(B, nbp, g.bn, g.bk, pb, sexp_b, nzb)) != TNC_OK) return st;
             for (int64_t qa = 0; qa < (1ll << pA); ++qa) {  // row panels of A: top pA bits of m fixed
                 tnc::Operand A = Ak;
                 for (int j = 0; j < pA; ++j)
                     if ((qa >> j) & 1) A.ptr += g.am[mbp + j];
                 if (pB == 0 || qb == 0 || pA > 0)  // else the A planes of this K panel are still in place
-                    if ((st = split(A, mbp, g.am, g.ak, pa, amax_a, nza)) != TNC_OK) return st;
+                    if ((st = split(A, mbp, g.am, g.ak, pa, sexp_a, nza)) != TNC_OK) return st;
                 tnc::TcGemmParams tp{};
                 tp.mb = mbp;
                 tp.nb = nbp;
@@ -729,8 +714,8 @@ tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, 
                 tp.c_ld = N;
                 tp.err = net->d_err;
                 tp.row_bytes = row_bytes;
-                tp.amax_a = amax_a;
-                tp.amax_b = amax_b;
+                tp.sexp_a = sexp_a;
+                tp.sexp_b = sexp_b;
                 tp.group_m = net->tc_group_m;
                 tp.spin_limit = net->tc_spin_limit;
                 tp.test_stall = net->tc_test_stall;
@@ -1713,10 +1698,10 @@ tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
     const int R = 1 << net->plan.obits;
     double* out = nullptr;
     CUDA_TRY(cudaMalloc(&out, (size_t)R * 16));
-    // variants: FP32 CUDA cores, tensor cores with 128- and 64-byte rows; the
-    // network's default row width is variant kDefault
+    // variants: the network's default row width (first), the other row width,
+    // FP32 CUDA cores
     constexpr int NV = 3, kReps = 3;
-    const int variants[NV] = {net->tc_row_bytes, net->tc_row_bytes == 128 ? 64 : 128, 0};
+    const int variants[NV] = {net->tc_row_bytes, net->tc_row_bytes == 64 ? 32 : 64, 0};
     std::map<int, std::array<double, kReps>> t[NV];  // per node and timed repeat: ms of all its launches
     const bool timing = net->timing;
     net->tuning = true;
@@ -1802,7 +1787,7 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     if (!net || !key) return fail(TNC_E_INVALID, "NULL argument");
     std::string k(key);
     if (k == "tc_row_bytes") {
-        if (value != 64 && value != 128) return fail(TNC_E_INVALID, "tc_row_bytes must be 64 or 128");
+        if (value != 32 && value != 64) return fail(TNC_E_INVALID, "tc_row_bytes must be 32 or 64");
         net->tc_row_bytes = (int)value;
     } else if (k == "tc_group_m") {
         if (value < 1 || value > 64) return fail(TNC_E_INVALID, "tc_group_m must be in [1, 64]");

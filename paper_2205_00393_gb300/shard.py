@@ -48,6 +48,8 @@ def sharded_sum(contract, lo, hi, per_call, world=1, rank=0, group=None):
             probe = probe.detach().cpu().numpy() if hasattr(probe, "detach") else np.asarray(probe)
             total = np.zeros_like(probe, dtype=np.complex128)
         t = torch.from_numpy(np.ascontiguousarray(total).view(np.float64).copy())
+        if dist.get_backend(group) == "nccl":  # NCCL reduces device tensors only
+            t = t.cuda()
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-        total = t.numpy().view(np.complex128)
+        total = t.cpu().numpy().view(np.complex128)
     return total

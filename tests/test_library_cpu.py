@@ -154,7 +154,11 @@ def test_tensor_core_cuts_on_the_53_qubit_plan():
     st = net.stats()
     b = st["tc_cut_batch"]
     cap = 1 << 32
-    planes = {"1": (6, 4), "2": (9, 2), "3": (6, 2), "4": (6, 2)}  # (planes, bytes per element)
+    # (planes, bytes per element): the parts of Re and of Im
+    planes = {"1": (4, 4), "2": (6, 2), "3": (4, 2), "4": (4, 2)}
+
+    def align(x):
+        return (x + 255) // 256 * 256
     seen = {}
     for mode, cuts in st["tc_cuts"].items():
         n_pl, elem = planes[mode]
@@ -163,8 +167,9 @@ def test_tensor_core_cuts_on_the_53_qubit_plan():
             per = st["nodes"][i][3]
             bb = b if per else 1
 
-            def fits(rb, k):
-                return bb * n_pl * elem * (1 << (rb + k)) + (256 if mode == "4" else 0) <= cap
+            def fits(rb, k):  # split FP16x2 adds one scale byte per row and 256-wide K chunk
+                scales = align(bb * (1 << max(k - 8, 0)) << rb) if mode == "4" else 0
+                return align(bb * n_pl * elem * (1 << (rb + k))) + scales <= cap
             if pK:
                 assert kb > max(mb, nb)
                 assert fits(mb, kb - pK) and fits(nb, kb - pK) or kb - pK == 6
@@ -189,10 +194,10 @@ def test_option_validation():
     from paper_2205_00393_gb300 import Network, TNCError
     t = np.ones((2, 2), dtype=np.complex64)
     net = Network([t, t], [(0, 1), (1, 2)], [2, 2, 2], [0, 2])
-    good = {"tc_row_bytes": [64, 128], "tc_group_m": [1, 64],
+    good = {"tc_row_bytes": [32, 64], "tc_group_m": [1, 64],
             "tc_plane_cap_log2": [16, 40], "backward_keep_every": [0, 64], "cache_invariants": [0, 1],
             "tc_spin_limit": [0, 1 << 20], "tc_test_stall": [0]}
-    bad = {"tc_row_bytes": [32, 256], "tc_group_m": [0, 65], "tc_pair": [0, 1], "tc_multicast": [0, 1],
+    bad = {"tc_row_bytes": [16, 128], "tc_group_m": [0, 65], "tc_pair": [0, 1], "tc_multicast": [0, 1],
            "tc_plane_cap_log2": [15, 41], "backward_keep_every": [-1, 65], "tc_spin_limit": [-1], "no_such_key": [1]}
     for k, vals in good.items():
         for v in vals:

@@ -116,10 +116,10 @@ def test_panelled_planes_identical(lib, mode):
 
 @pytest.mark.parametrize("scale_a,scale_b", [(-70, 50), (60, -90), (0, 0)])
 def test_fp16x2_operand_scaling(lib, scale_a, scale_b):
-    """Split FP16x2 scales each operand by 2^e so that its largest component
-    lands in [2^13, 2^14): operands of magnitude 2^-70 .. 2^60 (far outside
-    FP16's range) are contracted to the same relative accuracy, and an
-    all-zero operand gives exactly zero."""
+    """Split FP16x2 scales every row chunk of an operand by 2^e so that its
+    largest component lands in [2^14, 2^15): operands of magnitude 2^-70 ..
+    2^60 (far outside FP16's range) are contracted to the same relative
+    accuracy, and an all-zero operand gives exactly zero."""
     from paper_2205_00393_gb300 import Network
     net_ref = _three_leaf(77, 9, 8, 10, True)
     ts = list(net_ref.tensors)
@@ -140,6 +140,60 @@ def test_fp16x2_operand_scaling(lib, scale_a, scale_b):
     zero = net.contract(0, 1, 4).cpu().numpy()
     net.check_device()
     assert np.array_equal(zero, np.zeros_like(zero))
+
+
+def _scaled_pair(seed, mb, nb, kb, a_span, b_span, b_transposed):
+    """A[m,k] B[k,n] I[n,o] with I the identity: the root copies the
+    tensor-core node's output C = A B to the result exactly (one nonzero
+    product per output). Row m of A is scaled by 2^-ea[m] and column n of B
+    by 2^-eb[n], with exponents spread evenly over [0, a_span] and [0,
+    b_span]; B is stored as B[k,n] or transposed as B[n,k]."""
+    from tnc_inputs.network import TensorNetwork
+    rng = np.random.default_rng(seed)
+    M, N, K = 1 << mb, 1 << nb, 1 << kb
+
+    def rnd(*shape):
+        return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2)
+    ea = np.round(np.linspace(0, a_span, M)).astype(int)
+    eb = np.round(np.linspace(0, b_span, N)).astype(int)
+    rng.shuffle(ea)
+    rng.shuffle(eb)
+    a = (rnd(M, K) * np.ldexp(1.0, -ea)[:, None]).astype(np.complex64)
+    b = (rnd(K, N) * np.ldexp(1.0, -eb)[None, :]).astype(np.complex64)
+    eye = np.eye(N, dtype=np.complex64)
+    dims = np.array([M, K, N, N], dtype=np.int64)  # indices m, k, n, o
+    if b_transposed:
+        tensors, idx = [a, np.ascontiguousarray(b.T), eye], [(0, 1), (2, 1), (2, 3)]
+    else:
+        tensors, idx = [a, b, eye], [(0, 1), (1, 2), (2, 3)]
+    return TensorNetwork(tensors, idx, dims, (0, 3), [-1, -1, -1]), ea, eb
+
+
+@pytest.mark.parametrize("mode", [4, 2, 1, 3])
+@pytest.mark.parametrize("mb,nb,kb,b_transposed", [(9, 8, 10, False), (8, 9, 11, True), (7, 7, 5, False)])
+def test_rows_and_columns_of_very_different_magnitude(lib, mode, mb, nb, kb, b_transposed):
+    """Rows of A spanning 2^-30 .. 1 and columns of B spanning 2^-20 .. 1.
+    Every output C[m,n] is compared with the FP64 oracle relative to its own
+    scale: both are multiplied back by 2^(ea[m] + eb[n]) (exact), then held to
+    the mode's bound with the 0.1-rms floor. In split FP16x2 each row of A and
+    column of B carries its own scale per 256-wide K chunk; a single scale per
+    operand would leave the small rows with a few significant bits."""
+    from paper_2205_00393_gb300 import Network
+    net_ref, ea, eb = _scaled_pair(500 + mb + nb + kb, mb, nb, kb, 30, 20, b_transposed)
+    net = Network.from_tn(net_ref)
+    path = [(0, 1), (2, 3)]
+    net.set_path(path)
+    net.set_timing(True)
+    got = net.contract(0, 1, mode).cpu().numpy()
+    recs, _ = net.last_timings()
+    net.set_timing(False)
+    net.check_device()
+    assert 3 in {r["kind"] for r in recs}  # the A*B node ran on the tensor cores
+    ref = tn.contract(net_ref, path)
+    unscale = np.ldexp(1.0, ea[:, None] + eb[None, :]).reshape(-1)
+    err = floored_rel_err(got * unscale, ref * unscale, 0)
+    print("mode %d (%d,%d,%d) rows 2^-30..1, columns 2^-20..1: err %.3e" % (mode, mb, nb, kb, err))
+    assert err <= TOL[mode]
 
 
 def _three_leaf_sliced(seed, mb, nb, kb):

@@ -1,4 +1,5 @@
-"""The allocation-free entry point against the regular contraction.
+"""The allocation-free entry point against the regular contraction and an
+FP64 NumPy product of the same matrices.
 
 tnc_reduce_pair_noalloc serves callers that may not allocate device memory
 (their device memory belongs to another allocator, or a cudaMalloc would stall
@@ -48,15 +49,21 @@ def test_noalloc_matches_contract(libtnc, m_log2, n_log2, k_log2):
     da = torch.from_numpy(a.view(np.float32).reshape(-1).copy()).cuda()
     db = torch.from_numpy(b.view(np.float32).reshape(-1).copy()).cuda()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+    # an independent reference: the same product in FP64 by NumPy, no library kernel involved
+    exact = (a.astype(np.complex128) @ b.astype(np.complex128)).reshape(-1)
+
+    def err(got, want):
+        rms = float(np.sqrt(np.mean(np.abs(want) ** 2)))
+        return float(np.max(np.abs(got - want) / np.maximum(np.abs(want), 0.1 * rms)))
+    assert err(ref, exact) <= TOL
     for call in range(2):  # two calls in a row share the static scratch
         out = torch.full((M * N,), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
         st = fn(ctypes.c_void_p(da.data_ptr()), ctypes.c_void_p(db.data_ptr()), m_log2, n_log2, k_log2,
                 ctypes.c_void_p(out.data_ptr()), stream)
         assert st == 0, libtnc.tnc_last_error()
         got = out.cpu().numpy()
-        err = np.max(np.abs(got - ref) / np.maximum(np.abs(ref), rms))
-        assert err <= TOL, (call, err)
+        assert err(got, ref) <= TOL, (call, err(got, ref))
+        assert err(got, exact) <= TOL, (call, err(got, exact))
 
 
 def test_noalloc_rejects_oversize(libtnc):
