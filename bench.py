@@ -170,28 +170,59 @@ def kernel_breakdown(recs):
     return by_kind
 
 
-def roofline_of(by_kind, mode, peaks, peak_src, sustained):
-    """Roofline entry of the kernel with the most time."""
+def probe_peaks(iters_ffma=300, iters_mma=1 << 22):
+    """Peak rates measured by the library's own probe kernels (tnc_peak_probe),
+    each timed alone with CUDA events after one warm-up launch (about 0.3 s
+    per probe): FP32 FMA on the CUDA cores and tcgen05 MMA in kind::tf32,
+    kind::f16 with BF16 and with FP16 operands."""
+    import torch
+    from paper_2205_00393_gb300 import peak_probe
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, kind, iters in (("ffma_tflops", 0, iters_ffma), ("tf32_tflops", 1, iters_mma),
+                              ("bf16_tflops", 2, iters_mma), ("fp16_tflops", 3, iters_mma)):
+        peak_probe(kind, max(1, iters // 16), stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        flops = peak_probe(kind, iters, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        out[name] = flops / (ev0.elapsed_time(ev1) / 1e3) / 1e12
+    return out
+
+
+def roofline_of(by_kind, mode, peaks, peak_src, sustained, probed=None):
+    """Roofline entry of the kernel with the most time. Tensor-core kernels in
+    BF16/FP16 take the measured cuBLAS BF16 peak (the FP16 dense rate equals
+    BF16's); TF32 takes the library's own kind::tf32 probe when given (else
+    the BF16 peak times the nominal 1.1/2.25 ratio); FP32 CUDA-core kernels
+    take the FFMA probe (else the unit-count derivation)."""
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     d = by_kind[dom]
     share = d["ms"] / sum(v["ms"] for v in by_kind.values())
     sec = d["ms"] / 1e3
     if dom == 3:
-        bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
-        peak = bf16 * (TF32_OVER_BF16 if mode == "tf32" else 1.0)
         achieved = d["cmacs"] * TENSOR_FLOPS_PER_CMAC[mode] / sec / 1e12
-        src = "%s bf16 %s (MEASURED_PEAKS.json)%s" % (
-            "sustained" if sustained else "burst", peak_src,
-            " x nominal tf32/bf16 ratio 1.1/2.25" if mode == "tf32" else "")
+        if mode == "tf32" and probed:
+            peak = probed["tf32_tflops"]
+            src = "tcgen05 kind::tf32 probe of this run (tnc_peak_probe, 128x256x8 MMAs, one CTA per SM)"
+        else:
+            bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
+            peak = bf16 * (TF32_OVER_BF16 if mode == "tf32" else 1.0)
+            src = "%s bf16 %s (MEASURED_PEAKS.json)%s" % (
+                "sustained" if sustained else "burst", peak_src,
+                " x nominal tf32/bf16 ratio 1.1/2.25" if mode == "tf32" else "")
         r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
              "frac": achieved / peak, "peak_source": src,
              "algorithmic_flops": "%d*M*N*K tensor flops per node (4 real products, %s part pairs)" % (
                  TENSOR_FLOPS_PER_CMAC[mode], mode)}
     else:
         achieved = d["cmacs"] * 8 / sec / 1e12
-        r = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-             "frac": achieved / FP32_PEAK_TFLOPS,
-             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
+        peak = probed["ffma_tflops"] if probed else FP32_PEAK_TFLOPS
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "frac": achieved / peak,
+             "peak_source": ("FP32 FMA probe of this run (tnc_peak_probe, 8 chains per thread, 2048 threads "
+                             "per SM)") if probed else "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
              "algorithmic_flops": "8*M*N*K FP32 flops per node (4 real FMAs per complex MAC)"}
     r.update({"traffic": kernel_traffic(KIND_NAMES[dom], mode, d["cmacs"] / max(d["launches"], 1)),
               "kernel": KIND_NAMES[dom],
@@ -716,7 +747,8 @@ def main():
     # ---- dominant kernel roofline (per-launch CUDA events over the timed region)
     by_kind = kernel_breakdown(recs)
     peaks, peak_src = load_peaks()
-    roofline = roofline_of(by_kind, args.mode, peaks, peak_src, sustained=True)
+    probed = probe_peaks()
+    roofline = roofline_of(by_kind, args.mode, peaks, peak_src, sustained=True, probed=probed)
 
     # ---- end to end through the public API with host buffers
     leaf_bytes = net.leaf_bytes()
@@ -770,7 +802,7 @@ def main():
                    "l2": "working set > L2 (1 GiB intermediates), no flush",
                    "parallelism": "slices sharded over ranks" if world > 1 else "1 GPU"},
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launches,
-        "sharded_sum_check": shard_check,
+        "sharded_sum_check": shard_check, "peaks_probed": probed,
         "kernel_time_ms": {KIND_NAMES[k]: v["ms"] for k, v in by_kind.items()},
         "top_nodes": top_nodes(recs, stats),
         "tuned_shapes": [e for e in tune_table() if e[0] == mode],
@@ -782,6 +814,7 @@ def main():
             net.contract(lo, hi, MODES["fp32"], out=out)
         torch.cuda.synchronize()
         barrier()
+        net.set_timing(True)
         ev0.record(stream)
         f32_flops = 0
         for i in range(args.steps):
@@ -791,6 +824,10 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         Tf = ev0.elapsed_time(ev1) / 1e3
+        f_recs, _ = net.last_timings()
+        net.set_timing(False)
+        line["fp32_roofline"] = roofline_of(kernel_breakdown(f_recs), "fp32", peaks, peak_src, sustained=True,
+                                            probed=probed)
         if world > 1:
             t = torch.tensor([Tf], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -831,7 +868,8 @@ def main():
             line["split_modes"][m] = {
                 "value": m_flops / Tm / 1e12, "ms_per_step": 1e3 * Tm / args.steps,
                 "s_per_1024_slices": Tm / n_sl_tot * 1024,
-                "roofline": roofline_of(kernel_breakdown(m_recs), m, peaks, peak_src, sustained=True)}
+                "roofline": roofline_of(kernel_breakdown(m_recs), m, peaks, peak_src, sustained=True,
+                                        probed=probed)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         path_py = [tuple(p) for p in path]
         macs, dt, ref0 = run_oracle_sample(ref_net, path_py, S)

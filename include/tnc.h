@@ -270,6 +270,20 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable);
 tnc_status tnc_last_timings(tnc_net_t net, int* node, int* kind, int* batch, double* cmacs,
                             float* ms, int cap, int* n_out, int64_t* n_launches);
 
+/* Peak-rate probe for the roofline denominators (not part of the paper's
+ * method): launches, on `stream`, one kernel that keeps one execution unit
+ * busy and returns in *flops_out the floating-point operations it performs;
+ * the caller times the launch (e.g. with CUDA events on the same stream).
+ *  kind 0: FP32 FMA chains on the CUDA cores (2048 threads per SM; iters x 128
+ *          FMAs per thread)
+ *  kind 1: tcgen05.mma kind::tf32, 128 x 256 x 8 per instruction, one CTA per SM
+ *  kind 2: tcgen05.mma kind::f16 with BF16 operands, 128 x 256 x 16
+ *  kind 3: tcgen05.mma kind::f16 with FP16 operands, 128 x 256 x 16
+ * For the MMA kinds iters is the number of instructions per SM (rounded up to
+ * a multiple of 64). Errors: TNC_E_INVALID for an unknown kind or iters
+ * outside [1, 2^30]; TNC_E_CUDA if the launch fails. */
+tnc_status tnc_peak_probe(int kind, int64_t iters, double* flops_out, void* stream);
+
 /* Capacity, in complex doubles, of the static scratch of tnc_reduce_pair_noalloc. */
 #define TNC_NOALLOC_MAX_PARTIALS 65536
 

@@ -70,6 +70,7 @@ def load_library():
                               P(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p],
         "tnc_param_grads": [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p, ctypes.c_void_p],
+        "tnc_peak_probe": [ctypes.c_int, ctypes.c_int64, P(ctypes.c_double), ctypes.c_void_p],
         "tnc_last_timings": [ctypes.c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                              P(ctypes.c_double), P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int), c_i64p],
     }
@@ -105,6 +106,15 @@ def tune_table():
     buf = ctypes.create_string_buffer(1 << 20)
     _check(lib, lib.tnc_tune_table(buf, 1 << 20))
     return json.loads(buf.value.decode())
+
+
+def peak_probe(kind, iters, stream=None):
+    """Launch one peak-rate probe kernel (tnc_peak_probe) on `stream`; returns
+    the floating-point operations it performs (the caller times it)."""
+    lib = load_library()
+    flops = ctypes.c_double(0.0)
+    _check(lib, lib.tnc_peak_probe(int(kind), int(iters), ctypes.byref(flops), _stream_ptr(stream)))
+    return flops.value
 
 
 def contract_many(networks, ranges=None, mode=FP32, outs=None, use_graph=True, stream=None):

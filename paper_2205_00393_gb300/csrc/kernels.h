@@ -78,6 +78,7 @@ struct SplitParams {
     int64_t slice0;
     void* dst;
     int8_t* sexp;          // split FP16x2: scale exponents [batch][K / min(K, 256)][R] (written here)
+    int vec2;              // set by launch_split: pairs along the unit-stride mode load as 16 bytes
 };
 
 struct TcGemmParams {

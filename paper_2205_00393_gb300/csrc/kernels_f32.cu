@@ -42,9 +42,12 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
 // Shared-memory stages are double buffered: the gather of tile t+1 goes to
 // registers while tile t is multiplied, then to the other stage (one barrier
 // per tile). Accumulation is two-level: each group of GROUP_TILES k-tiles is
-// summed in a fresh partial that is then added to the result, so the FP32
-// rounding error grows like sqrt(64) + sqrt(K / 64) instead of sqrt(K). The
-// register budget (128 per thread) keeps two CTAs per SM.
+// summed in a fresh partial that is then added to the result with TwoSum
+// (Knuth's error-free addition), whose rounding errors are collected in a
+// per-thread compensation kept in shared memory and added once at the end.
+// The FP32 rounding error thus grows like the 64-term partial sums alone
+// instead of also with the K / 64 additions of partials, and the register
+// budget (128 per thread) still keeps two CTAs per SM.
 constexpr int PAD = 2;           // keeps 16-byte alignment of fragment rows
 constexpr int GROUP_TILES = 4;   // 64 k-terms per partial sum
 
@@ -58,7 +61,18 @@ struct GemmSmem {
     float2 As[2][BK][BM + PAD];
     float2 Bs[2][BK][2][BH];
     int64_t rowA[BM], colB[BN], klA[BK], klB[BK];
+    float2 comp[16][NT];  // TwoSum compensation of each thread's 4 x 4 outputs
 };
+
+// a += b with the rounding error of the addition added to c (TwoSum: the
+// error term is exact whatever the magnitudes of a and b)
+__device__ __forceinline__ void two_sum_into(float& a, float b, float& c) {
+    const float s = a + b;
+    const float bv = s - a;
+    const float e = (a - (s - bv)) + (b - bv);
+    a = s;
+    c += e;
+}
 
 // One 64x64 output tile `tile` of slice z (slice id slice0 + z) of the
 // contraction described by p.
@@ -131,6 +145,7 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
         for (int j = 0; j < 4; ++j) {
             acc[i][j] = make_float2(0.f, 0.f);
             part[i][j] = make_float2(0.f, 0.f);
+            sm.comp[4 * i + j][tid] = make_float2(0.f, 0.f);  // this thread's own slots
         }
 
     const int64_t ntiles = (K + BK - 1) / BK;
@@ -160,14 +175,24 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    acc[i][j].x += part[i][j].x;
-                    acc[i][j].y += part[i][j].y;
+                    float2 c = sm.comp[4 * i + j][tid];
+                    two_sum_into(acc[i][j].x, part[i][j].x, c.x);
+                    two_sum_into(acc[i][j].y, part[i][j].y, c.y);
+                    sm.comp[4 * i + j][tid] = c;
                     part[i][j] = make_float2(0.f, 0.f);
                 }
         }
         if (t + 1 < ntiles) stage_store(st ^ 1);
         __syncthreads();
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 c = sm.comp[4 * i + j][tid];
+            acc[i][j].x += c.x;
+            acc[i][j].y += c.y;
+        }
     float2* C = p.C + z * p.c_batch_stride;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -188,7 +213,8 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
 }
 
 __global__ void __launch_bounds__(NT, 2) k_gemm_f32(const __grid_constant__ GemmParams p) {
-    __shared__ __align__(16) GemmSmem sm;
+    extern __shared__ __align__(16) uint8_t gemm_dyn[];
+    GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gemm_dyn);
     gemm_tile(p, blockIdx.x, blockIdx.z, p.slice0, sm);
 }
 
@@ -197,7 +223,8 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_f32(const __grid_constant__ Gemm
 __global__ void __launch_bounds__(NT, 2) k_gemm_f32_group(const GemmParams* __restrict__ params,
                                                        const int64_t* __restrict__ tile_off, int n,
                                                        int64_t slice0) {
-    __shared__ __align__(16) GemmSmem sm;
+    extern __shared__ __align__(16) uint8_t gemm_dyn[];
+    GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gemm_dyn);
     const int64_t b = blockIdx.x;
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -340,11 +367,35 @@ __global__ void k_slice_sum_f32(const __grid_constant__ SumParams p, int batch, 
 
 }  // namespace
 
+__global__ void __launch_bounds__(NT, 2) k_gemm_f32_group_multi(const GemmParams* __restrict__ params,
+                                                             const int64_t* __restrict__ tile_off, int n,
+                                                             const int* __restrict__ net,
+                                                             const int64_t* __restrict__ rs0,
+                                                             const int* __restrict__ rb);
+
+// The FP32 GEMM kernels take GemmSmem (over 48 KB) as dynamic shared memory;
+// the limit is raised once per process (a host-side setting, not a stream
+// operation, so it is safe before or during graph capture).
+cudaError_t gemm_smem_attr() {
+    static cudaError_t done = [] {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm_f32_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm_f32_group_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(GemmSmem));
+        return e;
+    }();
+    return done;
+}
+
 cudaError_t launch_gemm_f32(const GemmParams& p, int batch, cudaStream_t s) {
     int64_t M = 1ll << p.mb, N = 1ll << p.nb;
     int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     if (tiles > 0x7fffffffll || batch < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
-    k_gemm_f32<<<dim3((unsigned)tiles, 1, batch), NT, 0, s>>>(p);
+    cudaError_t e = gemm_smem_attr();
+    if (e != cudaSuccess) return e;
+    k_gemm_f32<<<dim3((unsigned)tiles, 1, batch), NT, sizeof(GemmSmem), s>>>(p);
     return cudaGetLastError();
 }
 
@@ -356,7 +407,8 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_f32_group_multi(const GemmParams
                                                              const int* __restrict__ net,
                                                              const int64_t* __restrict__ rs0,
                                                              const int* __restrict__ rb) {
-    __shared__ __align__(16) GemmSmem sm;
+    extern __shared__ __align__(16) uint8_t gemm_dyn[];
+    GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gemm_dyn);
     const int64_t b = blockIdx.x;
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -445,7 +497,10 @@ cudaError_t launch_gemm_f32_group(const GemmParams* d_params, const int64_t* d_t
                                   int64_t total_tiles, int64_t slice0, int batch, cudaStream_t s) {
     if (n < 1 || total_tiles < 1 || total_tiles > 0x7fffffffll || batch < 1 || batch > 65535)
         return cudaErrorInvalidConfiguration;
-    k_gemm_f32_group<<<dim3((unsigned)total_tiles, 1, batch), NT, 0, s>>>(d_params, d_tile_off, n, slice0);
+    cudaError_t e = gemm_smem_attr();
+    if (e != cudaSuccess) return e;
+    k_gemm_f32_group<<<dim3((unsigned)total_tiles, 1, batch), NT, sizeof(GemmSmem), s>>>(d_params, d_tile_off, n,
+                                                                                       slice0);
     return cudaGetLastError();
 }
 
@@ -454,8 +509,10 @@ cudaError_t launch_gemm_f32_group_multi(const GemmParams* d_params, const int64_
                                         const int* d_rb, int max_batch, cudaStream_t s) {
     if (n < 1 || total_tiles < 1 || total_tiles > 0x7fffffffll || max_batch < 1 || max_batch > 65535)
         return cudaErrorInvalidConfiguration;
-    k_gemm_f32_group_multi<<<dim3((unsigned)total_tiles, 1, max_batch), NT, 0, s>>>(d_params, d_tile_off, n,
-                                                                                     d_net, d_rs0, d_rb);
+    cudaError_t e = gemm_smem_attr();
+    if (e != cudaSuccess) return e;
+    k_gemm_f32_group_multi<<<dim3((unsigned)total_tiles, 1, max_batch), NT, sizeof(GemmSmem), s>>>(
+        d_params, d_tile_off, n, d_net, d_rs0, d_rb);
     return cudaGetLastError();
 }
 

@@ -496,11 +496,58 @@ __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ S
     if (tid < SK) koff[tid] = bits_offset(k0 + tid, p.ks, p.kb, 0);
     __syncthreads();
     const int n = SR * SK;
-    for (int e = tid; e < n; e += 256) {
-        int rr, kk;
-        if (kfast) { kk = e % SK; rr = e / SK; }
-        else { rr = e % SR; kk = e / SR; }
-        tile[rr * LD + kk + (kk >> 3)] = src[roff[rr] + koff[kk]];
+    if (p.vec2) {
+        // pairs of elements adjacent along the unit-stride mode arrive as one
+        // 16-byte load; all of a thread's loads are in flight before any store
+        if (kfast) {  // 1024 pairs (rr, kk..kk+1)
+            float4 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int pi = tid + 256 * i, kk = 2 * (pi % (SK / 2)), rr = pi / (SK / 2);
+                v[i] = *reinterpret_cast<const float4*>(src + roff[rr] + koff[kk]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int pi = tid + 256 * i, kk = 2 * (pi % (SK / 2)), rr = pi / (SK / 2);
+                float2* d = tile + rr * LD + kk + (kk >> 3);
+                d[0] = make_float2(v[i].x, v[i].y);
+                d[1] = make_float2(v[i].z, v[i].w);
+            }
+        } else {      // 2048 pairs (rr..rr+1, kk)
+            float4 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int pi = tid + 256 * i, rr = 2 * (pi % (SR / 2)), kk = pi / (SR / 2);
+                v[i] = *reinterpret_cast<const float4*>(src + roff[rr] + koff[kk]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int pi = tid + 256 * i, rr = 2 * (pi % (SR / 2)), kk = pi / (SR / 2);
+                float2* d = tile + rr * LD + kk + (kk >> 3);
+                d[0] = make_float2(v[i].x, v[i].y);
+                d[LD] = make_float2(v[i].z, v[i].w);
+            }
+        }
+    } else {
+        for (int e0 = 0; e0 < n; e0 += 8 * 256) {
+            float2 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int e = e0 + tid + 256 * i;
+                int rr, kk;
+                if (kfast) { kk = e % SK; rr = e / SK; }
+                else { rr = e % SR; kk = e / SR; }
+                v[i] = src[roff[rr] + koff[kk]];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int e = e0 + tid + 256 * i;
+                int rr, kk;
+                if (kfast) { kk = e % SK; rr = e / SK; }
+                else { rr = e % SR; kk = e / SR; }
+                tile[rr * LD + kk + (kk >> 3)] = v[i];
+            }
+        }
     }
     __syncthreads();
     constexpr int Q = C_::PLANES;
@@ -683,7 +730,26 @@ int tc_elem_bytes(int mode) { return mode == 1 ? 4 : 2; }
 int tc_min_kb(int) { return 5; }
 int tc_scale_chunks(int kb) { return 1 << (kb > 8 ? kb - 8 : 0); }
 
-cudaError_t launch_split(const SplitParams& p, int mode, int batch, cudaStream_t s) {
+// Whether the split may load pairs of elements adjacent along the operand's
+// unit-stride mode (bit 0 of k, else bit 0 of the rows) as one 16-byte load:
+// the unit stride sits there, every other stride is even, and the base is
+// 16-byte aligned, so every pair starts on a 16-byte boundary.
+static bool split_pairs(const SplitParams& p) {
+    const bool kfast = p.kb > 0 && p.ks[0] == 1;
+    if (!kfast && !(p.rb > 0 && p.rs[0] == 1)) return false;
+    if (reinterpret_cast<uintptr_t>(p.src.ptr) % 16 || p.src.batch_stride % 2) return false;
+    for (int j = 0; j < p.src.n_sl; ++j)
+        if (p.src.sl_stride[j] % 2) return false;
+    for (int j = kfast ? 1 : 0; j < p.kb; ++j)
+        if (p.ks[j] % 2) return false;
+    for (int j = kfast ? 0 : 1; j < p.rb; ++j)
+        if (p.rs[j] % 2) return false;
+    return true;
+}
+
+cudaError_t launch_split(const SplitParams& p_in, int mode, int batch, cudaStream_t s) {
+    SplitParams p = p_in;
+    p.vec2 = split_pairs(p) ? 1 : 0;
     const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
     if (K < 32 || batch < 1 || batch > 65535 || p.rb < 7) return cudaErrorInvalidConfiguration;
     const bool kfast = p.kb > 0 && p.ks[0] == 1;
