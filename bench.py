@@ -43,7 +43,7 @@ TENSOR_FLOPS_PER_CMAC = {"bf16": 4 * 6 * 2, "tf32": 4 * 3 * 2, "bf16x2": 4 * 3 *
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
-              4: "k_split_operand", 7: "k_ksplit_reduce", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
+              4: "k_split_operand", 7: "k_ksplit_reduce", 8: "k_stem_fused", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
 
 
 def workload_name():
@@ -614,6 +614,73 @@ def backward_bench(args):
     return 0
 
 
+def stem_bench(args):
+    """Fused stem groups (secondary slicing, Sec. 5.2) on a time-ordered stem
+    path (every contraction a narrow step: a stem absorbing a gate): 28-qubit
+    4x7 grid, 12 cycles (seed 4), last 4 qubits open (16 amplitudes), not
+    sliced, so the stem reaches 2^28 complex elements (2 GiB, far above L2).
+    The whole contraction is timed with fusion on (the default) and off."""
+    import torch
+    from tnc_inputs import circuit_to_network, grid_rqc, stem_path
+    from paper_2205_00393_gb300 import Network
+    torch.cuda.set_device(0)
+    rows, cols = (int(x) for x in args.stem_grid.split("x"))
+    c = grid_rqc(rows, cols, 12, 4, n_open=4)
+    tn_ = circuit_to_network(c).as_complex64()
+    net = Network.from_tn(tn_)
+    net.set_path(stem_path(tn_, c))
+    stats = net.stats()
+    groups = stats["stem_groups"]
+    flops = node_flops(stats, 1)
+    stream = torch.cuda.current_stream()
+    out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
+    res = {}
+    for name, cap in (("fused", 12), ("unfused", 0)):
+        net.set_option("stem_cap_log2", cap)
+        ws = torch.empty(net.workspace_bytes(1), dtype=torch.uint8, device="cuda")
+        net.set_workspace(ws)
+        for _ in range(args.warmup):
+            net.contract(0, 1, 0, out=out)
+        torch.cuda.synchronize()
+        net.set_timing(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                net.contract(0, 1, 0, out=out)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        net.check_device()
+        T = ev0.elapsed_time(ev1) / 1e3 / args.steps
+        recs, n_launches = net.last_timings()
+        net.set_timing(False)
+        res[name] = {"s_per_call": T, "value": flops / T / 1e12, "launches_per_call": n_launches / args.steps,
+                     "kernel_time_ms_per_call": {KIND_NAMES.get(k, str(k)): v["ms"] / args.steps
+                                                 for k, v in kernel_breakdown(recs).items()},
+                     "clocks": clk.summary(), "amplitudes": out.cpu().numpy()}
+        del ws
+    a, b = res["fused"].pop("amplitudes"), res["unfused"].pop("amplitudes")
+    # the fused kernel against HBM: per launch it reads its input stem and writes its output once
+    st_ms = res["fused"]["kernel_time_ms_per_call"].get("k_stem_fused", 0.0)
+    st_bytes = sum(8 * ((1 << g[5]) + (1 << g[6])) for g in groups)
+    peaks, peak_src = load_peaks()
+    gbs = st_bytes / (st_ms / 1e3) / 1e9 if st_ms else None
+    line = {"metric": "fused stem groups (secondary slicing) on a stem path: effective complex TFLOPS",
+            "value": res["fused"]["value"], "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "speedup_vs_unfused": res["unfused"]["s_per_call"] / res["fused"]["s_per_call"],
+            "fused_vs_unfused_max_rel_diff": float(np.max(np.abs(a - b)) / np.max(np.abs(b))),
+            "groups": len(groups), "fused_steps": sum(g[1] for g in groups), "nodes": len(stats["nodes"]),
+            "k_stem_fused": {"ms_per_call": st_ms, "algorithmic_bytes_per_call": st_bytes,
+                             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                          "frac": gbs / peaks["hbm_gbs"] if gbs else None,
+                                          "peak_source": "hbm copy %s (MEASURED_PEAKS.json)" % peak_src}},
+            "fused": res["fused"], "unfused": res["unfused"],
+            "config": {"workload": "rqc-%s-12cyc-seed4-open4 time-ordered stem path, not sliced" % args.stem_grid,
+                       "max_log2_size": stats["max_log2_size"], "mode": "fp32 (narrow steps run on CUDA cores)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -639,6 +706,9 @@ def main():
                     help="42-qubit gradient configuration (adjoint vs finite differences) instead")
     ap.add_argument("--many", action="store_true",
                     help="time the batched uneven workload of many circuits instead")
+    ap.add_argument("--stem", action="store_true",
+                    help="time fused stem groups against separate launches on a 28-qubit stem path instead")
+    ap.add_argument("--stem-grid", default="4x7", help="--stem: grid of the circuit (ROWSxCOLS)")
     ap.add_argument("--backward", action="store_true",
                     help="time the adjoint pass (leaf environments of all fSim gates) instead")
     ap.add_argument("--single-node", default=None,
@@ -648,7 +718,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.slices_per_step is None:
-        plain = not (args.grad42 or args.c53 or args.many or args.backward or args.single_node)
+        plain = not (args.grad42 or args.c53 or args.many or args.backward or args.single_node or args.stem)
         args.slices_per_step = 4 if plain else 2
     if args.mode is None:
         if args.grad42:
@@ -667,6 +737,8 @@ def main():
         return single_node(args)
     if args.backward:
         return backward_bench(args)
+    if args.stem:
+        return stem_bench(args)
     if args.many:
         return many_bench(args)
     if args.grad42:

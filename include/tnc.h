@@ -202,7 +202,10 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
                              int mode, double* const* outs_c128, int use_graph, void* stream);
 
 /* JSON statistics of the current plan: Eq. 1 cost, Eq. 3 cost, Eq. 2
- * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace, and
+ * overhead, sliced ids, per-node (M, N, K) and kernel choice, workspace,
+ * "stem_groups": [first node index, steps, outer bits, largest inner bits,
+ * per slice, log2 elements of its input stem, log2 elements of its output]
+ * of every fused stem group for the current options, and
  * "tc_cuts": per split mode, [node index, A row-panel bits, B row-panel bits,
  * K-panel bits, K-split bits] of every tensor-core-eligible contraction for
  * the last batch size ("tc_cut_batch"). */
@@ -229,6 +232,22 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  and skip their recomputation while the plan, leaf data,
  *                  mode, batch, workspace and tuning are unchanged (the
  *                  workspace must not be used for anything else meanwhile)
+ *  "stem_cap_log2" 0 or 2..14 (default 12): fused stem groups (Sec. 5.2,
+ *                  secondary slicing). Consecutive narrow stem steps (a
+ *                  stem of more than 2^value elements absorbing branches of
+ *                  at most 16 contracted and 16 new elements) run as one
+ *                  launch when every tensor of the sub-path, without the stem
+ *                  modes that live through all of its steps, fits 2^value
+ *                  elements: one CTA per assignment of those long-lived modes
+ *                  keeps its sub-tensor in shared memory across the steps. A
+ *                  narrow step that starts no longer group runs alone in the
+ *                  same kernel. 0 turns fusion off: every contraction then
+ *                  runs on the GEMM kernels (tnc_contract_many never fuses)
+ *  "stem_min_outer_log2" 0..30 (default 7): a fused group needs at least
+ *                  2^value sub-tensors (CTAs) per slice
+ *  "stem_coalesce_bits" 0..6 (default 3): the lowest-stride modes of a
+ *                  group's input and output stem that stay inner, so that
+ *                  each CTA reads and writes runs of 2^value elements
  *  "tc_spin_limit" polls before a bounded device-side wait gives up (0 = the
  *                  kernel default, 2^24)
  *  "tc_test_stall" tests only: nonzero makes the tensor-core producer issue no
@@ -262,7 +281,8 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable);
 /* Launch records since the last tnc_set_timing (waits for their events): per timed
  * launch the node's tensor id, kernel kind (0 FP32 GEMM, 1 FP64 root reduction,
  * 2 GEMM root + FP64 slice sum, 3 tensor-core GEMM, 4 operand split,
- * 7 reduction of a tensor-core GEMM's K-split partials, -1 leaf slice sum), slice batch, complex multiply-accumulates of the
+ * 7 reduction of a tensor-core GEMM's K-split partials, 8 fused stem group (node = its
+ * output tensor), -1 leaf slice sum), slice batch, complex multiply-accumulates of the
  * launch (all its nodes and slices) and milliseconds; a grouped launch of
  * several nodes of one tree level reports node -1. Any output array may be NULL. *n_out receives the number
  * of records (TNC_E_INVALID if it exceeds cap); *n_launches (may be NULL) the

@@ -143,6 +143,52 @@ cudaError_t launch_f64_to_f32(const double2* src, int64_t n, float2* dst, cudaSt
 cudaError_t launch_param_grads(int n, const int64_t* env_off, const int64_t* d_off, const int64_t* size,
                                const float2* env, const float2* d, double2* out, cudaStream_t s);
 
+// Fused stem group (secondary slicing, Sec. 5.2): n consecutive stem steps
+// T_i = contract(T_{i-1}, B_i), each contracting nk <= 4 binary modes of the
+// stem with a small branch tensor B_i and adding its nn <= 4 other modes. The
+// stem modes that survive all n steps are the outer modes U: one CTA per
+// assignment of U (and per slice of the batch) gathers the sub-tensor X_0 of
+// T_0 over the remaining (inner) modes into shared memory, runs the n
+// absorptions there and writes X_n into T_n. A step with nk == nn runs in
+// place: new mode b takes the bit position of contracted mode b, so
+// X_i[.. n ..] = sum_k X_{i-1}[.. k ..] B_i[k, n] over the same positions.
+// Other steps lay X_i out as [kept modes of X_{i-1} | new modes] in a second
+// buffer. n = 1 is the streaming kernel of a single narrow contraction.
+constexpr int kStemMaxSteps = 32;
+constexpr int kStemMaxInner = 14;  // inner binary modes of any X_i
+
+struct StemStep {
+    int nr, nk, nn;                 // kept, contracted, new binary modes
+    int inplace;                    // nk == nn: new bit b takes the place of contracted bit b in X
+    int rstr[kStemMaxInner];        // general step: X_{i-1} stride of kept bit b (least significant first)
+    int kstr_x[4];                  // X_{i-1} stride of contracted bit b
+    int ins[4];                     // in place: the contracted bits' positions in X, ascending
+    int kstr_b[4], nstr_b[4];       // branch strides of contracted and new bits
+    int b_off;                      // offset of the step's dense [K][N] branch copy in shared memory
+    Operand br;                     // the branch tensor (sliced leaf or intermediate)
+};
+
+struct StemParams {
+    Operand in;                     // T_0
+    int n_in;                       // inner bits of X_0
+    int64_t istr[kStemMaxInner];    // T_0 stride of X_0 bit b
+    int nu;                         // outer bits
+    int64_t ustr_in[kMaxBits], ustr_out[kMaxBits];  // strides of outer bit b in T_0 and T_n
+    int n_out;                      // inner bits of X_n
+    int64_t ostr[kStemMaxInner];    // T_n stride of X_n bit b
+    float2* out;                    // T_n
+    int64_t out_batch_stride;
+    int nsteps, b_total;            // steps; complex elements of all dense branch copies
+    int two_buffers;                // 1 if some step is not in place
+    StemStep steps[kStemMaxSteps];
+};
+
+// Launch fused stem groups: params is a device array of n groups; group g
+// runs 2^nu[g] CTAs per slice (their maximum is max_outer_log2) with
+// 2 * 2^cap_log2 + b_total complex elements of shared memory.
+cudaError_t launch_stem_fused(const StemParams* d_params, const StemParams& host_params, int cap_log2,
+                              int64_t slice0, int batch, cudaStream_t s);
+
 // Message returned by tnc_last_error() on this thread.
 void set_last_error(const std::string& msg);
 

@@ -51,7 +51,7 @@ int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Kernel chosen for a contraction node.
 enum NodeKind {
-    K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_KRED = 7
+    K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_KRED = 7, K_STEM = 8
 };
 
 // Tensor-core eligibility of a non-root node in a split mode: both output
@@ -81,6 +81,16 @@ struct NodePlan {
     int chunks = 1;       // root reduction chunks
 };
 
+// A fused stem group (secondary slicing, Sec. 5.2): consecutive narrow stem
+// steps whose intermediates never leave shared memory (see kernels.h).
+struct StemGroupPlan {
+    std::vector<int> steps;   // indices into Plan::nodes, in order
+    int in = -1, out = -1;    // tensor ids of T_0 and T_n
+    std::vector<int> U;       // outer modes: live through every step of the group
+    int max_inner = 0;        // largest inner bit count of any X_i
+    bool per_slice = false;
+};
+
 struct Plan {
     bool valid = false;
     uint64_t version = 0;                                   // distinguishes rebuilt plans
@@ -92,6 +102,10 @@ struct Plan {
     std::vector<NodePlan> nodes;                            // SSA order
     std::vector<int64_t> out_stride;                        // result-order bit j -> root offset
     int obits = 0;
+    // fused stem groups for the cap they were planned with (stem_cap = -1: not planned)
+    int stem_cap = -1;
+    std::vector<StemGroupPlan> stems;
+    std::vector<int> stem_of;        // per node index: its group, or -1
 };
 
 struct Arena {
@@ -108,6 +122,7 @@ struct Group {
     bool per_slice = false;
     std::vector<int> fp32;   // node tensor ids run by one grouped FP32 launch
     std::vector<int> tc;     // nodes launched one by one: tensor-core nodes and large FP32 nodes
+    std::vector<int> stems;  // fused stem groups ending at this level (Plan::stems indices)
     int first = 0;           // first entry of the group's parameters in the table
     int off_first = 0;       // first entry of its n + 1 tile offsets
     int64_t tiles = 0;
@@ -118,6 +133,7 @@ struct GroupPlan {
     std::vector<Group> inv, ps;
     std::vector<tnc::GemmParams> params;
     std::vector<int64_t> tile_off;
+    std::vector<tnc::StemParams> stem_params;  // per Plan::stems entry (device copy in d_stem)
 };
 
 int64_t stride_of(const std::vector<std::pair<int, int64_t>>& s, int mode) {
@@ -168,6 +184,12 @@ struct tnc_net {
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
     int force_choice = -1;       // autotuning: force 0 (FP32) or a tensor-core row width
+    int stem_cap_log2 = 12;      // fused stem groups: inner sub-tensors up to 2^this elements (0 = off)
+    int stem_min_outer = 7;      // fused stem groups: at least 2^this sub-tensors (CTAs) per slice
+    int stem_coalesce_bits = 3;  // fused stem groups: lowest-stride modes of T_0 and T_n kept inner
+    bool in_many = false;        // building a many-network call: no fused stem groups
+    tnc::StemParams* d_stem = nullptr;
+    size_t d_stem_cap = 0;
     bool cache_invariants = false;  // keep slice-invariant inputs of per-slice nodes across calls
     std::string inv_key;            // state under which the cached invariants were computed
     uint64_t leaf_version = 0;      // bumped whenever leaf data changes
@@ -194,6 +216,7 @@ struct tnc_net {
         if (d_params) cudaFree(d_params);
         if (d_tile_off) cudaFree(d_tile_off);
         if (d_pg) cudaFree(d_pg);
+        if (d_stem) cudaFree(d_stem);
         if (ws_own) cudaFree(ws_own);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
@@ -337,6 +360,119 @@ void build_plan(tnc_net* net) {
 
 int64_t tensor_bytes(const Plan& P, int v) { return (int64_t)8 << P.layout[v].size(); }
 
+// ------------------------------------------------------ fused stem groups ----
+//
+// Secondary slicing (Sec. 5.2): along a chain of narrow stem steps (a big
+// intermediate absorbing small branch tensors one after another), the modes of
+// the stem that live through n consecutive steps are sliced for the GPU's
+// shared memory (one CTA per assignment) and the other (inner) modes are
+// carried through the n steps on chip. Following the paper, a group starts at
+// a step and grows while every tensor of the sub-path, restricted to its
+// inner modes, fits 2^cap elements; groups of at least two steps run fused.
+
+bool stem_fusion(const tnc_net* net) {
+    return net->stem_cap_log2 > 0 && !net->in_many && !net->tuning && net->plan.stem_cap == net->stem_cap_log2;
+}
+
+// A narrow stem step: the bigger operand A is an intermediate larger than
+// one on-chip sub-tensor (2^cap elements) and the branch B brings at most 4
+// contracted and 4 new modes.
+bool stem_step(const tnc_net* net, const NodePlan& np) {
+    return !np.is_root && np.kb <= 4 && np.nb <= 4 && np.A >= net->n_leaves &&
+           (int)net->plan.layout[np.A].size() > net->stem_cap_log2;
+}
+
+void plan_stems(tnc_net* net) {
+    Plan& P = net->plan;
+    const int cap = std::min(net->stem_cap_log2, tnc::kStemMaxInner);
+    P.stems.clear();
+    P.stem_of.assign(P.nodes.size(), -1);
+    P.stem_cap = net->stem_cap_log2;
+    if (cap <= 0) return;
+    const int nl = net->n_leaves;
+    const int nn = (int)P.nodes.size();
+    std::vector<int> next(nn, -1);
+    std::vector<char> has_prev(nn, 0);
+    for (int j = 0; j < nn; ++j) {
+        const NodePlan& nj = P.nodes[j];
+        if (!stem_step(net, nj)) continue;
+        const int i = nj.A - nl;  // the node whose output is this step's stem operand
+        if (i >= 0 && stem_step(net, P.nodes[i]) && P.nodes[i].per_slice == nj.per_slice) {
+            next[i] = j;
+            has_prev[j] = 1;
+        }
+    }
+    auto pos_stride = [](const std::vector<int>& L, int m) -> int64_t {
+        for (size_t q = 0; q < L.size(); ++q)
+            if (L[q] == m) return (int64_t)1 << (L.size() - 1 - q);
+        return -1;
+    };
+    // the group chain[i .. i + n): outer modes U and the largest inner size.
+    // The stem_coalesce_bits lowest-stride modes of T_0 and of T_n stay inner
+    // (they would otherwise interleave the CTAs' reads and writes), so each
+    // CTA moves runs of at least 2^stem_coalesce_bits consecutive elements.
+    const int cb = net->stem_coalesce_bits;
+    auto eval = [&](const std::vector<int>& chain, size_t i, size_t n, StemGroupPlan& g) -> bool {
+        const std::vector<int>& L0 = P.layout[P.nodes[chain[i]].A];
+        const std::vector<int>& Ln = P.layout[P.nodes[chain[i + n - 1]].v];
+        std::set<int> contracted;
+        for (size_t j = i; j < i + n; ++j)
+            for (int m : P.nodes[chain[j]].km) contracted.insert(m);
+        std::vector<int> U;
+        for (int m : L0) {
+            const int64_t s0 = pos_stride(L0, m), sn = pos_stride(Ln, m);
+            if (!contracted.count(m) && s0 >= ((int64_t)1 << cb) && sn >= ((int64_t)1 << cb)) U.push_back(m);
+        }
+        const std::set<int> Us(U.begin(), U.end());
+        int mx = (int)L0.size() - (int)U.size();
+        for (size_t j = i; j < i + n; ++j) {
+            int inner = 0;
+            for (int m : P.layout[P.nodes[chain[j]].v])
+                if (!Us.count(m)) ++inner;
+            mx = std::max(mx, inner);
+        }
+        if (mx > cap || (int)U.size() < net->stem_min_outer || U.size() > 30) return false;
+        g = StemGroupPlan();
+        g.steps.assign(chain.begin() + i, chain.begin() + i + n);
+        g.in = P.nodes[chain[i]].A;
+        g.out = P.nodes[chain[i + n - 1]].v;
+        g.U = U;
+        g.max_inner = mx;
+        g.per_slice = P.nodes[chain[i]].per_slice;
+        return true;
+    };
+    for (int c0 = 0; c0 < nn; ++c0) {
+        if (!stem_step(net, P.nodes[c0]) || has_prev[c0]) continue;
+        std::vector<int> chain;
+        for (int j = c0; j >= 0; j = next[j]) chain.push_back(j);
+        size_t i = 0;
+        while (i < chain.size()) {
+            // the longest group from chain[i] that fits; a single step is the
+            // streaming form of one narrow contraction
+            size_t best = 0;
+            StemGroupPlan bg;
+            for (size_t n = 1; i + n <= chain.size() && (int)n <= tnc::kStemMaxSteps; ++n) {
+                StemGroupPlan g;
+                if (!eval(chain, i, n, g)) break;
+                best = n;
+                bg = g;
+            }
+            if (best < 1) {
+                ++i;
+                continue;
+            }
+            const int gi = (int)P.stems.size();
+            for (int k : bg.steps) P.stem_of[k] = gi;
+            P.stems.push_back(bg);
+            i += best;
+        }
+    }
+}
+
+// Kernel parameters of fused stem group gi for a batch of nb slices (see kernels.h).
+tnc::StemParams stem_params(const tnc_net* net, const Arena& ar, char* ws, int gi, int64_t nb);
+
+
 std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice);
 
 // Plane data of one operand (rows x K, every plane, every batch entry); split
@@ -431,6 +567,8 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
     auto run_level = [&](const Group& g, int64_t b) {
         for (int v : g.fp32) ar.off[v] = alloc(b * tensor_bytes(P, v));
         for (int v : g.tc) ar.off[v] = alloc(b * tensor_bytes(P, v));
+        // fused stem groups: only T_n is stored; T_1 .. T_{n-1} stay on chip
+        for (int gi : g.stems) ar.off[P.stems[gi].out] = alloc(b * tensor_bytes(P, P.stems[gi].out));
         for (int v : g.tc) {
             const NodePlan& np = P.nodes[v - net->n_leaves];
             if (!shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root)) continue;
@@ -443,6 +581,13 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
                 for (int c : {np.A, np.B})
                     if (c >= net->n_leaves && P.per_slice[c] == (char)g.per_slice) release(ar.off[c]);
             }
+        for (int gi : g.stems) {
+            const StemGroupPlan& sg = P.stems[gi];
+            std::vector<int> ins{sg.in};
+            for (int k : sg.steps) ins.push_back(P.nodes[k].B);
+            for (int c : ins)
+                if (c >= net->n_leaves && P.per_slice[c] == (char)g.per_slice) release(ar.off[c]);
+        }
     };
     // phase 1: invariant levels (batch 1); invariant tensors consumed by
     // per-slice nodes stay live for the whole call
@@ -504,7 +649,72 @@ tnc_status ensure_plan(tnc_net* net) {
             return fail(TNC_E_INVALID, e.what());
         }
     }
+    if (net->plan.stem_cap != net->stem_cap_log2) plan_stems(net);
     return TNC_OK;
+}
+
+tnc::StemParams stem_params(const tnc_net* net, const Arena& ar, char* ws, int gi, int64_t nb) {
+    const Plan& P = net->plan;
+    const StemGroupPlan& g = P.stems[gi];
+    tnc::StemParams sp{};
+    const std::set<int> Us(g.U.begin(), g.U.end());
+    sp.in = operand(net, ar, ws, g.in, nb);
+    std::vector<int> X;  // modes of the current inner sub-tensor, most significant first
+    for (int m : P.layout[g.in])
+        if (!Us.count(m)) X.push_back(m);
+    sp.n_in = (int)X.size();
+    for (int b = 0; b < sp.n_in; ++b) sp.istr[b] = stride_of(P.str[g.in], X[sp.n_in - 1 - b]);
+    sp.nu = (int)g.U.size();
+    for (int b = 0; b < sp.nu; ++b) {
+        sp.ustr_in[b] = stride_of(P.str[g.in], g.U[b]);
+        sp.ustr_out[b] = stride_of(P.str[g.out], g.U[b]);
+    }
+    int boff = 0;
+    sp.nsteps = (int)g.steps.size();
+    for (int j = 0; j < sp.nsteps; ++j) {
+        const NodePlan& np = P.nodes[g.steps[j]];
+        tnc::StemStep& st = sp.steps[j];
+        std::map<int, int> bit;  // mode -> bit position in X (least significant 0)
+        for (size_t q = 0; q < X.size(); ++q) bit[X[q]] = (int)(X.size() - 1 - q);
+        const std::set<int> K(np.km.begin(), np.km.end());
+        std::vector<int> kept;
+        for (int m : X)
+            if (!K.count(m)) kept.push_back(m);
+        st.nr = (int)kept.size();
+        st.nk = np.kb;
+        st.nn = np.nb;
+        for (int b = 0; b < st.nr; ++b) st.rstr[b] = 1 << bit[kept[st.nr - 1 - b]];
+        for (int b = 0; b < st.nk; ++b) {
+            st.kstr_x[b] = 1 << bit[np.km[st.nk - 1 - b]];
+            st.kstr_b[b] = (int)np.bk[b];
+        }
+        for (int b = 0; b < st.nn; ++b) st.nstr_b[b] = (int)np.bn[b];
+        st.b_off = boff;
+        boff += 1 << (st.nk + st.nn);
+        st.br = operand(net, ar, ws, np.B, nb);
+        st.inplace = st.nk == st.nn && st.nk > 0;
+        if (st.inplace) {
+            // new mode nm[t] takes the place of contracted mode km[t] (k bit b
+            // and n bit b are km[nk-1-b] and nm[nn-1-b])
+            std::vector<int> pos;
+            for (int m : np.km) pos.push_back(bit[m]);
+            std::sort(pos.begin(), pos.end());
+            for (int t = 0; t < st.nk; ++t) st.ins[t] = pos[t];
+            for (int t = 0; t < st.nk; ++t)
+                for (int& m : X)
+                    if (m == np.km[t]) m = np.nm[t];
+        } else {
+            sp.two_buffers = 1;
+            X = kept;
+            X.insert(X.end(), np.nm.begin(), np.nm.end());
+        }
+    }
+    sp.b_total = boff;
+    sp.n_out = (int)X.size();
+    for (int b = 0; b < sp.n_out; ++b) sp.ostr[b] = stride_of(P.str[g.out], X[sp.n_out - 1 - b]);
+    sp.out = reinterpret_cast<float2*>(ws + ar.off[g.out]);
+    sp.out_batch_stride = g.per_slice ? tensor_bytes(P, g.out) / 8 : 0;
+    return sp;
 }
 
 tnc_status ensure_leaves(tnc_net* net, cudaStream_t st) {
@@ -565,9 +775,11 @@ int64_t pick_batch(const tnc_net* net, int64_t want, size_t budget, int mode) {
 
 std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice) {
     const Plan& P = net->plan;
+    const bool fuse = stem_fusion(net);
     std::map<int, int> level;  // tensor id -> level
     std::map<int, Group> by_level;
-    for (const NodePlan& np : P.nodes) {
+    for (size_t ni = 0; ni < P.nodes.size(); ++ni) {
+        const NodePlan& np = P.nodes[ni];
         if (np.per_slice != per_slice || np.is_root) continue;
         int l = 0;
         for (int c : {np.A, np.B}) {
@@ -577,6 +789,11 @@ std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice) {
         level[np.v] = l + 1;
         Group& g = by_level[l + 1];
         g.per_slice = per_slice;
+        if (fuse && P.stem_of[ni] >= 0) {  // a fused stem group runs at the level of its last step
+            const int gi = P.stem_of[ni];
+            if (P.stems[gi].steps.back() == (int)ni) g.stems.push_back(gi);
+            continue;
+        }
         // large contractions keep their own launch (parameters in kernel parameter space)
         if (shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root) ||
             (net->tuning && tc_node(mode, np.mb, np.nb, np.kb, np.is_root)) ||
@@ -595,7 +812,8 @@ std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice) {
 tnc_status ensure_groups(tnc_net* net, const Arena& ar, char* ws, int mode, int64_t nb, cudaStream_t s) {
     std::string key = std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string((uintptr_t)ws) +
                       ":" + std::to_string(net->plan.version) + ":" + std::to_string(g_tune_version) + ":" +
-                      std::to_string(net->force_choice) + ":" + std::to_string(net->tuning ? 1 : 0);
+                      std::to_string(net->force_choice) + ":" + std::to_string(net->tuning ? 1 : 0) + ":" +
+                      std::to_string(stem_fusion(net) ? net->stem_cap_log2 : 0);
     if (key == net->group_key) return TNC_OK;
     GroupPlan G;
     G.inv = level_groups(net, mode, false);
@@ -619,6 +837,21 @@ tnc_status ensure_groups(tnc_net* net, const Arena& ar, char* ws, int mode, int6
             G.tile_off.push_back(tiles);
             g.tiles = tiles;
         }
+    }
+    if (stem_fusion(net)) {
+        G.stem_params.resize(net->plan.stems.size());
+        for (const auto* list : {&G.inv, &G.ps})
+            for (const Group& g : *list)
+                for (int gi : g.stems) G.stem_params[gi] = stem_params(net, ar, ws, gi, g.per_slice ? nb : 1);
+        if (G.stem_params.size() > net->d_stem_cap) {
+            if (net->d_stem) CUDA_TRY(cudaFree(net->d_stem));
+            net->d_stem = nullptr;
+            CUDA_TRY(cudaMalloc(&net->d_stem, G.stem_params.size() * sizeof(tnc::StemParams)));
+            net->d_stem_cap = G.stem_params.size();
+        }
+        if (!G.stem_params.empty())
+            CUDA_TRY(cudaMemcpyAsync(net->d_stem, G.stem_params.data(), G.stem_params.size() * sizeof(tnc::StemParams),
+                                     cudaMemcpyHostToDevice, s));
     }
     if (G.params.size() > net->d_params_cap) {
         if (net->d_params) CUDA_TRY(cudaFree(net->d_params));
@@ -770,6 +1003,14 @@ tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, in
         gp.c_batch_stride = g.per_slice ? tensor_bytes(net->plan, np.v) / 8 : 0;
         gp.slice0 = slice0;
         if ((st = launch_node(net, ar, ws, np, gp, b, mode, s)) != TNC_OK) return st;
+    }
+    for (int gi : g.stems) {
+        const StemGroupPlan& sg = net->plan.stems[gi];
+        double cm = 0.0;
+        for (int k : sg.steps) cm += node_cmacs(net, net->plan.nodes[k].v);
+        CUDA_TRY(timed_begin(net, sg.out, K_STEM, b, s, cm * b));
+        CUDA_TRY(tnc::launch_stem_fused(net->d_stem + gi, net->groups.stem_params[gi], sg.max_inner, slice0, b, s));
+        CUDA_TRY(timed_end(net, s));
     }
     return TNC_OK;
 }
@@ -1240,6 +1481,12 @@ tnc_status many_run(ManyCall& mc, cudaStream_t s) {
 tnc_status many_build(ManyCall& mc, cudaStream_t s) {
     tnc_status st;
     const int n = (int)mc.nets.size();
+    // the merged level launches of many networks take no fused stem groups
+    struct NoFuse {
+        std::vector<tnc_net*>& nets;
+        explicit NoFuse(std::vector<tnc_net*>& v) : nets(v) { for (auto* t : nets) t->in_many = true; }
+        ~NoFuse() { for (auto* t : nets) t->in_many = false; }
+    } no_fuse(mc.nets);
     mc.arenas.resize(n);
     mc.wss.resize(n);
     mc.nb.resize(n);
@@ -1799,6 +2046,25 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
         if (value < 16 || value > 40) return fail(TNC_E_INVALID, "tc_plane_cap_log2 must be in [16, 40]");
         net->plane_cap_log2 = (int)value;
         net->group_key.clear();
+    } else if (k == "stem_cap_log2") {
+        if (value != 0 && (value < 2 || value > tnc::kStemMaxInner))
+            return fail(TNC_E_INVALID, "stem_cap_log2 must be 0 or in [2, 14]");
+        net->stem_cap_log2 = (int)value;
+        net->plan.stem_cap = -1;
+        net->group_key.clear();
+        net->inv_key.clear();
+    } else if (k == "stem_coalesce_bits") {
+        if (value < 0 || value > 6) return fail(TNC_E_INVALID, "stem_coalesce_bits must be in [0, 6]");
+        net->stem_coalesce_bits = (int)value;
+        net->plan.stem_cap = -1;
+        net->group_key.clear();
+        net->inv_key.clear();
+    } else if (k == "stem_min_outer_log2") {
+        if (value < 0 || value > 30) return fail(TNC_E_INVALID, "stem_min_outer_log2 must be in [0, 30]");
+        net->stem_min_outer = (int)value;
+        net->plan.stem_cap = -1;
+        net->group_key.clear();
+        net->inv_key.clear();
     } else if (k == "cache_invariants") {
         net->cache_invariants = value != 0;
         net->inv_key.clear();
@@ -2092,6 +2358,16 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
             o << "]";
         }
         o << "}";
+        // fused stem groups for the current cap: [first node, steps, outer bits, inner bits, per slice]
+        if (net->plan.stem_cap != net->stem_cap_log2) plan_stems(net);
+        o << ",\"stem_cap_log2\":" << net->stem_cap_log2 << ",\"stem_groups\":[";
+        for (size_t gi = 0; gi < net->plan.stems.size(); ++gi) {
+            const StemGroupPlan& g = net->plan.stems[gi];
+            o << (gi ? "," : "") << "[" << g.steps.front() << "," << g.steps.size() << "," << g.U.size() << ","
+              << g.max_inner << "," << (g.per_slice ? 1 : 0) << "," << net->plan.layout[g.in].size() << ","
+              << net->plan.layout[g.out].size() << "]";
+        }
+        o << "]";
     } else {
         o << ",\"plan_error\":\"" << perr << "\"";
     }
