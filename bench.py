@@ -43,7 +43,7 @@ TENSOR_FLOPS_PER_CMAC = {"bf16": 4 * 6 * 2, "tf32": 4 * 3 * 2, "bf16x2": 4 * 3 *
 # dense TF32 / BF16 nominal rate ratio (1.1 vs 2.25 PFLOP/s per GPU)
 TF32_OVER_BF16 = 1.1 / 2.25
 KIND_NAMES = {0: "k_gemm_f32", 1: "k_root_partials", 2: "k_gemm_f32+slice_sum", 3: "k_cgemm_tc",
-              4: "k_split_operand", 7: "k_ksplit_reduce", 8: "k_stem_fused", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
+              4: "k_split_operand", 7: "k_ksplit_reduce", 8: "k_stem_fused", 9: "k_persist", -1: "k_slice_sum_f32", -2: "k_leaf_env_accum"}
 
 
 def workload_name():
@@ -165,7 +165,7 @@ def kernel_breakdown(recs):
         d = by_kind.setdefault(r["kind"], {"ms": 0.0, "cmacs": 0.0, "launches": 0})
         d["ms"] += r["ms"]
         d["launches"] += 1
-        if r["kind"] in (0, 1, 2, 3):
+        if r["kind"] in (0, 1, 2, 3, 9):
             d["cmacs"] += r["cmacs"]
     return by_kind
 
@@ -191,18 +191,27 @@ def probe_peaks(iters_ffma=300, iters_mma=1 << 22):
     return out
 
 
-def roofline_of(by_kind, mode, peaks, peak_src, sustained, probed=None):
+def roofline_of(by_kind, mode, peaks, peak_src, sustained, probed=None, persist_tc_cmacs=None):
     """Roofline entry of the kernel with the most time. Tensor-core kernels in
     BF16/FP16 take the measured cuBLAS BF16 peak (the FP16 dense rate equals
     BF16's); TF32 takes the library's own kind::tf32 probe when given (else
     the BF16 peak times the nominal 1.1/2.25 ratio); FP32 CUDA-core kernels
-    take the FFMA probe (else the unit-count derivation)."""
+    take the FFMA probe (else the unit-count derivation). The persistent
+    kernel (k_persist) in a split mode counts only its tensor-core
+    contractions as work (persist_tc_cmacs, from the library's stats) against
+    its whole time, which also holds the splits, the FP32 contractions and the
+    reductions it runs."""
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     d = by_kind[dom]
     share = d["ms"] / sum(v["ms"] for v in by_kind.values())
     sec = d["ms"] / 1e3
+    tc_cmacs = None
     if dom == 3:
-        achieved = d["cmacs"] * TENSOR_FLOPS_PER_CMAC[mode] / sec / 1e12
+        tc_cmacs = d["cmacs"]
+    elif dom == 9 and mode != "fp32" and persist_tc_cmacs:
+        tc_cmacs = persist_tc_cmacs
+    if tc_cmacs is not None:
+        achieved = tc_cmacs * TENSOR_FLOPS_PER_CMAC[mode] / sec / 1e12
         if mode == "tf32" and probed:
             peak = probed["tf32_tflops"]
             src = "tcgen05 kind::tf32 probe of this run (tnc_peak_probe, 128x256x8 MMAs, one CTA per SM)"
@@ -216,6 +225,9 @@ def roofline_of(by_kind, mode, peaks, peak_src, sustained, probed=None):
              "frac": achieved / peak, "peak_source": src,
              "algorithmic_flops": "%d*M*N*K tensor flops per node (4 real products, %s part pairs)" % (
                  TENSOR_FLOPS_PER_CMAC[mode], mode)}
+        if dom == 9:
+            r["algorithmic_flops"] += ("; tensor-core contractions of the persistent kernel only, over its "
+                                       "whole time")
     else:
         achieved = d["cmacs"] * 8 / sec / 1e12
         peak = probed["ffma_tflops"] if probed else FP32_PEAK_TFLOPS
@@ -294,6 +306,12 @@ def apply_options(net, args):
         net.set_option("tc_row_bytes", args.tc_row_bytes)
     if args.tc_group_m:
         net.set_option("tc_group_m", args.tc_group_m)
+    if args.persistent is not None:
+        net.set_option("persistent", args.persistent)
+
+
+def executor_of(by_kind):
+    return "persistent (k_persist, one launch per slice batch)" if 9 in by_kind else "one launch per tree level"
 
 
 def single_node(args):
@@ -697,6 +715,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tc-row-bytes", type=int, default=None)
     ap.add_argument("--tc-group-m", type=int, default=None)
+    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1],
+                    help="executor: 1 the persistent work-list kernel, 0 one launch per tree level "
+                         "(default: the library's choice)")
     ap.add_argument("--c53", action="store_true",
                     help="53-qubit lattice, 20 cycles, t = 30: time a fixed subset of slices")
     ap.add_argument("--c53-slices", type=int, default=1024)
@@ -802,6 +823,7 @@ def main():
         barrier()
     T = ev0.elapsed_time(ev1) / 1e3
     recs, n_launches = net.last_timings()
+    persist_tc = net.stats()["timed_persist_tc_cmacs"]
     net.set_timing(False)
     n_sl_done = sum(slice_range(args.warmup + i)[1] - slice_range(args.warmup + i)[0]
                     for i in range(args.steps))
@@ -820,7 +842,8 @@ def main():
     by_kind = kernel_breakdown(recs)
     peaks, peak_src = load_peaks()
     probed = probe_peaks()
-    roofline = roofline_of(by_kind, args.mode, peaks, peak_src, sustained=True, probed=probed)
+    roofline = roofline_of(by_kind, args.mode, peaks, peak_src, sustained=True, probed=probed,
+                           persist_tc_cmacs=persist_tc)
 
     # ---- end to end through the public API with host buffers
     leaf_bytes = net.leaf_bytes()
@@ -874,6 +897,7 @@ def main():
                    "l2": "working set > L2 (1 GiB intermediates), no flush",
                    "parallelism": "slices sharded over ranks" if world > 1 else "1 GPU"},
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launches,
+        "executor": executor_of(by_kind),
         "sharded_sum_check": shard_check, "peaks_probed": probed,
         "kernel_time_ms": {KIND_NAMES[k]: v["ms"] for k, v in by_kind.items()},
         "top_nodes": top_nodes(recs, stats),
@@ -900,6 +924,7 @@ def main():
         net.set_timing(False)
         line["fp32_roofline"] = roofline_of(kernel_breakdown(f_recs), "fp32", peaks, peak_src, sustained=True,
                                             probed=probed)
+        line["fp32_executor"] = executor_of(kernel_breakdown(f_recs))
         if world > 1:
             t = torch.tensor([Tf], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -931,6 +956,7 @@ def main():
             torch.cuda.synchronize()
             Tm = ev0.elapsed_time(ev1) / 1e3
             m_recs, _ = net.last_timings()
+            m_tc = net.stats()["timed_persist_tc_cmacs"]
             net.set_timing(False)
             if world > 1:
                 t = torch.tensor([Tm], device="cuda", dtype=torch.float64)
@@ -941,7 +967,8 @@ def main():
                 "value": m_flops / Tm / 1e12, "ms_per_step": 1e3 * Tm / args.steps,
                 "s_per_1024_slices": Tm / n_sl_tot * 1024,
                 "roofline": roofline_of(kernel_breakdown(m_recs), m, peaks, peak_src, sustained=True,
-                                        probed=probed)}
+                                        probed=probed, persist_tc_cmacs=m_tc),
+                "executor": executor_of(kernel_breakdown(m_recs))}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         path_py = [tuple(p) for p in path]
         macs, dt, ref0 = run_oracle_sample(ref_net, path_py, S)

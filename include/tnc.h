@@ -208,7 +208,9 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
  * of every fused stem group for the current options, and
  * "tc_cuts": per split mode, [node index, A row-panel bits, B row-panel bits,
  * K-panel bits, K-split bits] of every tensor-core-eligible contraction for
- * the last batch size ("tc_cut_batch"). */
+ * the last batch size ("tc_cut_batch"); "persistent" (the option) and
+ * "timed_persist_tc_cmacs": the complex multiply-accumulates that timed
+ * persistent launches (since tnc_set_timing) ran on the tensor cores. */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 
 /* Tuning options of the tensor-core GEMM (no effect on results):
@@ -248,6 +250,23 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *  "stem_coalesce_bits" 0..6 (default 3): the lowest-stride modes of a
  *                  group's input and output stem that stay inner, so that
  *                  each CTA reads and writes runs of 2^value elements
+ *  "persistent"    0 or 1 (default 1): the persistent executor. A call whose
+ *                  contractions all fit it (no fused stem group in use, no
+ *                  tensor-core contraction cut into row or K panels) runs
+ *                  each batch of slices as ONE launch of a work-list kernel
+ *                  with one CTA per SM: the tasks (FP32 GEMM tiles, operand
+ *                  split blocks, 128 x 128 tensor-core tiles, K-split
+ *                  reductions, root chunks and sums) are taken in list order
+ *                  from an atomic ticket and each waits, on device counters,
+ *                  for the tasks that produce its inputs and for the previous
+ *                  tree level. Results equal the per-level launches' up to
+ *                  the order of FP32 additions in a K split; other calls, and
+ *                  0, use one launch per tree level
+ *  "persist_wait_ms" 0..600000 (default 0 = 10 s): bound of one dependency
+ *                  wait of the persistent executor; a wait that runs out
+ *                  stops every CTA and tnc_check_device reports TNC_E_TIMEOUT
+ *  "persist_test_stall" tests only: nonzero adds a task that waits on a
+ *                  counter no task decrements, so that bound runs out
  *  "tc_spin_limit" polls before a bounded device-side wait gives up (0 = the
  *                  kernel default, 2^24)
  *  "tc_test_stall" tests only: nonzero makes the tensor-core producer issue no
@@ -282,7 +301,8 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable);
  * launch the node's tensor id, kernel kind (0 FP32 GEMM, 1 FP64 root reduction,
  * 2 GEMM root + FP64 slice sum, 3 tensor-core GEMM, 4 operand split,
  * 7 reduction of a tensor-core GEMM's K-split partials, 8 fused stem group (node = its
- * output tensor), -1 leaf slice sum), slice batch, complex multiply-accumulates of the
+ * output tensor), 9 persistent executor (node -1; one launch per slice batch), -1 leaf
+ * slice sum), slice batch, complex multiply-accumulates of the
  * launch (all its nodes and slices) and milliseconds; a grouped launch of
  * several nodes of one tree level reports node -1. Any output array may be NULL. *n_out receives the number
  * of records (TNC_E_INVALID if it exceeds cap); *n_launches (may be NULL) the

@@ -15,6 +15,7 @@
 
 #include <cstdint>
 #include <string>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace tnc {
@@ -188,6 +189,97 @@ struct StemParams {
 // 2 * 2^cap_log2 + b_total complex elements of shared memory.
 cudaError_t launch_stem_fused(const StemParams* d_params, const StemParams& host_params, int cap_log2,
                               int64_t slice0, int batch, cudaStream_t s);
+
+// ------------------------------------------------- persistent executor
+//
+// One launch runs a whole slice batch (or many-network round): one CTA per
+// SM pulls tasks from a device work list in list order. A task runs when the
+// counters it waits on have reached zero; when it is done it decrements its
+// own counter. The list is topologically ordered (a task only waits on tasks
+// earlier in the list, which CTAs that are running have already taken), so
+// the waits always end; they are bounded all the same and report
+// TNC_E_TIMEOUT in the error word.
+enum PersistTaskType {
+    PT_GEMM = 0,   // one 64x64 FP32 tile (idx: GemmParams, item: tile)
+    PT_SPLIT = 1,  // count split blocks from item on (idx: SplitParams)
+    PT_TC = 2,     // one 128x128 tensor-core tile (idx: TcNode, item: tile + tiles * K split)
+    PT_KRED = 3,   // K-split reduction of 16384 complex pairs from item * 16384 (idx: KredParams)
+    PT_ROOT = 4,   // one chunk of a final contraction (idx: RootParams, item: chunk)
+    PT_ACC = 5,    // ordered FP64 sum of a final contraction's chunk sums into the result (idx: AccParams)
+    PT_SUM = 6,    // FP64 slice sum of a root tensor with more than 64 outputs (idx: SumTaskParams)
+    PT_STALL = 7   // tests only: waits on a counter nothing signals
+};
+
+struct PersistTask {
+    int type;
+    int idx;        // parameter entry of the task's type
+    int64_t item;   // tile, chunk or first block
+    int z;          // batch entry
+    int net;        // network (slice0 = rs0[net] when the launch has a table)
+    int count;      // PT_SPLIT: blocks
+    int wait[3];    // counters to wait for (-1: none)
+    int signal;     // counter to decrement when done
+    int signal2;    // a second one (-1: none): the task's tree level
+};
+
+// One tensor-core contraction of a work list: the launch parameters and the
+// tensor maps of its planes (TMA reads them from global memory).
+struct TcNode {
+    CUtensorMap map_a, map_b;
+    TcGemmParams p;
+    int nbatch;     // batch entries (the K-split partials are [split][z][m][n])
+};
+
+struct KredParams {
+    const float2* partial;
+    int nsplit, batch, nb;
+    int64_t mn2;            // float4 steps of two complex elements per batch entry
+    float2* C;
+    int64_t c_batch_stride, c_ld;
+    int accumulate;
+};
+
+struct AccParams {
+    const double2* partials;  // [count][R] in the root's order
+    int count;
+    PermParams pp;
+    double2* out;
+};
+
+struct SumTaskParams {
+    SumParams sp;
+    int batch;
+    double2* out;
+};
+
+struct PersistParams {
+    const PersistTask* tasks;
+    int ntasks;
+    int* counters;
+    int* ticket;
+    int* err;
+    const GemmParams* gemm;
+    const SplitParams* split;
+    const TcNode* tc;
+    const KredParams* kred;
+    const RootParams* root;
+    const AccParams* acc;
+    const SumTaskParams* sum;
+    const int64_t* rs0;     // per network first slice of the batch (null: slice0)
+    int64_t slice0;
+    uint64_t wait_ns;       // bound of one dependency wait (0: 10 s)
+    uint32_t spin_limit;    // bound of one tensor-core pipeline wait (0: default)
+};
+
+// Launch the persistent executor for mode (FP32 or a split mode) over p's
+// work list; ticket and counters must hold 0 and the initial counts.
+cudaError_t launch_persist(const PersistParams& p, int mode, cudaStream_t s);
+// Fill a work-list tensor-core node (planes from launch_split layouts).
+bool tc_make_node(TcNode* node, const TcGemmParams& p, int mode, const void* planesA, const void* planesB, int batch);
+// Output tiles (x K splits) of a tensor-core contraction.
+int64_t tc_node_tiles(const TcGemmParams& p);
+// Split blocks of one batch entry; the split's pair-load flag is set.
+int64_t tc_split_prepare(SplitParams& p);
 
 // Message returned by tnc_last_error() on this thread.
 void set_last_error(const std::string& msg);

@@ -39,6 +39,7 @@
 
 #include <cstring>
 
+#include "f32_device.cuh"
 #include "kernels.h"
 
 namespace tnc {
@@ -208,89 +209,99 @@ constexpr int EPI_LDW = 66;    // float2 per row of a warp's staged 32 x 64 outp
 static_assert(EPI_WARPS * 32 * EPI_LDW * 8 <= SMEM_PIPE, "staged epilogue fits the pipeline ring");
 constexpr int PRODUCER_WARP = 8, MMA_WARP = 9, NTHREADS = 320;
 
-template <int KIND, int ROWB>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_cgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const __grid_constant__ TcGemmParams p) {
+// Shared-memory state of one CTA's tensor-core pipeline.
+struct TcShared {
+    uint64_t full_bar[8], empty_bar[8], tfull[2], tfree[2], drain_bar;
+    uint32_t tmem_base;
+    int abort;
+    float colscale[EPI_WARPS][64];  // split FP16x2: per-warp column factors of a chunk
+};
+
+// k-blocks and TMEM chunks a CTA's tensor-core roles have processed so far:
+// the barrier phases of the pipeline continue from one output tile to the
+// next when a CTA computes several (the persistent executor).
+struct TcPipe {
+    uint32_t it = 0, ch = 0;
+};
+
+// thread 0, before the CTA-wide barrier that precedes the first tile
+__device__ __forceinline__ void tc_init(TcShared& sh) {
+    for (int s = 0; s < 8; ++s) {
+        mbar_init(smem_u32(&sh.full_bar[s]), 1);
+        mbar_init(smem_u32(&sh.empty_bar[s]), 1);
+    }
+    for (int t = 0; t < 2; ++t) {
+        mbar_init(smem_u32(&sh.tfull[t]), 1);
+        mbar_init(smem_u32(&sh.tfree[t]), EPI_WARPS);
+    }
+    mbar_init(smem_u32(&sh.drain_bar), 1);
+    sh.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One 128x128 complex output tile of the contraction p: tile index `cta` in
+// grouped rasterisation order, K split ky, batch entry z of nbatch. Run by all
+// NTHREADS threads (warps 0-7 epilogue, warp 8 TMA producer, warp 9 MMA
+// issuer); smem is the TMA ring (also the epilogue's staging area), tmem the
+// CTA's 512 TMEM columns. On a bounded wait that gives up, sh.abort and
+// *p.err are set and the roles stop (MMAs and loads in flight drained).
+template <int KIND, int ROWB, bool GLOBAL_MAPS = false>
+__device__ __forceinline__ void tc_tile(const CUtensorMap* tmA, const CUtensorMap* tmB, const TcGemmParams& p,
+                                        int64_t cta, int ky, int z, int nbatch, uint8_t* smem, TcShared& sh,
+                                        uint32_t tmem, TcPipe& pipe) {
     using C_ = Cfg<KIND, ROWB>;
     constexpr int PT = C_::PART_TILE;
     const int GROUP_M = p.group_m < 1 ? 1 : p.group_m;
-    extern __shared__ __align__(1024) uint8_t dsmem[];
-    __shared__ __align__(8) uint64_t full_bar[C_::STAGES], empty_bar[C_::STAGES], tfull[2], tfree[2], drain_bar;
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
-    __shared__ __align__(16) float colscale[EPI_WARPS][64];  // split FP16x2: per-warp column factors of a chunk
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
-    // grouped rasterisation: consecutive CTAs cover GROUP_M row tiles x all column tiles
+    // grouped rasterisation: consecutive tiles cover GROUP_M row tiles x all column tiles
     const int64_t tiles_n = N / TN, tiles_m = M / TM;
     const int64_t per_group = (int64_t)GROUP_M * tiles_n;
-    const int64_t cta = blockIdx.x;
     const int64_t grp = cta / per_group, in_grp = cta % per_group;
     const int64_t gm = (tiles_m - grp * GROUP_M) < GROUP_M ? (tiles_m - grp * GROUP_M) : GROUP_M;
     const int m0 = (int)((grp * GROUP_M + in_grp % gm) * TM);
     const int n0 = (int)((in_grp / gm) * TN);
-    const int z = blockIdx.z;
     const int za = p.a_shared ? 0 : z, zb = p.b_shared ? 0 : z;  // batch entry of each operand's planes
-    const int nkb = (int)((K >> p.ksplit_bits) / C_::BK);         // k-blocks of this CTA's K split
-    const int kb_off = (int)blockIdx.y * nkb;
+    const int nkb = (int)((K >> p.ksplit_bits) / C_::BK);         // k-blocks of this K split
+    const int kb_off = ky * nkb;
     const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;  // k-blocks per chunk
     const int nchunks = nkb / kpc;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C_::STAGES; ++s) {
-            mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), 1);
-        }
-        for (int t = 0; t < 2; ++t) {
-            mbar_init(smem_u32(&tfull[t]), 1);
-            mbar_init(smem_u32(&tfree[t]), EPI_WARPS);
-        }
-        mbar_init(smem_u32(&drain_bar), 1);
-        abort_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (warp == MMA_WARP) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"(512u)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;
-    volatile int* abort_flag = &abort_sh;
+    volatile int* abort_flag = &sh.abort;
     const uint32_t spin = p.spin_limit ? p.spin_limit : kSpinLimit;
 
     if (warp == PRODUCER_WARP && lane == 0) {
         // ---------------- TMA producer: one stage per k-block, every plane of A and of B
+        asm volatile("fence.proxy.async.global;" ::: "memory");  // planes written by generic stores
+        if constexpr (GLOBAL_MAPS) {  // tensor maps in global memory: acquire them for the tensormap proxy
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmB) : "memory");
+        }
         int issued = 0;
         for (int it = 0; it < nkb && !p.test_stall; ++it) {
-            const int s = it % C_::STAGES;
-            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, abort_flag, spin)) {
-                abort_sh = 1;
+            const uint32_t g = pipe.it + it;
+            const int s = g % C_::STAGES;
+            const uint32_t ph = (g / C_::STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&sh.empty_bar[s]), ph ^ 1u, abort_flag, spin)) {
+                sh.abort = 1;
                 atomicExch(p.err, kErrTimeout);
                 break;
             }
             const uint32_t sa = smem_u32(smem + s * C_::STAGE_BYTES);
-            const uint32_t fb = smem_u32(&full_bar[s]);
+            const uint32_t fb = smem_u32(&sh.full_bar[s]);
             mbar_expect_tx(fb, C_::STAGE_BYTES);
-            tma_load_4d(sa, &tmA, (it + kb_off) * C_::BK, m0, 0, za, fb);
-            tma_load_4d(sa + C_::OP_BYTES, &tmB, (it + kb_off) * C_::BK, n0, 0, zb, fb);
+            tma_load_4d(sa, tmA, (it + kb_off) * C_::BK, m0, 0, za, fb);
+            tma_load_4d(sa + C_::OP_BYTES, tmB, (it + kb_off) * C_::BK, n0, 0, zb, fb);
             issued = it + 1;
         }
         if (*abort_flag) {
             // drain: wait (bounded) for every load that may still be in flight
             int first = issued - C_::STAGES < 0 ? 0 : issued - C_::STAGES;
             for (int it = first; it < issued; ++it) {
-                const int s = it % C_::STAGES;
-                const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-                for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&full_bar[s]), ph); ++i) {
+                const uint32_t g = pipe.it + it;
+                const int s = g % C_::STAGES;
+                const uint32_t ph = (g / C_::STAGES) & 1u;
+                for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&sh.full_bar[s]), ph); ++i) {
                 }
             }
         }
@@ -299,13 +310,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         constexpr uint32_t idesc = instr_desc<KIND>(false), idesc_neg = instr_desc<KIND>(true);
         bool any = false;
         for (int it = 0; it < nkb && !*abort_flag; ++it) {
-            const int s = it % C_::STAGES;
-            const uint32_t ph = (uint32_t)(it / C_::STAGES) & 1u;
-            const int c = it / kpc, kbi = it % kpc, buf = c & 1;
-            if ((kbi == 0 && c >= 2 &&
-                 !mbar_wait(smem_u32(&tfree[buf]), (uint32_t)((c - 2) >> 1) & 1u, abort_flag, spin)) ||
-                !mbar_wait(smem_u32(&full_bar[s]), ph, abort_flag, spin)) {
-                abort_sh = 1;
+            const uint32_t g = pipe.it + it;
+            const int s = g % C_::STAGES;
+            const uint32_t ph = (g / C_::STAGES) & 1u;
+            const int kbi = it % kpc;
+            const uint32_t cgl = pipe.ch + it / kpc;  // chunk over all tiles of this CTA
+            const int buf = cgl & 1;
+            if ((kbi == 0 && cgl >= 2 &&
+                 !mbar_wait(smem_u32(&sh.tfree[buf]), ((cgl - 2) >> 1) & 1u, abort_flag, spin)) ||
+                !mbar_wait(smem_u32(&sh.full_bar[s]), ph, abort_flag, spin)) {
+                sh.abort = 1;
                 atomicExch(p.err, kErrTimeout);
                 break;
             }
@@ -331,12 +345,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             any = true;
-            mma_commit(smem_u32(&empty_bar[s]));
-            if (kbi == kpc - 1) mma_commit(smem_u32(&tfull[buf]));
+            mma_commit(smem_u32(&sh.empty_bar[s]));
+            if (kbi == kpc - 1) mma_commit(smem_u32(&sh.tfull[buf]));
         }
         if (*abort_flag && any) {
-            mma_commit(smem_u32(&drain_bar));
-            for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&drain_bar), 0); ++i) {
+            mma_commit(smem_u32(&sh.drain_bar));
+            for (uint32_t i = 0; i < spin && !mbar_try(smem_u32(&sh.drain_bar), 0); ++i) {
             }
         }
     } else if (warp < EPI_WARPS) {
@@ -357,19 +371,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ea_row = p.sexp_a + (int64_t)za * nch * M + m0 + 32 * g + lane;
             eb_col = p.sexp_b + (int64_t)zb * nch * N + n0 + 64 * h;
         }
-        float* colf = colscale[warp];
+        float* colf = sh.colscale[warp];
         bool ok = true;
         for (int c = 0; c < nchunks && ok; ++c) {
-            const int buf = c & 1;
+            const uint32_t cgl = pipe.ch + c;
+            const int buf = cgl & 1;
             int w = 0;
-            if (lane == 0) w = mbar_wait(smem_u32(&tfull[buf]), (uint32_t)(c >> 1) & 1u, abort_flag, spin) ? 1 : 0;
+            if (lane == 0) w = mbar_wait(smem_u32(&sh.tfull[buf]), (cgl >> 1) & 1u, abort_flag, spin) ? 1 : 0;
             w = __shfl_sync(0xffffffffu, w, 0);
             if (!w) {
                 ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int64_t cg = (int64_t)blockIdx.y * nchunks + c;  // chunk index over the planes' K
+            const int64_t cg = (int64_t)ky * nchunks + c;  // chunk index over the planes' K
             float sa = 1.f;
             if constexpr (KIND == 3) {
                 sa = pow2f(-(int)ea_row[cg * M]);
@@ -397,11 +412,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tfree[buf]));
+            if (lane == 0) mbar_arrive(smem_u32(&sh.tfree[buf]));
         }
         if (!ok) {
-            if (lane == 0 && !abort_sh) {
-                abort_sh = 1;
+            if (lane == 0 && !sh.abort) {
+                sh.abort = 1;
                 atomicExch(p.err, kErrTimeout);
             }
         } else {
@@ -414,9 +429,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 reinterpret_cast<float4*>(stg + lane * EPI_LDW + j)[0] = make_float4(cr[j], ci[j], cr[j + 1], ci[j + 1]);
             __syncwarp();
             const int64_t ld = p.ksplit_bits ? N : (p.c_ld ? p.c_ld : N);
-            float2* cb = p.ksplit_bits
-                             ? p.partial + ((int64_t)blockIdx.y * gridDim.z + z) * (N << p.mb)
-                             : p.C + (int64_t)z * p.c_batch_stride;
+            float2* cb = p.ksplit_bits ? p.partial + ((int64_t)ky * nbatch + z) * (N << p.mb)
+                                       : p.C + (int64_t)z * p.c_batch_stride;
             float2* cbase = cb + (int64_t)(m0 + 32 * g) * ld + n0 + 64 * h;
             if (p.accumulate) {
 #pragma unroll 4
@@ -434,8 +448,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
     }
+    pipe.it += nkb;
+    pipe.ch += nchunks;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncwarp();
+}
+
+template <int KIND, int ROWB>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_cgemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ TcGemmParams p) {
+    extern __shared__ __align__(1024) uint8_t dsmem[];
+    __shared__ TcShared sh;
+    const int warp = threadIdx.x >> 5;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+    if (threadIdx.x == 0) tc_init(sh);
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sh.tmem_base;
+    TcPipe pipe;
+    tc_tile<KIND, ROWB>(&tmA, &tmB, p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, smem, sh, tmem, pipe);
     __syncthreads();
     if (warp == MMA_WARP) {
         __syncwarp();
@@ -474,27 +513,36 @@ __host__ __device__ inline int split_tile_rows(int kb, bool kfast) { return (kfa
 // shared-memory slots per tile row: one padding slot every 8 k keeps the
 // write phase's 8-wide groups on distinct banks
 __host__ __device__ inline int split_ld(int sk) { return sk + sk / 8 + 1; }
+// largest split tile in bytes: SR * SK = 4096 elements, one padding slot per
+// 8 k and one per row (SR <= 128 rows, which K >= 32 ensures)
+constexpr int kSplitTileBytesMax = (4096 + 4096 / 8 + 128) * 8;
+
+template <int BAR>
+__device__ __forceinline__ void tc_bar() {
+    if constexpr (BAR == 0) __syncthreads();
+    else asm volatile("bar.sync 1, 256;" ::: "memory");
+}
 
 // planes: out[((z * PLANES + q) * R + r) * K + k], q = t * PARTS + part (t = 0 Re, 1 Im);
-// FP16x2 scale exponents: sexp[(z * (K / SK) + chunk) * R + r]
-template <int KIND>
-__global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ SplitParams p) {
+// FP16x2 scale exponents: sexp[(z * (K / SK) + chunk) * R + r]. One split tile
+// (block) of batch entry z (slice id slice0 + z), run by threads 0-255; BAR as
+// in the FP32 routines (0: whole CTA, 1: named barrier over 256 threads).
+template <int KIND, int BAR>
+__device__ __forceinline__ void split_block(const SplitParams& p, int64_t block, int z, int64_t slice0, float2* tile,
+                                            int64_t* roff, int64_t* koff) {
     using C_ = Cfg<KIND, 64>;
-    extern __shared__ float2 tile[];
-    __shared__ int64_t roff[128], koff[256];
     const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
     const bool kfast = p.kb > 0 && p.ks[0] == 1;
     const int SK = split_tile_k(p.kb);
     const int SR = split_tile_rows(p.kb, kfast);
     const int LD = split_ld(SK);
     const int64_t tiles_k = K / SK;
-    const int64_t r0 = (blockIdx.x / tiles_k) * SR, k0 = (blockIdx.x % tiles_k) * SK;
-    const int z = blockIdx.z;
-    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, p.slice0 + z);
+    const int64_t r0 = (block / tiles_k) * SR, k0 = (block % tiles_k) * SK;
+    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, slice0 + z);
     const int tid = threadIdx.x;
     if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
     if (tid < SK) koff[tid] = bits_offset(k0 + tid, p.ks, p.kb, 0);
-    __syncthreads();
+    tc_bar<BAR>();
     const int n = SR * SK;
     if (p.vec2) {
         // pairs of elements adjacent along the unit-stride mode arrive as one
@@ -549,7 +597,7 @@ __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ S
             }
         }
     }
-    __syncthreads();
+    tc_bar<BAR>();
     constexpr int Q = C_::PLANES;
     const int64_t plane = R * K;
     uint8_t* out = reinterpret_cast<uint8_t*>(p.dst) + (int64_t)z * Q * plane * C_::ELEM;
@@ -618,6 +666,14 @@ __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ S
             }
         }
     }
+    tc_bar<BAR>();  // the tile buffer may be refilled after this
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ SplitParams p) {
+    extern __shared__ float2 tile[];
+    __shared__ int64_t roff[128], koff[256];
+    split_block<KIND, 0>(p, blockIdx.x, blockIdx.z, p.slice0, tile, roff, koff);
 }
 
 // ------------------------------------------------------------ K-split reduction
@@ -719,6 +775,223 @@ cudaError_t launch_tc_rows(const TcGemmParams& p, const void* pa, const void* pb
     return launch_tc_impl<KIND, 64>(p, pa, pb, batch, s);
 }
 
+// ------------------------------------------------------------ persistent executor
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// One CTA per SM. Thread 0 takes the next task in list order, waits (bounded
+// by p.wait_ns of the global timer) until the counters it names reach zero,
+// and the CTA runs it; every thread fences its writes (and, for split planes,
+// hands them to the TMA's async proxy) before thread 0 decrements the task's
+// counter. A wait that runs out, a tensor-core wait that gives up, or an error
+// another CTA has recorded stops every CTA at its next task.
+template <int KIND, int NT_>
+__global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid_constant__ PersistParams P) {
+    extern __shared__ __align__(1024) uint8_t dsmem[];
+    __shared__ TcShared sh;
+    __shared__ int task_sh;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+    // scratch of the task types, all at the start of the dynamic shared memory:
+    // the split tile at 0 and its offset tables after the largest tile
+    constexpr int kSplitOffBytes = 40 * 1024;
+    static_assert(kSplitTileBytesMax <= kSplitOffBytes && kSplitOffBytes + (128 + 256) * 8 <= SMEM_PIPE,
+                  "split scratch fits the ring");
+    int64_t* split_roff = reinterpret_cast<int64_t*>(smem + kSplitOffBytes);
+    int64_t* split_koff = split_roff + 128;
+    double2* root_red = reinterpret_cast<double2*>(smem);
+    int64_t(*root_ta)[256] = reinterpret_cast<int64_t(*)[256]>(smem + 4096);
+    int64_t(*root_tb)[256] = reinterpret_cast<int64_t(*)[256]>(smem + 4096 + 5 * 256 * 8);
+    constexpr bool TC = KIND >= 0;
+    if (tid == 0) {
+        if constexpr (TC) tc_init(sh);
+        else sh.abort = 0;
+    }
+    if constexpr (TC) {
+        if (warp == MMA_WARP) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&sh.tmem_base)),
+                         "r"(512u)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if constexpr (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = TC ? sh.tmem_base : 0u;
+    const uint64_t wait_ns = P.wait_ns ? P.wait_ns : 10000000000ull;
+    TcPipe pipe;
+    for (;;) {
+        if (tid == 0) {
+            int t = atomicAdd(P.ticket, 1);
+            if (t < P.ntasks) {
+                const PersistTask& tk = P.tasks[t];
+                const uint64_t t0 = global_ns();
+                for (int w = 0; w < 3 && t >= 0; ++w) {
+                    const int c = tk.wait[w];
+                    if (c < 0) continue;
+                    while (ld_acquire(P.counters + c) > 0) {
+                        if (*(volatile int*)P.err) {
+                            t = -1;
+                            break;
+                        }
+                        if (global_ns() - t0 > wait_ns) {
+                            atomicExch(P.err, kErrTimeout);
+                            t = -1;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+            }
+            task_sh = t;
+        }
+        __syncthreads();
+        const int t = task_sh;
+        if (t < 0 || t >= P.ntasks) break;
+        __threadfence();
+        const PersistTask tk = P.tasks[t];
+        const int64_t slice0 = P.rs0 ? P.rs0[tk.net] : P.slice0;
+        switch (tk.type) {
+            case PT_GEMM:
+                if (tid < 256)
+                    f32dev::gemm_tile<1>(P.gemm[tk.idx], tk.item, tk.z, slice0,
+                                         *reinterpret_cast<f32dev::GemmSmem*>(smem));
+                break;
+            case PT_SPLIT:
+                if constexpr (TC) {
+                    if (tid < 256) {
+                        for (int b = 0; b < tk.count; ++b)
+                            split_block<KIND, 1>(P.split[tk.idx], tk.item + b, tk.z, slice0,
+                                                 reinterpret_cast<float2*>(smem), split_roff, split_koff);
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                    }
+                }
+                break;
+            case PT_TC:
+                if constexpr (TC) {
+                    const TcNode& nd = P.tc[tk.idx];
+                    const int64_t tiles = (1ll << (nd.p.mb - 7)) << (nd.p.nb - 7);
+                    tc_tile<KIND, 64, true>(&nd.map_a, &nd.map_b, nd.p, tk.item % tiles, (int)(tk.item / tiles),
+                                            tk.z, nd.nbatch, smem, sh, tmem, pipe);
+                }
+                break;
+            case PT_KRED: {
+                const KredParams& kp = P.kred[tk.idx];
+                const int64_t i0 = tk.item * 16384, i1 = i0 + 16384 < kp.mn2 ? i0 + 16384 : kp.mn2;
+                for (int64_t i = i0 + tid; i < i1; i += NT_) {
+                    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+                    for (int sp = 0; sp < kp.nsplit; ++sp) {
+                        const float4 v = reinterpret_cast<const float4*>(kp.partial)[((int64_t)sp * kp.batch + tk.z) * kp.mn2 + i];
+                        a0 += v.x;
+                        a1 += v.y;
+                        a2 += v.z;
+                        a3 += v.w;
+                    }
+                    const int64_t e = 2 * i, m = e >> kp.nb, n = e & ((1ll << kp.nb) - 1);
+                    float4* dst = reinterpret_cast<float4*>(kp.C + (int64_t)tk.z * kp.c_batch_stride + m * kp.c_ld + n);
+                    float4 r = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+                    if (kp.accumulate) {
+                        const float4 o = *dst;
+                        r = make_float4(o.x + r.x, o.y + r.y, o.z + r.z, o.w + r.w);
+                    }
+                    *dst = r;
+                }
+            } break;
+            case PT_ROOT:  // count: the AccParams entry whose partials this chunk fills
+                if (tid < 256) {
+                    const RootParams& rp = P.root[tk.idx];
+                    const int R = 1 << (rp.g.mb + rp.g.nb);
+                    double2* part = const_cast<double2*>(P.acc[tk.count].partials);
+                    f32dev::root_chunk<1>(rp, (int)tk.item, tk.z, slice0,
+                                          part + ((int64_t)tk.z * rp.chunks + tk.item) * R, root_red, root_ta,
+                                          root_tb);
+                }
+                break;
+            case PT_ACC: {
+                const AccParams& ap = P.acc[tk.idx];
+                const int64_t R = 1ll << ap.pp.obits;
+                for (int64_t r = tid; r < R; r += NT_) {
+                    const int64_t src = f32dev::bits_offset(r, ap.pp.ostride, ap.pp.obits, 0);
+                    double2 acc = make_double2(0.0, 0.0);
+                    for (int i = 0; i < ap.count; ++i) {
+                        const double2 v = ap.partials[(int64_t)i * R + src];
+                        acc.x += v.x;
+                        acc.y += v.y;
+                    }
+                    ap.out[r].x += acc.x;
+                    ap.out[r].y += acc.y;
+                }
+            } break;
+            case PT_SUM: {
+                const SumTaskParams& sp = P.sum[tk.idx];
+                const int64_t R = 1ll << sp.sp.obits;
+                for (int64_t r = tid; r < R; r += NT_) {
+                    const int64_t off = f32dev::bits_offset(r, sp.sp.ostride, sp.sp.obits, 0);
+                    double2 acc = make_double2(0.0, 0.0);
+                    for (int z = 0; z < sp.batch; ++z) {
+                        const float2* src = sp.sp.src.ptr + z * sp.sp.src.batch_stride +
+                                            f32dev::slice_offset(sp.sp.src, slice0 + z);
+                        const float2 v = src[off];
+                        acc.x += v.x;
+                        acc.y += v.y;
+                    }
+                    sp.out[r].x += acc.x;
+                    sp.out[r].y += acc.y;
+                }
+            } break;
+            default:
+                break;
+        }
+        __threadfence();
+        // this task's generic shared-memory stores (split tiles, GEMM operands,
+        // staged outputs) before the next task's TMA writes to the same bytes
+        if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (sh.abort) atomicExch(P.err, kErrTimeout);
+            atomicSub(P.counters + tk.signal, 1);
+            if (tk.signal2 >= 0) atomicSub(P.counters + tk.signal2, 1);
+        }
+        if (sh.abort) break;
+    }
+    if constexpr (TC) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp == MMA_WARP) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+        }
+    }
+}
+
+template <int KIND, int NT_>
+cudaError_t launch_persist_impl(const PersistParams& p, size_t smem, cudaStream_t s) {
+    static size_t set_for = 0;
+    if (smem > set_for) {
+        cudaError_t e = cudaFuncSetAttribute(k_persist<KIND, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_for = smem;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    k_persist<KIND, NT_><<<KIND >= 0 ? sms : 2 * sms, NT_, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // tnc_mode -> kernel configuration: 1 TF32 (2 parts), 2 BF16 (3 parts), 3 BF16 (2 parts),
@@ -779,6 +1052,45 @@ cudaError_t launch_ksplit_reduce(const float2* partial, int ksplit_bits, int bat
     k_ksplit_reduce<<<dim3(blocks, batch), 256, 0, s>>>(reinterpret_cast<const float4*>(partial), 1 << ksplit_bits,
                                                         batch, mn2, nb, C, c_batch_stride, c_ld, accumulate);
     return cudaGetLastError();
+}
+
+cudaError_t launch_persist(const PersistParams& p, int mode, cudaStream_t s) {
+    if (!p.tasks || p.ntasks < 0 || !p.counters || !p.ticket || !p.err) return cudaErrorInvalidValue;
+    if (mode == 0) {
+        const size_t smem = (sizeof(f32dev::GemmSmem) > 28 * 1024 ? sizeof(f32dev::GemmSmem) : 28 * 1024) + 1024;
+        return launch_persist_impl<-1, 256>(p, smem, s);
+    }
+    switch (kind_of(mode)) {
+        case 0: return launch_persist_impl<0, NTHREADS>(p, Cfg<0, 64>::STAGES * Cfg<0, 64>::STAGE_BYTES + 1024, s);
+        case 1: return launch_persist_impl<1, NTHREADS>(p, Cfg<1, 64>::STAGES * Cfg<1, 64>::STAGE_BYTES + 1024, s);
+        case 3: return launch_persist_impl<3, NTHREADS>(p, Cfg<3, 64>::STAGES * Cfg<3, 64>::STAGE_BYTES + 1024, s);
+        default: return launch_persist_impl<2, NTHREADS>(p, Cfg<2, 64>::STAGES * Cfg<2, 64>::STAGE_BYTES + 1024, s);
+    }
+}
+
+bool tc_make_node(TcNode* node, const TcGemmParams& p, int mode, const void* planesA, const void* planesB,
+                  int batch) {
+    const int64_t M = 1ll << p.mb, N = 1ll << p.nb, K = 1ll << p.kb;
+    if (p.mb < 7 || p.nb < 7 || p.kb < tc_min_kb(mode) || (K >> p.ksplit_bits) < 32) return false;
+    if ((K >> p.ksplit_bits) > KC_ELEMS && (K >> p.ksplit_bits) % KC_ELEMS) return false;
+    node->p = p;
+    node->nbatch = batch;
+    switch (kind_of(mode)) {
+        case 0: return make_map<0, 64>(&node->map_a, planesA, M, K, batch) && make_map<0, 64>(&node->map_b, planesB, N, K, batch);
+        case 1: return make_map<1, 64>(&node->map_a, planesA, M, K, batch) && make_map<1, 64>(&node->map_b, planesB, N, K, batch);
+        case 3: return make_map<3, 64>(&node->map_a, planesA, M, K, batch) && make_map<3, 64>(&node->map_b, planesB, N, K, batch);
+        default: return make_map<2, 64>(&node->map_a, planesA, M, K, batch) && make_map<2, 64>(&node->map_b, planesB, N, K, batch);
+    }
+}
+
+int64_t tc_node_tiles(const TcGemmParams& p) { return ((1ll << (p.mb - 7)) << (p.nb - 7)) << p.ksplit_bits; }
+
+int64_t tc_split_prepare(SplitParams& p) {
+    p.vec2 = split_pairs(p) ? 1 : 0;
+    const bool kfast = p.kb > 0 && p.ks[0] == 1;
+    const int64_t SK = split_tile_k(p.kb), SR = split_tile_rows(p.kb, kfast);
+    if (p.kb < 5 || SR > 128 || (1ll << p.rb) < SR) return 0;  // the tile and offset tables would not fit
+    return ((1ll << p.rb) / SR) * ((1ll << p.kb) / SK);
 }
 
 cudaError_t launch_cgemm_tc(const TcGemmParams& p, int mode, const void* planesA, const void* planesB,

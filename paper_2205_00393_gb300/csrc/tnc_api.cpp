@@ -51,7 +51,7 @@ int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Kernel chosen for a contraction node.
 enum NodeKind {
-    K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_KRED = 7, K_STEM = 8
+    K_GEMM_F32 = 0, K_ROOT_F64 = 1, K_GEMM_ROOT_SUM = 2, K_TC = 3, K_SPLIT = 4, K_KRED = 7, K_STEM = 8, K_PERSIST = 9
 };
 
 // Tensor-core eligibility of a non-root node in a split mode: both output
@@ -136,6 +136,20 @@ struct GroupPlan {
     std::vector<tnc::StemParams> stem_params;  // per Plan::stems entry (device copy in d_stem)
 };
 
+// Device copy of a work list: one allocation holding the tables, the initial
+// counters, the counters themselves and the ticket.
+struct DeviceWorkList {
+    void* mem = nullptr;
+    tnc::PersistParams prm{};
+    int* init = nullptr;
+    size_t n_counters = 0;
+    double cmacs = 0.0;     // complex multiply-accumulates of one launch
+    double tc_cmacs = 0.0;  // the part of them on the tensor cores
+    ~DeviceWorkList() {
+        if (mem) cudaFree(mem);
+    }
+};
+
 int64_t stride_of(const std::vector<std::pair<int, int64_t>>& s, int mode) {
     for (auto& p : s)
         if (p.first == mode) return p.second;
@@ -209,6 +223,12 @@ struct tnc_net {
     struct TimedLaunch { int node; int kind; int batch; double cmacs; size_t ev; };
     std::vector<TimedLaunch> timed;
     int64_t launches = 0;
+    // persistent executor (one launch per slice batch); its device work lists by key
+    int persistent = 1;
+    uint64_t persist_wait_ns = 0;    // bound of one dependency wait (0: 10 s)
+    int persist_test_stall = 0;      // tests only: one task waits on a counter nothing signals
+    std::map<std::string, std::unique_ptr<DeviceWorkList>> worklists;
+    double timed_persist_tc_cmacs = 0.0;  // tensor-core share of the timed persistent launches
 
     ~tnc_net() {
         if (d_leaves) cudaFree(d_leaves);
@@ -569,11 +589,16 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
         for (int v : g.tc) ar.off[v] = alloc(b * tensor_bytes(P, v));
         // fused stem groups: only T_n is stored; T_1 .. T_{n-1} stay on chip
         for (int gi : g.stems) ar.off[P.stems[gi].out] = alloc(b * tensor_bytes(P, P.stems[gi].out));
+        // the split planes of a level's tensor-core contractions are live
+        // together: the persistent executor runs a level's contractions at
+        // the same time
         for (int v : g.tc) {
             const NodePlan& np = P.nodes[v - net->n_leaves];
-            if (!shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root)) continue;
-            tc_planes(np, b);
-            tc_release(np);
+            if (shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root)) tc_planes(np, b);
+        }
+        for (int v : g.tc) {
+            const NodePlan& np = P.nodes[v - net->n_leaves];
+            if (shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root)) tc_release(np);
         }
         for (auto* list : {&g.fp32, &g.tc})
             for (int v : *list) {
@@ -1015,6 +1040,453 @@ tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, in
     return TNC_OK;
 }
 
+
+// ------------------------------------------------------ persistent executor
+//
+// A work list is the whole computation of one launch: every contraction of a
+// slice batch (and, in the first batch of a call, the slice-invariant ones)
+// broken into tasks, in level order so that every task only waits on tasks
+// before it (see kernels.h). Per node, one counter counts the tasks of its
+// last stage; a task waits on the counters of the nodes that produce its
+// inputs in the same launch.
+
+struct WorkList {
+    std::vector<tnc::PersistTask> tasks;
+    std::vector<int> counters;
+    std::vector<tnc::GemmParams> gemm;
+    std::vector<tnc::SplitParams> split;
+    std::vector<tnc::TcNode> tc;
+    std::vector<tnc::KredParams> kred;
+    std::vector<tnc::RootParams> root;
+    std::vector<tnc::AccParams> acc;
+    std::vector<tnc::SumTaskParams> sum;
+    double cmacs = 0.0, tc_cmacs = 0.0;
+    int new_counter(int count) {
+        counters.push_back(count);
+        return (int)counters.size() - 1;
+    }
+    // tree-level chain of the network being emitted: tasks wait on the
+    // previous level's counter and also count down the current level's
+    int lvl_prev = -1, lvl_cur = -1;
+    void task(int type, int idx, int64_t item, int z, int net, int count, int w0, int w1, int w2, int signal) {
+        tnc::PersistTask t{};
+        t.type = type;
+        t.idx = idx;
+        t.item = item;
+        t.z = z;
+        t.net = net;
+        t.count = count;
+        t.wait[0] = w0;
+        t.wait[1] = w1;
+        t.wait[2] = w2;
+        t.signal = signal;
+        t.signal2 = lvl_cur;
+        // a slot left free takes the previous level (a task of a level waits
+        // for the whole level before it: the workspace reuses memory across levels)
+        if (lvl_prev >= 0) {
+            bool have = false;
+            for (int q = 0; q < 3; ++q) have |= t.wait[q] == lvl_prev;
+            for (int q = 0; q < 3 && !have; ++q)
+                if (t.wait[q] < 0) {
+                    t.wait[q] = lvl_prev;
+                    have = true;
+                }
+        }
+        if (lvl_cur >= 0) ++counters[lvl_cur];
+        tasks.push_back(t);
+    }
+    void begin_level() {
+        lvl_prev = lvl_cur;
+        lvl_cur = new_counter(0);
+    }
+};
+
+
+constexpr int kSplitBlocksPerTask = 16;
+
+// Tasks of one non-root contraction np for batch b into W; ctr maps a tensor
+// produced in this launch to its counter. False if the contraction needs row
+// or K panels (not run by the persistent executor).
+bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b, int mode, int netidx, WorkList& W,
+             std::map<int, int>& ctr) {
+    const Plan& P = net->plan;
+    tnc::GemmParams g = gemm_params(net, ar, ws, np, b);
+    g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
+    g.c_batch_stride = np.per_slice ? tensor_bytes(P, np.v) / 8 : 0;
+    // inputs come from earlier tree levels, which the level chain already waits for
+    const int wa = -1, wb = -1;
+    W.cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * b;
+    const int choice = shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root);
+    if (!choice) {
+        const int gi = (int)W.gemm.size();
+        W.gemm.push_back(g);
+        const int64_t tiles = tnc::gemm_f32_tiles(np.mb, np.nb);
+        const int c = W.new_counter((int)(tiles * b));
+        for (int z = 0; z < b; ++z)
+            for (int64_t t = 0; t < tiles; ++t) W.task(tnc::PT_GEMM, gi, t, z, netidx, 0, wa, wb, -1, c);
+        ctr[np.v] = c;
+        return true;
+    }
+    const TcCut cut = tc_cut(net, mode, g.mb, g.nb, g.kb, b);
+    if (cut.pA || cut.pB || cut.pK) return false;
+    W.tc_cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * b;
+    const size_t i = np.v - net->n_leaves;
+    char* pa = ws + ar.planes_a[i];
+    char* pb = ws + ar.planes_b[i];
+    const bool a_shared = b > 1 && g.A.batch_stride == 0 && g.A.n_sl == 0;
+    const bool b_shared = b > 1 && g.B.batch_stride == 0 && g.B.n_sl == 0;
+    int8_t* sexp_a = nullptr;
+    int8_t* sexp_b = nullptr;
+    if (mode == TNC_SPLIT_FP16X2) {
+        sexp_a = reinterpret_cast<int8_t*>(pa + plane_data_bytes(mode, g.mb, g.kb, b));
+        sexp_b = reinterpret_cast<int8_t*>(pb + plane_data_bytes(mode, g.nb, g.kb, b));
+    }
+    auto split = [&](const tnc::Operand& src, int rb, const int64_t* rs, const int64_t* ks, void* dst, int8_t* sexp,
+                     int nz, int wsrc) {
+        tnc::SplitParams sp{};
+        sp.src = src;
+        sp.rb = rb;
+        sp.kb = g.kb;
+        for (int j = 0; j < rb; ++j) sp.rs[j] = rs[j];
+        for (int j = 0; j < g.kb; ++j) sp.ks[j] = ks[j];
+        sp.dst = dst;
+        sp.sexp = sexp;
+        const int64_t blocks = tnc::tc_split_prepare(sp);
+        if (blocks <= 0) return -2;
+        const int si = (int)W.split.size();
+        W.split.push_back(sp);
+        const int64_t per = (blocks + kSplitBlocksPerTask - 1) / kSplitBlocksPerTask;
+        const int c = W.new_counter((int)(per * nz));
+        for (int z = 0; z < nz; ++z)
+            for (int64_t q = 0; q < blocks; q += kSplitBlocksPerTask)
+                W.task(tnc::PT_SPLIT, si, q, z, netidx,
+                       (int)std::min<int64_t>(kSplitBlocksPerTask, blocks - q), wsrc, -1, -1, c);
+        return c;
+    };
+    const int ca = split(g.A, g.mb, g.am, g.ak, pa, sexp_a, a_shared ? 1 : b, wa);
+    const int cb = split(g.B, g.nb, g.bn, g.bk, pb, sexp_b, b_shared ? 1 : b, wb);
+    if (ca == -2 || cb == -2) return false;
+    tnc::TcGemmParams tp{};
+    tp.mb = g.mb;
+    tp.nb = g.nb;
+    tp.kb = g.kb;
+    tp.C = g.C;
+    tp.c_batch_stride = g.c_batch_stride;
+    tp.c_ld = 1ll << g.nb;
+    tp.err = net->d_err;
+    tp.row_bytes = 64;
+    tp.group_m = net->tc_group_m;
+    tp.spin_limit = net->tc_spin_limit;
+    tp.test_stall = net->tc_test_stall;
+    tp.sexp_a = sexp_a;
+    tp.sexp_b = sexp_b;
+    tp.ksplit_bits = cut.ks;
+    tp.partial = cut.ks ? reinterpret_cast<float2*>(pa + cut.partial_off) : nullptr;
+    tp.accumulate = 0;
+    tp.a_shared = a_shared ? 1 : 0;
+    tp.b_shared = b_shared ? 1 : 0;
+    tnc::TcNode nd{};
+    if (!tnc::tc_make_node(&nd, tp, mode, pa, pb, b)) return false;
+    const int ti = (int)W.tc.size();
+    W.tc.push_back(nd);
+    const int64_t tiles = tnc::tc_node_tiles(tp);
+    const int ct = W.new_counter((int)(tiles * b));
+    for (int z = 0; z < b; ++z)
+        for (int64_t t = 0; t < tiles; ++t) W.task(tnc::PT_TC, ti, t, z, netidx, 0, ca, cb, -1, ct);
+    if (!cut.ks) {
+        ctr[np.v] = ct;
+        return true;
+    }
+    tnc::KredParams kp{};
+    kp.partial = tp.partial;
+    kp.nsplit = 1 << cut.ks;
+    kp.batch = b;
+    kp.nb = g.nb;
+    kp.mn2 = (1ll << (g.mb + g.nb)) / 2;
+    kp.C = g.C;
+    kp.c_batch_stride = g.c_batch_stride;
+    kp.c_ld = 1ll << g.nb;
+    kp.accumulate = 0;
+    const int ki = (int)W.kred.size();
+    W.kred.push_back(kp);
+    const int64_t chunks = (kp.mn2 + 16383) / 16384;
+    const int ck = W.new_counter((int)(chunks * b));
+    for (int z = 0; z < b; ++z)
+        for (int64_t q = 0; q < chunks; ++q) W.task(tnc::PT_KRED, ki, q, z, netidx, 0, ct, -1, -1, ck);
+    ctr[np.v] = ck;
+    return true;
+}
+
+// Tasks of the final contraction of network netidx for batch b: FP64 chunk
+// sums then their ordered sum into out (at most 64 outputs), or an FP32 root
+// tensor then its FP64 slice sum.
+bool wl_root(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b, int netidx, double* out, WorkList& W,
+             std::map<int, int>& ctr) {
+    const Plan& P = net->plan;
+    const int wa = -1, wb = -1;  // the level chain waits for the inputs
+    tnc::GemmParams g = gemm_params(net, ar, ws, np, b);
+    tnc::PermParams pp{};
+    pp.obits = P.obits;
+    for (int j = 0; j < P.obits; ++j) pp.ostride[j] = P.out_stride[j];
+    W.cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * b;
+    if (np.kind == K_ROOT_F64) {
+        tnc::RootParams rp{};
+        rp.g = g;
+        rp.chunks = np.chunks;
+        const int ri = (int)W.root.size();
+        W.root.push_back(rp);
+        tnc::AccParams ap{};
+        ap.partials = reinterpret_cast<const double2*>(ws + ar.root_scratch_off);
+        ap.count = b * np.chunks;
+        ap.pp = pp;
+        ap.out = reinterpret_cast<double2*>(out);
+        const int ai = (int)W.acc.size();
+        W.acc.push_back(ap);
+        const int cr = W.new_counter(b * np.chunks);
+        for (int z = 0; z < b; ++z)
+            for (int c = 0; c < np.chunks; ++c) W.task(tnc::PT_ROOT, ri, c, z, netidx, ai, wa, wb, -1, cr);
+        const int cdone = W.new_counter(1);
+        W.task(tnc::PT_ACC, ai, 0, 0, netidx, 0, cr, -1, -1, cdone);
+        return true;
+    }
+    g.C = reinterpret_cast<float2*>(ws + ar.root_scratch_off);
+    g.c_batch_stride = tensor_bytes(P, np.v) / 8;
+    const int gi = (int)W.gemm.size();
+    W.gemm.push_back(g);
+    const int64_t tiles = tnc::gemm_f32_tiles(np.mb, np.nb);
+    const int cg = W.new_counter((int)(tiles * b));
+    for (int z = 0; z < b; ++z)
+        for (int64_t t = 0; t < tiles; ++t) W.task(tnc::PT_GEMM, gi, t, z, netidx, 0, wa, wb, -1, cg);
+    tnc::SumTaskParams st{};
+    st.sp.src.ptr = g.C;
+    st.sp.src.batch_stride = g.c_batch_stride;
+    st.sp.obits = P.obits;
+    for (int j = 0; j < P.obits; ++j) st.sp.ostride[j] = P.out_stride[j];
+    st.batch = b;
+    st.out = reinterpret_cast<double2*>(out);
+    const int si = (int)W.sum.size();
+    W.sum.push_back(st);
+    const int cdone = W.new_counter(1);
+    W.task(tnc::PT_SUM, si, 0, 0, netidx, 0, cg, -1, -1, cdone);
+    return true;
+}
+
+// Whether the persistent executor can run this network's contraction in
+// mode: at least one contraction, no fused stem groups in use.
+bool persist_eligible(tnc_net* net) {
+    return net->persistent && !net->plan.nodes.empty() && !(stem_fusion(net) && !net->plan.stems.empty()) &&
+           !net->tuning;
+}
+
+// Tasks of one network for a batch b: the slice-invariant levels (if with_inv),
+// the per-slice levels and the final contraction.
+bool wl_network(tnc_net* net, const Arena& ar, char* ws, int b, int mode, bool with_inv, int netidx, double* out,
+                WorkList& W) {
+    std::map<int, int> ctr;
+    const Plan& P = net->plan;
+    W.lvl_prev = W.lvl_cur = -1;
+    for (bool per : {false, true}) {
+        if (!per && !with_inv) continue;
+        for (const Group& g : level_groups(net, mode, per)) {
+            W.begin_level();
+            for (auto* list : {&g.fp32, &g.tc})
+                for (int v : *list)
+                    if (!wl_node(net, ar, ws, P.nodes[v - net->n_leaves], per ? b : 1, mode, netidx, W, ctr)) return false;
+        }
+    }
+    W.begin_level();
+    for (const NodePlan& np : P.nodes)
+        if (np.is_root && !wl_root(net, ar, ws, np, b, netidx, out, W, ctr)) return false;
+    return true;
+}
+
+tnc_status wl_upload(const WorkList& W, DeviceWorkList& D, int* err, uint64_t wait_ns, uint32_t spin,
+                     cudaStream_t s) {
+    size_t off = 0;
+    auto slot = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_tasks = slot(W.tasks.size() * sizeof(tnc::PersistTask));
+    const size_t o_init = slot(W.counters.size() * sizeof(int));
+    const size_t o_ctr = slot(W.counters.size() * sizeof(int) + sizeof(int));  // + ticket
+    const size_t o_gemm = slot(W.gemm.size() * sizeof(tnc::GemmParams));
+    const size_t o_split = slot(W.split.size() * sizeof(tnc::SplitParams));
+    const size_t o_tc = slot(W.tc.size() * sizeof(tnc::TcNode));
+    const size_t o_kred = slot(W.kred.size() * sizeof(tnc::KredParams));
+    const size_t o_root = slot(W.root.size() * sizeof(tnc::RootParams));
+    const size_t o_acc = slot(W.acc.size() * sizeof(tnc::AccParams));
+    const size_t o_sum = slot(W.sum.size() * sizeof(tnc::SumTaskParams));
+    CUDA_TRY(cudaMalloc(&D.mem, std::max<size_t>(off, 256)));
+    char* base = static_cast<char*>(D.mem);
+    auto up = [&](size_t o, const void* src, size_t bytes) -> cudaError_t {
+        return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    CUDA_TRY(up(o_tasks, W.tasks.data(), W.tasks.size() * sizeof(tnc::PersistTask)));
+    CUDA_TRY(up(o_init, W.counters.data(), W.counters.size() * sizeof(int)));
+    CUDA_TRY(up(o_gemm, W.gemm.data(), W.gemm.size() * sizeof(tnc::GemmParams)));
+    CUDA_TRY(up(o_split, W.split.data(), W.split.size() * sizeof(tnc::SplitParams)));
+    CUDA_TRY(up(o_tc, W.tc.data(), W.tc.size() * sizeof(tnc::TcNode)));
+    CUDA_TRY(up(o_kred, W.kred.data(), W.kred.size() * sizeof(tnc::KredParams)));
+    CUDA_TRY(up(o_root, W.root.data(), W.root.size() * sizeof(tnc::RootParams)));
+    CUDA_TRY(up(o_acc, W.acc.data(), W.acc.size() * sizeof(tnc::AccParams)));
+    CUDA_TRY(up(o_sum, W.sum.data(), W.sum.size() * sizeof(tnc::SumTaskParams)));
+    CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors may go
+    tnc::PersistParams& P = D.prm;
+    P = tnc::PersistParams{};
+    P.tasks = reinterpret_cast<const tnc::PersistTask*>(base + o_tasks);
+    P.ntasks = (int)W.tasks.size();
+    P.counters = reinterpret_cast<int*>(base + o_ctr);
+    P.ticket = P.counters + W.counters.size();
+    P.err = err;
+    P.gemm = reinterpret_cast<const tnc::GemmParams*>(base + o_gemm);
+    P.split = reinterpret_cast<const tnc::SplitParams*>(base + o_split);
+    P.tc = reinterpret_cast<const tnc::TcNode*>(base + o_tc);
+    P.kred = reinterpret_cast<const tnc::KredParams*>(base + o_kred);
+    P.root = reinterpret_cast<const tnc::RootParams*>(base + o_root);
+    P.acc = reinterpret_cast<const tnc::AccParams*>(base + o_acc);
+    P.sum = reinterpret_cast<const tnc::SumTaskParams*>(base + o_sum);
+    P.wait_ns = wait_ns;
+    P.spin_limit = spin;
+    D.init = reinterpret_cast<int*>(base + o_init);
+    D.n_counters = W.counters.size();
+    D.cmacs = W.cmacs;
+    D.tc_cmacs = W.tc_cmacs;
+    return TNC_OK;
+}
+
+// Reset the counters and the ticket, then launch (stream-ordered; capturable).
+cudaError_t wl_launch(const DeviceWorkList& D, int mode, int64_t slice0, const int64_t* rs0, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(D.prm.counters, D.init, D.n_counters * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.prm.ticket, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    tnc::PersistParams p = D.prm;
+    p.slice0 = slice0;
+    p.rs0 = rs0;
+    return tnc::launch_persist(p, mode, s);
+}
+
+// Host-side check of a work list before its first launch: every range a task
+// reads or writes (operands through their strides and slice offsets, outputs,
+// split planes and scales, K-split partials, final sums) lies inside the
+// workspace, the packed leaves or the result. A violation is a planning bug;
+// the call then fails instead of launching.
+bool wl_validate(const tnc_net* net, const WorkList& W, const char* ws, size_t ws_bytes, const double* out, int mode,
+                 std::string* why) {
+    const char* lv = reinterpret_cast<const char*>(net->d_leaves);
+    const size_t lv_bytes = (size_t)net->total_leaf_elems * 8;
+    const char* ob = reinterpret_cast<const char*>(out);
+    const size_t out_bytes = (size_t)16 << net->plan.obits;
+    auto inside = [&](const void* p, int64_t bytes, const char* what) {
+        const char* c = static_cast<const char*>(p);
+        const bool ok = bytes >= 0 && ((c >= ws && c + bytes <= ws + ws_bytes) || (c >= lv && c + bytes <= lv + lv_bytes) ||
+                                       (c >= ob && c + bytes <= ob + out_bytes));
+        if (!ok) *why = std::string("work list range outside its buffers: ") + what;
+        return ok;
+    };
+    auto sum_of = [](const int64_t* st, int n) {
+        int64_t t = 0;
+        for (int j = 0; j < n; ++j) t += st[j];
+        return t;
+    };
+    auto operand_ok = [&](const tnc::Operand& op, const int64_t* s1, int n1, const int64_t* s2, int n2, int nz,
+                          const char* what) {
+        int64_t hi = (int64_t)(nz - 1) * op.batch_stride + sum_of(s1, n1) + sum_of(s2, n2);
+        for (int j = 0; j < op.n_sl; ++j) hi += op.sl_stride[j];
+        return inside(op.ptr, (hi + 1) * 8, what);
+    };
+    std::map<std::pair<int, int>, int> nz;  // (type, idx) -> largest z + 1
+    for (const tnc::PersistTask& t : W.tasks) {
+        int& v = nz[{t.type, t.idx}];
+        v = std::max(v, t.z + 1);
+    }
+    const int64_t pe = (int64_t)tnc::tc_plane_count(mode) * tnc::tc_elem_bytes(mode);
+    for (size_t i = 0; i < W.gemm.size(); ++i) {
+        const tnc::GemmParams& g = W.gemm[i];
+        const int z = std::max(1, nz[{tnc::PT_GEMM, (int)i}]);
+        if (!operand_ok(g.A, g.am, g.mb, g.ak, g.kb, z, "FP32 tile operand A") ||
+            !operand_ok(g.B, g.bk, g.kb, g.bn, g.nb, z, "FP32 tile operand B") ||
+            !inside(g.C, ((int64_t)(z - 1) * g.c_batch_stride + (1ll << (g.mb + g.nb))) * 8, "FP32 tile output"))
+            return false;
+    }
+    for (size_t i = 0; i < W.split.size(); ++i) {
+        const tnc::SplitParams& sp = W.split[i];
+        const int z = std::max(1, nz[{tnc::PT_SPLIT, (int)i}]);
+        if (!operand_ok(sp.src, sp.rs, sp.rb, sp.ks, sp.kb, z, "split source") ||
+            !inside(sp.dst, (int64_t)z * pe << (sp.rb + sp.kb), "split planes") ||
+            (sp.sexp && !inside(sp.sexp, ((int64_t)z * tnc::tc_scale_chunks(sp.kb)) << sp.rb, "split scales")))
+            return false;
+    }
+    for (size_t i = 0; i < W.tc.size(); ++i) {
+        const tnc::TcGemmParams& tp = W.tc[i].p;
+        const int nb = W.tc[i].nbatch;
+        const int64_t M = 1ll << tp.mb, N = 1ll << tp.nb;
+        if (!inside(tp.C, ((int64_t)(nb - 1) * tp.c_batch_stride + (M - 1) * (tp.c_ld ? tp.c_ld : N) + N) * 8,
+                    "tensor-core output") ||
+            (tp.ksplit_bits && !inside(tp.partial, ((int64_t)nb << tp.ksplit_bits) * M * N * 8, "K-split partials")))
+            return false;
+    }
+    for (const tnc::KredParams& kp : W.kred)
+        if (!inside(kp.C, ((int64_t)(kp.batch - 1) * kp.c_batch_stride + 2 * kp.mn2) * 8, "K-split output") ||
+            !inside(kp.partial, (int64_t)kp.nsplit * kp.batch * kp.mn2 * 16, "K-split partial sums"))
+            return false;
+    for (size_t i = 0; i < W.root.size(); ++i) {
+        const tnc::GemmParams& g = W.root[i].g;
+        const int z = std::max(1, nz[{tnc::PT_ROOT, (int)i}]);
+        if (!operand_ok(g.A, g.am, g.mb, g.ak, g.kb, z, "final contraction operand A") ||
+            !operand_ok(g.B, g.bk, g.kb, g.bn, g.nb, z, "final contraction operand B"))
+            return false;
+    }
+    for (const tnc::AccParams& ap : W.acc)
+        if (!inside(ap.partials, (int64_t)ap.count * 16 << ap.pp.obits, "final chunk sums") ||
+            !inside(ap.out, (int64_t)16 << ap.pp.obits, "result"))
+            return false;
+    for (const tnc::SumTaskParams& st : W.sum)
+        if (!operand_ok(st.sp.src, st.sp.ostride, st.sp.obits, nullptr, 0, st.batch, "root tensor") ||
+            !inside(st.out, (int64_t)16 << st.sp.obits, "result"))
+            return false;
+    for (const tnc::PersistTask& t : W.tasks)
+        for (int c : {t.wait[0], t.wait[1], t.wait[2], t.signal, t.signal2})
+            if (c >= (int)W.counters.size()) {
+                *why = "work list counter out of range";
+                return false;
+            }
+    return true;
+}
+
+// The work list of one tnc_contract batch (b slices, invariants included or
+// not), built and uploaded on first use; null if the persistent executor
+// cannot run it.
+DeviceWorkList* contract_worklist(tnc_net* net, const Arena& ar, char* ws, int b, int mode, bool with_inv,
+                                  double* out, cudaStream_t s, tnc_status* st) {
+    *st = TNC_OK;
+    const std::string key = net->group_key + "|" + std::to_string(b) + ":" + std::to_string(with_inv ? 1 : 0) + ":" +
+                            std::to_string((uintptr_t)out) + ":" + std::to_string(net->tc_spin_limit) + ":" +
+                            std::to_string(net->tc_test_stall) + ":" + std::to_string(net->persist_test_stall) + ":" +
+                            std::to_string(net->persist_wait_ns) + ":" + std::to_string(net->tc_group_m);
+    auto it = net->worklists.find(key);
+    if (it != net->worklists.end()) return it->second.get();
+    WorkList W;
+    if (!wl_network(net, ar, ws, b, mode, with_inv, 0, out, W)) return nullptr;
+    if (net->persist_test_stall) {  // a task that waits on a counter no task decrements
+        const int never = W.new_counter(1);
+        const int c = W.new_counter(1);
+        W.tasks.insert(W.tasks.begin(), tnc::PersistTask{tnc::PT_STALL, 0, 0, 0, 0, 0, {never, -1, -1}, c, -1});
+    }
+    std::string why;
+    const size_t ws_bytes = net->ws_user ? net->ws_user_bytes : net->ws_own_bytes;
+    if (!wl_validate(net, W, ws, ws_bytes, out, mode, &why)) {
+        *st = fail(TNC_E_STATE, why);
+        return nullptr;
+    }
+    auto D = std::make_unique<DeviceWorkList>();
+    if ((*st = wl_upload(W, *D, net->d_err, net->persist_wait_ns, net->tc_spin_limit, s)) != TNC_OK) return nullptr;
+    if (net->worklists.size() > 16) net->worklists.clear();
+    DeviceWorkList* raw = D.get();
+    net->worklists[key] = std::move(D);
+    return raw;
+}
 
 // ------------------------------------------------------------ adjoint pass
 
@@ -1872,9 +2344,36 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     CUDA_TRY(cudaMemsetAsync(net->d_err, 0, sizeof(int), s));
 
     if ((st = ensure_groups(net, ar, ws, mode, nb, s)) != TNC_OK) return st;
+    const std::string ikey = net->group_key + "|" + std::to_string(net->leaf_version);
+    // persistent executor: one launch per batch of slices, the slice-invariant
+    // contractions in the first one (unless cached). Every batch's work list is
+    // prepared before the first launch, so a call that it cannot run falls back
+    // to the launches below as a whole.
+    if (persist_eligible(net)) {
+        const bool inv_cached = net->cache_invariants && net->inv_key == ikey;
+        std::vector<std::pair<DeviceWorkList*, int64_t>> rounds;
+        bool ok = true;
+        for (int64_t s0 = lo; s0 < hi && ok; s0 += nb) {
+            const int b = (int)std::min<int64_t>(nb, hi - s0);
+            DeviceWorkList* wl = contract_worklist(net, ar, ws, b, mode, s0 == lo && !inv_cached, out_c128, s, &st);
+            if (st != TNC_OK) return st;
+            if (!wl) ok = false;
+            else rounds.emplace_back(wl, s0);
+        }
+        if (ok) {
+            for (auto& [wl, s0] : rounds) {
+                const int b = (int)std::min<int64_t>(nb, hi - s0);
+                CUDA_TRY(timed_begin(net, -1, K_PERSIST, b, s, wl->cmacs));
+                if (net->timing) net->timed_persist_tc_cmacs += wl->tc_cmacs;
+                CUDA_TRY(wl_launch(*wl, mode, s0, nullptr, s));
+                CUDA_TRY(timed_end(net, s));
+            }
+            net->inv_key = net->cache_invariants ? ikey : std::string();
+            return TNC_OK;
+        }
+    }
     // invariant nodes once, one launch per level (or reused from an earlier
     // call when caching is on and nothing they depend on has changed)
-    const std::string ikey = net->group_key + "|" + std::to_string(net->leaf_version);
     if (!(net->cache_invariants && net->inv_key == ikey)) {
         for (const Group& g : net->groups.inv)
             if ((st = run_group(net, ar, ws, g, 1, 0, mode, s)) != TNC_OK) return st;
@@ -2046,6 +2545,14 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
         if (value < 16 || value > 40) return fail(TNC_E_INVALID, "tc_plane_cap_log2 must be in [16, 40]");
         net->plane_cap_log2 = (int)value;
         net->group_key.clear();
+    } else if (k == "persistent") {
+        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "persistent must be 0 or 1");
+        net->persistent = (int)value;
+    } else if (k == "persist_wait_ms") {
+        if (value < 0 || value > 600000) return fail(TNC_E_INVALID, "persist_wait_ms must be in [0, 600000]");
+        net->persist_wait_ns = (uint64_t)value * 1000000ull;
+    } else if (k == "persist_test_stall") {
+        net->persist_test_stall = value != 0;
     } else if (k == "stem_cap_log2") {
         if (value != 0 && (value < 2 || value > tnc::kStemMaxInner))
             return fail(TNC_E_INVALID, "stem_cap_log2 must be 0 or in [2, 14]");
@@ -2084,6 +2591,7 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable) {
     net->timing = enable != 0;
     net->timed.clear();
     net->launches = 0;
+    net->timed_persist_tc_cmacs = 0.0;
     return TNC_OK;
 }
 
@@ -2371,6 +2879,7 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
     } else {
         o << ",\"plan_error\":\"" << perr << "\"";
     }
+    o << ",\"persistent\":" << net->persistent << ",\"timed_persist_tc_cmacs\":" << net->timed_persist_tc_cmacs;
     o << "}";
     std::string s = o.str();
     if (s.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small: need " + std::to_string(s.size() + 1));

@@ -152,22 +152,27 @@ def test_invalid_range_and_mode(lib):
         net.contract(0, 1, mode=9)
 
 
-def test_cached_invariants(lib):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_cached_invariants(lib, persistent):
     """cache_invariants: the second call reuses the slice-invariant tensors
-    (fewer launches) with identical results; changing a leaf recomputes them."""
+    (fewer complex multiply-accumulates run) with identical results; changing
+    a leaf recomputes them. Both executors: one launch per contraction level,
+    and the persistent one."""
     c, ref_net, net, path, S = _setup(4, 5, 12, 7, 2, 16)
+    net.set_option("persistent", persistent)
     n = net.n_slices
     base = _gpu(net, 0, n)
     net.set_option("cache_invariants", 1)
     net.set_timing(True)
     a = _gpu(net, 0, n)
-    _, l1 = net.last_timings()
+    r1, l1 = net.last_timings()
     net.set_timing(True)
     b = _gpu(net, 0, n)
-    _, l2 = net.last_timings()
+    r2, l2 = net.last_timings()
     net.set_timing(False)
     assert np.array_equal(a, base) and np.array_equal(b, base)
-    assert l2 < l1
+    assert sum(r["cmacs"] for r in r2) < sum(r["cmacs"] for r in r1)
+    assert l2 <= l1
     # change a leaf that no sliced index touches: the cache must be refreshed
     tree = planner.Tree(ref_net.indices, ref_net.dims, ref_net.open_ids, path)
     i = next(v for v in range(ref_net.n_tensors)

@@ -169,26 +169,35 @@ def _scaled_pair(seed, mb, nb, kb, a_span, b_span, b_transposed):
     return TensorNetwork(tensors, idx, dims, (0, 3), [-1, -1, -1]), ea, eb
 
 
+@pytest.mark.parametrize("persistent", [0, 1])
 @pytest.mark.parametrize("mode", [4, 2, 1, 3])
 @pytest.mark.parametrize("mb,nb,kb,b_transposed", [(9, 8, 10, False), (8, 9, 11, True), (7, 7, 5, False)])
-def test_rows_and_columns_of_very_different_magnitude(lib, mode, mb, nb, kb, b_transposed):
+def test_rows_and_columns_of_very_different_magnitude(lib, mode, mb, nb, kb, b_transposed, persistent):
     """Rows of A spanning 2^-30 .. 1 and columns of B spanning 2^-20 .. 1.
     Every output C[m,n] is compared with the FP64 oracle relative to its own
     scale: both are multiplied back by 2^(ea[m] + eb[n]) (exact), then held to
     the mode's bound with the 0.1-rms floor. In split FP16x2 each row of A and
     column of B carries its own scale per 256-wide K chunk; a single scale per
-    operand would leave the small rows with a few significant bits."""
+    operand would leave the small rows with a few significant bits. Both
+    executors: one launch per tree level (k_cgemm_tc) and the persistent
+    work-list kernel (the same tile routine inside k_persist)."""
     from paper_2205_00393_gb300 import Network
     net_ref, ea, eb = _scaled_pair(500 + mb + nb + kb, mb, nb, kb, 30, 20, b_transposed)
     net = Network.from_tn(net_ref)
     path = [(0, 1), (2, 3)]
     net.set_path(path)
+    net.set_option("persistent", persistent)
     net.set_timing(True)
     got = net.contract(0, 1, mode).cpu().numpy()
     recs, _ = net.last_timings()
+    persist_tc = net.stats()["timed_persist_tc_cmacs"]
     net.set_timing(False)
     net.check_device()
-    assert 3 in {r["kind"] for r in recs}  # the A*B node ran on the tensor cores
+    # the A*B node ran on the tensor cores
+    if persistent:
+        assert {r["kind"] for r in recs} == {9} and persist_tc == 2.0 ** (mb + nb + kb)
+    else:
+        assert 3 in {r["kind"] for r in recs}
     ref = tn.contract(net_ref, path)
     unscale = np.ldexp(1.0, ea[:, None] + eb[None, :]).reshape(-1)
     err = floored_rel_err(got * unscale, ref * unscale, 0)
@@ -216,16 +225,19 @@ def _three_leaf_sliced(seed, mb, nb, kb):
                          [-1, -1, -1]), s_id
 
 
+@pytest.mark.parametrize("persistent", [0, 1])
 @pytest.mark.parametrize("mode", [4, 2])
 @pytest.mark.parametrize("mb,nb,kb,cap,sliced", [(7, 7, 16, 32, False), (8, 8, 14, 24, False), (8, 7, 16, 27, True)])
-def test_k_panels_and_k_splits(lib, mode, mb, nb, kb, cap, sliced):
+def test_k_panels_and_k_splits(lib, mode, mb, nb, kb, cap, sliced, persistent):
     """K-dominant contractions: with few output tiles K is split over CTAs
     (FP32 partials added in split order by k_ksplit_reduce, kind 7); with
     the plane cap lowered to 2^cap bytes the contraction runs in K panels
     whose launches add into C. (7, 7, 16): split K only; (8, 8, 14), cap 16
     MB: K panels only; (8, 7, 16), cap 128 MB, one sliced index (batch 2): K
     panels and K splits. Results match the oracle within the mode's
-    tolerance and the uncut contraction within 1e-6."""
+    tolerance and the uncut contraction within 1e-6. The persistent executor
+    runs the K splits as tile tasks plus reduction tasks (7, 7, 16); a call
+    with K panels falls back to one launch per level."""
     from paper_2205_00393_gb300 import Network
     path = [(0, 1), (2, 3)]
     if sliced:
@@ -235,6 +247,7 @@ def test_k_panels_and_k_splits(lib, mode, mb, nb, kb, cap, sliced):
         net_ref, S = _three_leaf(400 + mb + nb + kb, mb, nb, kb, False), []
     net = Network.from_tn(net_ref)
     net.set_path(path)
+    net.set_option("persistent", persistent)
     if S:
         net.set_slices(S)
     hi = 2 if S else 1
@@ -247,7 +260,9 @@ def test_k_panels_and_k_splits(lib, mode, mb, nb, kb, cap, sliced):
     net.check_device()
     kinds = [r["kind"] for r in recs]
     tc_launches = kinds.count(3)
-    if (mb, nb, kb) == (7, 7, 16):
+    if persistent and (mb, nb, kb) == (7, 7, 16):
+        assert kinds == [9], kinds
+    elif (mb, nb, kb) == (7, 7, 16):
         assert 7 in kinds and tc_launches == 1, kinds
     elif (mb, nb, kb) == (8, 8, 14):
         assert 7 not in kinds and tc_launches >= 2, kinds
