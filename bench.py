@@ -355,11 +355,13 @@ def single_node(args):
     return 0
 
 
-def batched_circuits(n=256, seed0=1000, t_cap=24, cost_cap=2 ** 32):
+def batched_circuits(n=256, seed0=1000, t_cap=24, cost_cap=None):
     """Plan the batched uneven workload (tnc_inputs.circuits.batched_workload):
-    target t = min(W - k, t_cap) for a greedy tree of width W. Circuits whose
+    target t = min(W - k, t_cap) for a greedy tree of width W (k sliced modes
+    where the greedy tree allows it, more where W - k > t_cap: no
+    intermediate above 2^t_cap elements). With cost_cap, circuits whose
     slices cost more than cost_cap complex MACs are left out (returned
-    separately)."""
+    separately); by default every circuit is kept."""
     from tnc_inputs import circuit_to_network
     from tnc_inputs.circuits import batched_workload
     from paper_2205_00393_gb300 import Network
@@ -367,23 +369,28 @@ def batched_circuits(n=256, seed0=1000, t_cap=24, cost_cap=2 ** 32):
     for i, (circ, k) in enumerate(batched_workload(n, seed0)):
         tn_ = circuit_to_network(circ).as_complex64()
         net = Network.from_tn(tn_)
-        net.set_path(net.greedy_path())
+        path = net.greedy_path()
+        net.set_path(path)
         W = net.stats()["max_log2_size"]
         n_open = len(circ.open_qubits)
         t = max(min(W - k, t_cap), n_open + 4)
-        net.set_slices(net.find_slices(t, 7))
+        S = net.find_slices(t, 7)
+        net.set_slices(S)
         st = net.stats()
         per_slice = int(st["eq3"]) >> len(net.sliced)
         entry = dict(index=i, qubits=circ.n_qubits, cycles=circ.cycles, n_open=n_open, t=t,
-                     slices=net.n_slices, per_slice_cmacs=per_slice, net=net, tn=tn_, circuit=circ)
-        (kept if per_slice <= cost_cap else dropped).append(entry)
+                     slices=net.n_slices, per_slice_cmacs=per_slice, net=net, tn=tn_, circuit=circ,
+                     path=[tuple(p) for p in path], S=list(S))
+        (kept if cost_cap is None or per_slice <= cost_cap else dropped).append(entry)
     return kept, dropped
 
 
 def many_bench(args):
     """Batched uneven workload: every kept circuit contributes its first
     --slices-per-step slices to each step. Times separate tnc_contract calls,
-    one tnc_contract_many launch sequence without a graph, and its graph replay."""
+    and tnc_contract_many with the persistent executor (one launch per round,
+    eager and graph replay) and with the merged per-level launches (graph
+    replay). The headline value is the faster graph replay."""
     import torch
     from paper_2205_00393_gb300 import contract_many
     torch.cuda.set_device(0)
@@ -395,6 +402,10 @@ def many_bench(args):
     n_sl = sum(hi - lo for lo, hi in ranges)
     stream = torch.cuda.Stream()
     res = {}
+    def executor(p):
+        for n in nets:
+            n.set_option("persistent", p)
+
     with torch.cuda.stream(stream):
         outs = [torch.empty(n.n_out, dtype=torch.complex128, device="cuda") for n in nets]
 
@@ -413,21 +424,67 @@ def many_bench(args):
         def separate():
             for net, (lo, hi), o in zip(nets, ranges, outs):
                 net.contract(lo, hi, mode, out=o, stream=stream)
-        res["separate"] = timed(separate)
-        res["many_no_graph"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs, use_graph=False,
-                                                           stream=stream))
-        res["many_graph"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs, use_graph=True,
-                                                        stream=stream))
-    T = res["many_graph"]
+        executor(0)
+        res["separate_per_level"] = timed(separate)
+        res["many_graph_per_level"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs, use_graph=True,
+                                                                  stream=stream))
+        executor(1)
+        res["separate_persistent"] = timed(separate)
+        res["many_no_graph_persistent"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs,
+                                                                      use_graph=False, stream=stream))
+        res["many_graph_persistent"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs, use_graph=True,
+                                                                   stream=stream))
+        # kernels per step of each graph replay, counted by the library on the first network
+        launches = {}
+        for p, key in ((1, "persistent"), (0, "per_level")):
+            executor(p)
+            nets[0].set_timing(True)
+            contract_many(nets, ranges, mode, outs=outs, use_graph=True, stream=stream)
+            stream.synchronize()
+            launches[key] = nets[0].last_timings()[1]
+            nets[0].set_timing(False)
+        executor(1)
+    best = min(("many_graph_persistent", "many_graph_per_level"), key=lambda k: res[k])
+    T = res[best]
     line = {"metric": "batched uneven circuits: effective complex TFLOPS & s/1024 slices (graph replay)",
             "value": 8 * cmacs / T / 1e12, "unit": UNIT, "s_per_1024_slices": T / n_sl * 1024,
-            "ms_per_step": {k: 1e3 * v for k, v in res.items()},
-            "speedup_vs_separate_calls": res["separate"] / T, "mode": args.mode, "steps": args.steps,
+            "executor": best, "ms_per_step": {k: 1e3 * v for k, v in res.items()},
+            "kernels_per_step": launches,
+            "speedup_vs_separate_calls": min(res["separate_per_level"], res["separate_persistent"]) / T,
+            "speedup_persistent_vs_per_level": res["many_graph_per_level"] / res["many_graph_persistent"],
+            "mode": args.mode, "steps": args.steps,
             "warmup": args.warmup,
             "config": {"workload": "256 seeded grid circuits (seeds 1000..1255), qubits 20-36, cycles 10-16, "
-                                   "open 0-6, slicing depth 4-12, target t <= 24",
-                       "circuits_run": len(kept), "circuits_left_out_over_2^32_cmacs_per_slice": len(dropped),
+                                   "open 0-6, slicing depth k 4-12, target t = min(W - k, 24) for greedy width W",
+                       "circuits_run": len(kept), "circuits_left_out": len(dropped),
+                       "n_slices_log2_range": [min(int(np.log2(e["slices"])) for e in kept),
+                                                       max(int(np.log2(e["slices"])) for e in kept)],
+                       "per_slice_cmacs_log2_range": [float(np.log2(min(e["per_slice_cmacs"] for e in kept))),
+                                                float(np.log2(max(e["per_slice_cmacs"] for e in kept)))],
                        "slices_per_step": n_sl, "slices_per_circuit_max": args.slices_per_step}}
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on the cheapest circuits' slices of a step (about 15 s
+        # of CPU work), compared with this step's results for those circuits
+        from oracle import tn as oracle_tn
+        got = {e["index"]: o.cpu().numpy() for e, o in zip(kept, outs)}
+        t_cpu, macs, worst, done = 0.0, 0, 0.0, 0
+        for e, (lo, hi) in sorted(zip(kept, ranges), key=lambda er: er[0]["per_slice_cmacs"]):
+            if t_cpu > 15.0:
+                break
+            t0 = time.perf_counter()
+            want = oracle_tn.contract(e["tn"], e["path"], e["S"], range(lo, hi))
+            t_cpu += time.perf_counter() - t0
+            macs += e["per_slice_cmacs"] * (hi - lo)
+            done += 1
+            g = got[e["index"]]
+            rms = float(np.sqrt(np.mean(np.abs(want) ** 2)))
+            floor = max(0.1 * rms, 1e-300)  # a circuit whose amplitudes all vanish compares absolutely
+            worst = max(worst, float(np.max(np.abs(g - want) / np.maximum(np.abs(want), floor))))
+        line["cpu_baseline"] = {"value": 8 * macs / t_cpu / 1e12, "unit": UNIT, "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": "the %d cheapest circuits' slices of one step (NumPy complex128 "
+                                          "tensordot per node), %.1f s" % (done, t_cpu)}
+        line["rel_err_vs_oracle_floor_0.1rms"] = {"circuits": done, "max": worst}
     print(json.dumps(line))
     return 0
 

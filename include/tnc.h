@@ -195,7 +195,13 @@ tnc_status tnc_check_device(tnc_net_t net, void* stream);
  * slice batches; tensor-core nodes keep their own launches. With use_graph
  * != 0 and a non-default stream, the launch sequence is captured once into a
  * CUDA graph and replayed by later calls with identical arguments (networks,
- * ranges, outputs, workspaces and plans; leaf data may change between calls).
+ * ranges, outputs, workspaces, plans and options; leaf data may change between
+ * calls). When every network has the "persistent" option on and the
+ * persistent executor can run each of them, every round of slice batches is
+ * instead ONE launch of the work-list kernel holding all networks' tasks,
+ * ordered by tree level (level L of every network before level L + 1 of any);
+ * each network waits only on its own levels. A dependency wait that runs out
+ * is then reported through the first network's tnc_check_device.
  * Every network needs at most 64 outputs and at least two tensors. A network
  * may appear once. Destroying a network drops the cached sequences using it. */
 tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_lo, const int64_t* slice_hi,

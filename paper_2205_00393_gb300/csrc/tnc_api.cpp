@@ -21,6 +21,7 @@
 #include <memory>
 #include <numeric>
 #include <set>
+#include <iomanip>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -113,6 +114,7 @@ struct Arena {
     std::vector<int64_t> planes_a, planes_b;  // per node (tensor-core split planes)
     int64_t root_scratch_off = -1; // FP64 partials or FP32 per-slice root
     int64_t peak = 0;
+    int64_t batch = 1;             // slices per batch the per-slice temporaries are sized for
 };
 
 // Level groups: nodes whose inputs are ready at the same time run in one
@@ -626,7 +628,17 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
         ar.root_scratch_off = alloc(bytes);
     }
     ar.peak = top;
+    ar.batch = nb;
     return ar;
+}
+
+// Batch whose cut (panels, K splits, plane and partial layout) a tensor-core
+// contraction of np uses when it runs b slices: the batch its workspace
+// temporaries were sized for. A smaller last batch keeps that cut, since its
+// own could need more bytes (fewer panels, or deeper K splits with more
+// partials) than the arena reserved.
+int64_t cut_batch(const Arena& ar, const NodePlan& np, int64_t b) {
+    return std::max<int64_t>(b, np.per_slice ? ar.batch : 1);
 }
 
 tnc::Operand operand(const tnc_net* net, const Arena& ar, char* ws, int v, int64_t nb) {
@@ -838,8 +850,11 @@ tnc_status ensure_groups(tnc_net* net, const Arena& ar, char* ws, int mode, int6
     std::string key = std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string((uintptr_t)ws) +
                       ":" + std::to_string(net->plan.version) + ":" + std::to_string(g_tune_version) + ":" +
                       std::to_string(net->force_choice) + ":" + std::to_string(net->tuning ? 1 : 0) + ":" +
-                      std::to_string(stem_fusion(net) ? net->stem_cap_log2 : 0);
+                      std::to_string(stem_fusion(net) ? net->stem_cap_log2 : 0) + ":" +
+                      std::to_string(net->plane_cap_log2);
     if (key == net->group_key) return TNC_OK;
+    // the persistent work lists address this arena: built again on next use
+    net->worklists.clear();
     GroupPlan G;
     G.inv = level_groups(net, mode, false);
     G.ps = level_groups(net, mode, true);
@@ -909,8 +924,8 @@ tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, in
 // per-bit strides, output), cut up as tc_cut() says; pa and pb are workspace
 // temporaries of tc_bytes_a() and tc_bytes_b() bytes.
 tnc_status launch_tc_contraction(tnc_net* net, const tnc::GemmParams& g, int b, int mode, void* pa, void* pb,
-                                 int node, cudaStream_t s, int row_bytes) {
-    const TcCut cut = tc_cut(net, mode, g.mb, g.nb, g.kb, b);
+                                 int node, cudaStream_t s, int row_bytes, int64_t cut_b) {
+    const TcCut cut = tc_cut(net, mode, g.mb, g.nb, g.kb, std::max<int64_t>(cut_b, b));
     const int pA = cut.pA, pB = cut.pB, pK = cut.pK;
     const int mbp = g.mb - pA, nbp = g.nb - pB, kbp = g.kb - pK;
     const int64_t N = 1ll << g.nb;
@@ -1009,7 +1024,8 @@ tnc_status launch_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& 
         return TNC_OK;
     }
     const size_t i = np.v - net->n_leaves;
-    return launch_tc_contraction(net, g, b, mode, ws + ar.planes_a[i], ws + ar.planes_b[i], np.v, s, choice);
+    return launch_tc_contraction(net, g, b, mode, ws + ar.planes_a[i], ws + ar.planes_b[i], np.v, s, choice,
+                                 cut_batch(ar, np, b));
 }
 
 tnc_status run_group(tnc_net* net, const Arena& ar, char* ws, const Group& g, int b, int64_t slice0, int mode,
@@ -1066,8 +1082,11 @@ struct WorkList {
         return (int)counters.size() - 1;
     }
     // tree-level chain of the network being emitted: tasks wait on the
-    // previous level's counter and also count down the current level's
-    int lvl_prev = -1, lvl_cur = -1;
+    // previous level's counter and also count down the current level's;
+    // level[i] is task i's level number within its network
+    int lvl_prev = -1, lvl_cur = -1, lvl_no = -1;
+    std::vector<int> level;
+    bool no_slot = false;  // a task had no wait slot left for the level chain
     void task(int type, int idx, int64_t item, int z, int net, int count, int w0, int w1, int w2, int signal) {
         tnc::PersistTask t{};
         t.type = type;
@@ -1091,11 +1110,14 @@ struct WorkList {
                     t.wait[q] = lvl_prev;
                     have = true;
                 }
+            no_slot |= !have;
         }
         if (lvl_cur >= 0) ++counters[lvl_cur];
         tasks.push_back(t);
+        level.push_back(lvl_no);
     }
     void begin_level() {
+        ++lvl_no;
         lvl_prev = lvl_cur;
         lvl_cur = new_counter(0);
     }
@@ -1127,7 +1149,7 @@ bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
         ctr[np.v] = c;
         return true;
     }
-    const TcCut cut = tc_cut(net, mode, g.mb, g.nb, g.kb, b);
+    const TcCut cut = tc_cut(net, mode, g.mb, g.nb, g.kb, cut_batch(ar, np, b));
     if (cut.pA || cut.pB || cut.pK) return false;
     W.tc_cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * b;
     const size_t i = np.v - net->n_leaves;
@@ -1284,7 +1306,7 @@ bool wl_network(tnc_net* net, const Arena& ar, char* ws, int b, int mode, bool w
                 WorkList& W) {
     std::map<int, int> ctr;
     const Plan& P = net->plan;
-    W.lvl_prev = W.lvl_cur = -1;
+    W.lvl_prev = W.lvl_cur = W.lvl_no = -1;
     for (bool per : {false, true}) {
         if (!per && !with_inv) continue;
         for (const Group& g : level_groups(net, mode, per)) {
@@ -1297,7 +1319,66 @@ bool wl_network(tnc_net* net, const Arena& ar, char* ws, int b, int mode, bool w
     W.begin_level();
     for (const NodePlan& np : P.nodes)
         if (np.is_root && !wl_root(net, ar, ws, np, b, netidx, out, W, ctr)) return false;
-    return true;
+    return !W.no_slot;
+}
+
+// Appends the work list Wi (one network's tasks, its own tables and
+// counters) to W: table indices and counter ids move by W's sizes so far.
+void wl_append(WorkList& W, const WorkList& Wi) {
+    const int o_gemm = (int)W.gemm.size(), o_split = (int)W.split.size(), o_tc = (int)W.tc.size(),
+              o_kred = (int)W.kred.size(), o_root = (int)W.root.size(), o_acc = (int)W.acc.size(),
+              o_sum = (int)W.sum.size(), o_ctr = (int)W.counters.size();
+    for (size_t i = 0; i < Wi.tasks.size(); ++i) {
+        tnc::PersistTask t = Wi.tasks[i];
+        switch (t.type) {
+            case tnc::PT_GEMM: t.idx += o_gemm; break;
+            case tnc::PT_SPLIT: t.idx += o_split; break;
+            case tnc::PT_TC: t.idx += o_tc; break;
+            case tnc::PT_KRED: t.idx += o_kred; break;
+            case tnc::PT_ROOT:
+                t.idx += o_root;
+                t.count += o_acc;  // the AccParams entry its chunk sums go to
+                break;
+            case tnc::PT_ACC: t.idx += o_acc; break;
+            case tnc::PT_SUM: t.idx += o_sum; break;
+            default: break;
+        }
+        for (int& c : t.wait)
+            if (c >= 0) c += o_ctr;
+        t.signal += o_ctr;
+        if (t.signal2 >= 0) t.signal2 += o_ctr;
+        W.tasks.push_back(t);
+        W.level.push_back(Wi.level[i]);
+    }
+    W.counters.insert(W.counters.end(), Wi.counters.begin(), Wi.counters.end());
+    W.gemm.insert(W.gemm.end(), Wi.gemm.begin(), Wi.gemm.end());
+    W.split.insert(W.split.end(), Wi.split.begin(), Wi.split.end());
+    W.tc.insert(W.tc.end(), Wi.tc.begin(), Wi.tc.end());
+    W.kred.insert(W.kred.end(), Wi.kred.begin(), Wi.kred.end());
+    W.root.insert(W.root.end(), Wi.root.begin(), Wi.root.end());
+    W.acc.insert(W.acc.end(), Wi.acc.begin(), Wi.acc.end());
+    W.sum.insert(W.sum.end(), Wi.sum.begin(), Wi.sum.end());
+    W.cmacs += Wi.cmacs;
+    W.tc_cmacs += Wi.tc_cmacs;
+}
+
+// Orders the tasks of several networks by their level within their network
+// (stable, so each network keeps its own order): the CTAs take level L of
+// every network before level L + 1 of any. Every wait still names tasks
+// earlier in the list, since a network's tasks only wait on its own earlier
+// ones.
+void wl_interleave_levels(WorkList& W) {
+    std::vector<size_t> ord(W.tasks.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return W.level[a] < W.level[b]; });
+    std::vector<tnc::PersistTask> t(ord.size());
+    std::vector<int> l(ord.size());
+    for (size_t i = 0; i < ord.size(); ++i) {
+        t[i] = W.tasks[ord[i]];
+        l[i] = W.level[ord[i]];
+    }
+    W.tasks.swap(t);
+    W.level.swap(l);
 }
 
 tnc_status wl_upload(const WorkList& W, DeviceWorkList& D, int* err, uint64_t wait_ns, uint32_t spin,
@@ -1610,7 +1691,7 @@ tnc_status env_child(Backward& bw, const NodePlan& np, int c, int64_t b, int64_t
     if (tc) {
         // split precision with FP32 accumulation, as in the forward
         tnc_status st =
-            launch_tc_contraction(net, g, (int)b, bw.mode, bw.ws + pa, bw.ws + pb, np.v, bw.s, env_choice);
+            launch_tc_contraction(net, g, (int)b, bw.mode, bw.ws + pa, bw.ws + pb, np.v, bw.s, env_choice, b);
         bw.A.release(pa);
         bw.A.release(pb);
         return st;
@@ -1876,6 +1957,9 @@ struct ManyCall {
     int64_t* d_blk_off = nullptr;
     tnc::PermParams* d_perms = nullptr;
     double2** d_outs = nullptr;
+    // persistent executor: one work list (one launch) per round, empty when
+    // the call runs on the merged level launches
+    std::vector<std::unique_ptr<DeviceWorkList>> wls;
     cudaGraphExec_t graph = nullptr;
     bool warmed = false;
     int64_t kernels = 0;
@@ -1909,6 +1993,13 @@ tnc_status many_run(ManyCall& mc, cudaStream_t s) {
         CUDA_TRY(cudaMemsetAsync(mc.nets[i]->d_err, 0, sizeof(int), s));
     }
     mc.kernels = 0;
+    if (!mc.wls.empty()) {
+        for (size_t r = 0; r < mc.wls.size(); ++r) {
+            CUDA_TRY(wl_launch(*mc.wls[r], mc.mode, 0, mc.d_rs0 + (int64_t)r * n, s));
+            mc.kernels += 1;
+        }
+        return TNC_OK;
+    }
     auto run_groups = [&](const std::vector<ManyCall::MGroup>& groups, const int64_t* rs0, const int* rb,
                           const int64_t* h_rs0, const int* h_rb, bool per_slice) -> tnc_status {
         for (const auto& g : groups) {
@@ -2109,6 +2200,38 @@ tnc_status many_build(ManyCall& mc, cudaStream_t s) {
     CUDA_TRY(up(mc.d_perms, perms.data(), perms.size() * sizeof(tnc::PermParams)));
     CUDA_TRY(up(mc.d_outs, outs.data(), outs.size() * sizeof(double2*)));
     CUDA_TRY(cudaStreamSynchronize(s));
+    // persistent executor (when every network has it on): per round one work
+    // list with every network's tasks, levels interleaved; slice ids per
+    // network come from the round's row of the device table d_rs0. A network
+    // it cannot run keeps the whole call on the merged level launches.
+    bool pers = true;
+    for (tnc_net* net : mc.nets) pers &= net->persistent != 0;
+    for (int r = 0; r < R && pers; ++r) {
+        WorkList W;
+        for (int i = 0; i < n && pers; ++i) {
+            const int b = mc.h_rb[(size_t)r * n + i];
+            if (b < 1) continue;
+            tnc_net* net = mc.nets[i];
+            WorkList Wi;
+            if (!wl_network(net, mc.arenas[i], mc.wss[i], b, mc.mode, r == 0, i, mc.outs[i], Wi)) {
+                pers = false;
+                break;
+            }
+            std::string why;
+            const size_t ws_bytes = net->ws_user ? net->ws_user_bytes : net->ws_own_bytes;
+            if (!wl_validate(net, Wi, mc.wss[i], ws_bytes, mc.outs[i], mc.mode, &why))
+                return fail(TNC_E_STATE, "network " + std::to_string(i) + ": " + why);
+            wl_append(W, Wi);
+        }
+        if (!pers) break;
+        wl_interleave_levels(W);
+        auto D = std::make_unique<DeviceWorkList>();
+        if ((st = wl_upload(W, *D, mc.nets[0]->d_err, mc.nets[0]->persist_wait_ns, mc.nets[0]->tc_spin_limit, s)) !=
+            TNC_OK)
+            return st;
+        mc.wls.push_back(std::move(D));
+    }
+    if (!pers) mc.wls.clear();
     return TNC_OK;
 }
 
@@ -2751,7 +2874,10 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
         for (int j = 0; j < i; ++j)
             if (nets[j] == net) return fail(TNC_E_INVALID, "a network appears twice");
         key << "|" << net->uid << ":" << net->plan.version << ":" << slice_lo[i] << ":" << slice_hi[i] << ":"
-            << (uintptr_t)outs_c128[i] << ":" << (uintptr_t)net->ws_user << ":" << net->ws_user_bytes;
+            << (uintptr_t)outs_c128[i] << ":" << (uintptr_t)net->ws_user << ":" << net->ws_user_bytes << ":"
+            << net->persistent << ":" << net->persist_wait_ns << ":" << net->plane_cap_log2 << ":" << g_tune_version
+            << ":" << net->force_choice << ":" << net->tc_group_m << ":" << net->tc_spin_limit << ":"
+            << net->tc_row_bytes;
     }
     tnc_status st;
     // device copies of leaf data must be current before a cached sequence replays
@@ -2759,6 +2885,18 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
         if ((st = ensure_leaves(nets[i], s)) != TNC_OK) return st;
     auto& cache = many_cache();
     auto it = cache.find(key.str());
+    if (it != cache.end()) {
+        // a network's own workspace may have been reallocated by a later call
+        // of its own: the cached sequence addresses the old one
+        for (int i = 0; i < n && it != cache.end(); ++i) {
+            const tnc_net* net = nets[i];
+            const char* cur = static_cast<const char*>(net->ws_user ? net->ws_user : net->ws_own);
+            if (cur != it->second->wss[i]) {
+                cache.erase(it);
+                it = cache.end();
+            }
+        }
+    }
     ManyCall* mc = nullptr;
     if (it == cache.end()) {
         if (cache.size() >= 8) cache.clear();
@@ -2782,7 +2920,13 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
     // driver entry points) never happens inside a capture
     if (!graph || !mc->warmed) {
         mc->warmed = true;
-        return many_run(*mc, s);
+        // the call's kernels are counted on the first network, as for a replay
+        std::vector<int64_t> before(n);
+        for (int i = 0; i < n; ++i) before[i] = nets[i]->launches;
+        st = many_run(*mc, s);
+        for (int i = 0; i < n; ++i) nets[i]->launches = before[i];
+        nets[0]->launches += mc->kernels;
+        return st;
     }
     if (!mc->graph) {
         cudaGraph_t g = nullptr;
@@ -2879,7 +3023,8 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
     } else {
         o << ",\"plan_error\":\"" << perr << "\"";
     }
-    o << ",\"persistent\":" << net->persistent << ",\"timed_persist_tc_cmacs\":" << net->timed_persist_tc_cmacs;
+    o << ",\"persistent\":" << net->persistent << ",\"timed_persist_tc_cmacs\":" << std::setprecision(17)
+      << net->timed_persist_tc_cmacs;
     o << "}";
     std::string s = o.str();
     if (s.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small: need " + std::to_string(s.size() + 1));

@@ -1,6 +1,8 @@
 """tnc_contract_many: several circuits of uneven size in shared launches and
 a replayed CUDA graph must give the same amplitudes as separate contractions
-and as the FP64 oracle."""
+and as the FP64 oracle. Both executors: merged per-level launches, and the
+persistent work-list kernel (one launch per round of slice batches, every
+circuit's tasks in it, levels interleaved)."""
 
 import numpy as np
 import pytest
@@ -31,13 +33,27 @@ def _circuits():
     return out
 
 
-@pytest.mark.parametrize("mode", [0, 2])
-def test_many_matches_single_and_oracle(libtnc, mode):
+def _launches_of_replay(nets, ranges, mode, outs, stream):
+    """Kernels one graph replay of the call launches (counted on nets[0])."""
+    from paper_2205_00393_gb300 import contract_many
+    nets[0].set_timing(True)
+    contract_many(nets, ranges, mode, outs=outs, stream=stream)
+    stream.synchronize()
+    _, n = nets[0].last_timings()
+    nets[0].set_timing(False)
+    return n
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("mode", [0, 2, 4])
+def test_many_matches_single_and_oracle(libtnc, mode, persistent):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2205_00393_gb300 import contract_many
     cs = _circuits()
     nets = [c[2] for c in cs]
+    for n in nets:
+        n.set_option("persistent", persistent)
     ranges = [(0, n.n_slices) for n in nets]
     ranges[3] = (1, nets[3].n_slices - 1)  # a partial range
     stream = torch.cuda.Stream()
@@ -55,7 +71,13 @@ def test_many_matches_single_and_oracle(libtnc, mode):
                 assert np.allclose(got, single, rtol=1e-9, atol=1e-15), call
                 if call == 0:
                     want = tn.contract(ref, path, S, range(lo, hi))
-                    assert floored_rel_err(got, want, circ.n_qubits) <= 1e-5
+                    assert floored_rel_err(got, want, circ.n_qubits) <= (1e-5 if mode == 0 else 1e-4)
+        launches = _launches_of_replay(nets, ranges, mode, outs, stream)
+        for n in nets:
+            n.set_option("persistent", 1 - persistent)
+        other = _launches_of_replay(nets, ranges, mode, outs, stream)
+    # the persistent executor launches one kernel per round of slice batches
+    assert (launches < other) if persistent else (launches > other)
 
 
 def test_many_rejects_duplicates(libtnc):
@@ -67,11 +89,13 @@ def test_many_rejects_duplicates(libtnc):
         contract_many([cs[0][2], cs[0][2]])
 
 
+@pytest.mark.parametrize("persistent", [0, 1])
 @pytest.mark.parametrize("mode", [0, 2])
-def test_batched_uneven_workload_subset(libtnc, mode):
+def test_batched_uneven_workload_subset(libtnc, mode, persistent):
     """First 48 circuits of the seeded batched workload (those whose slices
-    cost at most 2^32 complex MACs), two slices each: the merged launches with
-    graph replay equal separate contractions."""
+    cost at most 2^32 complex MACs), two slices each: the merged launches
+    (or the persistent kernel) with graph replay equal separate
+    contractions."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import os
@@ -79,9 +103,11 @@ def test_batched_uneven_workload_subset(libtnc, mode):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from bench import batched_circuits
     from paper_2205_00393_gb300 import contract_many
-    kept, dropped = batched_circuits(n=48)
+    kept, dropped = batched_circuits(n=48, cost_cap=2 ** 32)
     assert len(kept) >= 20
     nets = [e["net"] for e in kept]
+    for n in nets:
+        n.set_option("persistent", persistent)
     ranges = [(0, min(2, e["slices"])) for e in kept]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
