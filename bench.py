@@ -310,6 +310,20 @@ def apply_options(net, args):
         net.set_option("persistent", args.persistent)
 
 
+PERSIST_TASK_NAMES = ["fp32_tile", "split_blocks", "tc_tile", "ksplit_reduce", "root_chunk", "root_acc",
+                      "root_sum", "stall"]
+
+
+def persist_profile_of(prof):
+    """Per task type of the persistent kernel: CTA-milliseconds in tasks (sum
+    over CTAs), task count, CTA-milliseconds in dependency waits, and share of
+    the task time."""
+    tot = sum(r[0] for r in prof) or 1
+    return {PERSIST_TASK_NAMES[t]: {"cta_ms": r[0] / 1e6, "tasks": r[1], "wait_cta_ms": r[2] / 1e6,
+                                    "share": r[0] / tot}
+            for t, r in enumerate(prof) if r[1]}
+
+
 def executor_of(by_kind):
     return "persistent (k_persist, one launch per slice batch)" if 9 in by_kind else "one launch per tree level"
 
@@ -426,6 +440,16 @@ def many_bench(args):
                 net.contract(lo, hi, mode, out=o, stream=stream)
         executor(0)
         res["separate_per_level"] = timed(separate)
+        # kernel time by kernel of one round of per-level separate calls
+        for n in nets:
+            n.set_timing(True)
+        separate()
+        stream.synchronize()
+        per_level_kernels = {}
+        for n in nets:
+            for k, v in kernel_breakdown(n.last_timings()[0]).items():
+                per_level_kernels[KIND_NAMES.get(k, str(k))] = per_level_kernels.get(KIND_NAMES.get(k, str(k)), 0.0) + v["ms"]
+            n.set_timing(False)
         res["many_graph_per_level"] = timed(lambda: contract_many(nets, ranges, mode, outs=outs, use_graph=True,
                                                                   stream=stream))
         executor(1)
@@ -444,12 +468,37 @@ def many_bench(args):
             launches[key] = nets[0].last_timings()[1]
             nets[0].set_timing(False)
         executor(1)
+        # where the persistent kernel's CTA time goes (one profiled call)
+        nets[0].set_option("persist_profile", 1)
+        contract_many(nets, ranges, mode, outs=outs, use_graph=True, stream=stream)
+        stream.synchronize()
+        nets[0].set_timing(True)
+        contract_many(nets, ranges, mode, outs=outs, use_graph=True, stream=stream)
+        stream.synchronize()
+        prof = persist_profile_of(nets[0].stats()["persist_profile"])
+        nets[0].set_timing(False)
+        nets[0].set_option("persist_profile", 0)
+        # the launch-bound end of the mix: circuits whose slices cost at most
+        # 2^26 complex MACs, both executors, graph replay
+        small = [i for i, e in enumerate(kept) if e["per_slice_cmacs"] <= 2 ** 26]
+        s_nets = [nets[i] for i in small]
+        s_ranges = [ranges[i] for i in small]
+        s_outs = [outs[i] for i in small]
+        subset = {"circuits": len(small),
+                  "cmacs_per_step": float(sum(kept[i]["per_slice_cmacs"] * (ranges[i][1] - ranges[i][0])
+                                              for i in small))}
+        for p, key in ((0, "per_level"), (1, "persistent")):
+            executor(p)
+            subset["ms_" + key] = 1e3 * timed(lambda: contract_many(s_nets, s_ranges, mode, outs=s_outs,
+                                                                    use_graph=True, stream=stream))
+        subset["speedup_persistent_vs_per_level"] = subset["ms_per_level"] / subset["ms_persistent"]
     best = min(("many_graph_persistent", "many_graph_per_level"), key=lambda k: res[k])
     T = res[best]
     line = {"metric": "batched uneven circuits: effective complex TFLOPS & s/1024 slices (graph replay)",
             "value": 8 * cmacs / T / 1e12, "unit": UNIT, "s_per_1024_slices": T / n_sl * 1024,
             "executor": best, "ms_per_step": {k: 1e3 * v for k, v in res.items()},
-            "kernels_per_step": launches,
+            "kernels_per_step": launches, "persistent_task_profile": prof,
+            "per_level_separate_kernel_ms": per_level_kernels, "launch_bound_subset": subset,
             "speedup_vs_separate_calls": min(res["separate_per_level"], res["separate_persistent"]) / T,
             "speedup_persistent_vs_per_level": res["many_graph_per_level"] / res["many_graph_persistent"],
             "mode": args.mode, "steps": args.steps,

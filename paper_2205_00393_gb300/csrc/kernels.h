@@ -269,7 +269,12 @@ struct PersistParams {
     int64_t slice0;
     uint64_t wait_ns;       // bound of one dependency wait (0: 10 s)
     uint32_t spin_limit;    // bound of one tensor-core pipeline wait (0: default)
+    // optional profile (null: off): per task type t, prof[3t] global-timer ns
+    // from the end of its dependency waits to the end of the task, summed over
+    // CTAs, prof[3t + 1] tasks, prof[3t + 2] ns spent in its dependency waits
+    unsigned long long* prof;
 };
+constexpr int kPersistProfWords = 3 * 8;
 
 // Launch the persistent executor for mode (FP32 or a split mode) over p's
 // work list; ticket and counters must hold 0 and the initial counts.

@@ -524,80 +524,162 @@ __device__ __forceinline__ void tc_bar() {
 }
 
 // planes: out[((z * PLANES + q) * R + r) * K + k], q = t * PARTS + part (t = 0 Re, 1 Im);
-// FP16x2 scale exponents: sexp[(z * (K / SK) + chunk) * R + r]. One split tile
-// (block) of batch entry z (slice id slice0 + z), run by threads 0-255; BAR as
-// in the FP32 routines (0: whole CTA, 1: named barrier over 256 threads).
-template <int KIND, int BAR>
-__device__ __forceinline__ void split_block(const SplitParams& p, int64_t block, int z, int64_t slice0, float2* tile,
-                                            int64_t* roff, int64_t* koff) {
-    using C_ = Cfg<KIND, 64>;
-    const int64_t R = 1ll << p.rb, K = 1ll << p.kb;
-    const bool kfast = p.kb > 0 && p.ks[0] == 1;
-    const int SK = split_tile_k(p.kb);
-    const int SR = split_tile_rows(p.kb, kfast);
-    const int LD = split_ld(SK);
-    const int64_t tiles_k = K / SK;
-    const int64_t r0 = (block / tiles_k) * SR, k0 = (block % tiles_k) * SK;
-    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, slice0 + z);
+// FP16x2 scale exponents: sexp[(z * (K / SK) + chunk) * R + r]. Split tiles
+// (blocks) block0 .. block0 + count - 1 of batch entry z (slice id slice0 +
+// z), run by threads 0-255; BAR as in the FP32 routines (0: whole CTA, 1:
+// named barrier over 256 threads). Each block is gathered (phase 1) into
+// registers, staged in a shared-memory tile (phase 2) and converted into the
+// part planes (phase 3). With count > 1 the blocks are software-pipelined:
+// block i + 1's gather loads are in flight while block i is converted, so
+// tile[] and the offset tables roff[], koff[] are double-buffered (tile[j]:
+// split_tile_floats() float2 each; roff[j]: 128, koff[j]: 256 entries).
+__host__ __device__ inline int split_tile_floats(int kb, bool kfast) {
+    return split_tile_rows(kb, kfast) * split_ld(split_tile_k(kb));
+}
+
+struct SplitGeom {
+    int64_t R, K, tiles_k;
+    int SK, SR, LD, n;
+    bool kfast;
+};
+
+__device__ __forceinline__ SplitGeom split_geom(const SplitParams& p) {
+    SplitGeom g;
+    g.R = 1ll << p.rb;
+    g.K = 1ll << p.kb;
+    g.kfast = p.kb > 0 && p.ks[0] == 1;
+    g.SK = split_tile_k(p.kb);
+    g.SR = split_tile_rows(p.kb, g.kfast);
+    g.LD = split_ld(g.SK);
+    g.tiles_k = g.K / g.SK;
+    g.n = g.SR * g.SK;  // 2048 (k fastest) or 4096 elements
+    return g;
+}
+
+// phase 0: the block's row and k offsets through the per-bit stride tables
+__device__ __forceinline__ void split_offsets(const SplitParams& p, const SplitGeom& g, int64_t block, int64_t* roff,
+                                              int64_t* koff) {
+    const int64_t r0 = (block / g.tiles_k) * g.SR, k0 = (block % g.tiles_k) * g.SK;
     const int tid = threadIdx.x;
-    if (tid < SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
-    if (tid < SK) koff[tid] = bits_offset(k0 + tid, p.ks, p.kb, 0);
-    tc_bar<BAR>();
-    const int n = SR * SK;
+    if (tid < g.SR) roff[tid] = bits_offset(r0 + tid, p.rs, p.rb, 0);
+    if (tid < g.SK) koff[tid] = bits_offset(k0 + tid, p.ks, p.kb, 0);
+}
+
+// phase 1: this thread's n / 256 elements of the block, all loads in flight
+// (pairs adjacent along the unit-stride mode as one 16-byte load when p.vec2)
+__device__ __forceinline__ void split_gather(const SplitParams& p, const SplitGeom& g, const float2* src,
+                                             const int64_t* roff, const int64_t* koff, float4 (&v)[8]) {
+    const int tid = threadIdx.x;
     if (p.vec2) {
-        // pairs of elements adjacent along the unit-stride mode arrive as one
-        // 16-byte load; all of a thread's loads are in flight before any store
-        if (kfast) {  // 1024 pairs (rr, kk..kk+1)
-            float4 v[4];
+        if (g.kfast) {  // 1024 pairs (rr, kk..kk+1)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int pi = tid + 256 * i, kk = 2 * (pi % (SK / 2)), rr = pi / (SK / 2);
+                const int pi = tid + 256 * i, kk = 2 * (pi % (g.SK / 2)), rr = pi / (g.SK / 2);
                 v[i] = *reinterpret_cast<const float4*>(src + roff[rr] + koff[kk]);
             }
+        } else {  // 2048 pairs (rr..rr+1, kk)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int pi = tid + 256 * i, rr = 2 * (pi % (g.SR / 2)), kk = pi / (g.SR / 2);
+                v[i] = *reinterpret_cast<const float4*>(src + roff[rr] + koff[kk]);
+            }
+        }
+    } else {  // element e = tid + 256 i; two per float4
+        const int ne = g.n / 256;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i >= ne) break;
+            const int e = tid + 256 * i;
+            const int rr = g.kfast ? e / g.SK : e % g.SR, kk = g.kfast ? e % g.SK : e / g.SR;
+            const float2 x = src[roff[rr] + koff[kk]];
+            if (i & 1) { v[i >> 1].z = x.x; v[i >> 1].w = x.y; }
+            else { v[i >> 1].x = x.x; v[i >> 1].y = x.y; }
+        }
+    }
+}
+
+// phase 2: the gathered elements into the staging tile (row rr, k kk at
+// rr * LD + kk + kk / 8)
+__device__ __forceinline__ void split_stage(const SplitParams& p, const SplitGeom& g, const float4 (&v)[8],
+                                            float2* tile) {
+    const int tid = threadIdx.x, LD = g.LD;
+    if (p.vec2) {
+        if (g.kfast) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int pi = tid + 256 * i, kk = 2 * (pi % (SK / 2)), rr = pi / (SK / 2);
+                const int pi = tid + 256 * i, kk = 2 * (pi % (g.SK / 2)), rr = pi / (g.SK / 2);
                 float2* d = tile + rr * LD + kk + (kk >> 3);
                 d[0] = make_float2(v[i].x, v[i].y);
                 d[1] = make_float2(v[i].z, v[i].w);
             }
-        } else {      // 2048 pairs (rr..rr+1, kk)
-            float4 v[8];
+        } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int pi = tid + 256 * i, rr = 2 * (pi % (SR / 2)), kk = pi / (SR / 2);
-                v[i] = *reinterpret_cast<const float4*>(src + roff[rr] + koff[kk]);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int pi = tid + 256 * i, rr = 2 * (pi % (SR / 2)), kk = pi / (SR / 2);
+                const int pi = tid + 256 * i, rr = 2 * (pi % (g.SR / 2)), kk = pi / (g.SR / 2);
                 float2* d = tile + rr * LD + kk + (kk >> 3);
                 d[0] = make_float2(v[i].x, v[i].y);
                 d[LD] = make_float2(v[i].z, v[i].w);
             }
         }
     } else {
-        for (int e0 = 0; e0 < n; e0 += 8 * 256) {
-            float2 v[8];
+        const int ne = g.n / 256;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int e = e0 + tid + 256 * i;
-                int rr, kk;
-                if (kfast) { kk = e % SK; rr = e / SK; }
-                else { rr = e % SR; kk = e / SR; }
-                v[i] = src[roff[rr] + koff[kk]];
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int e = e0 + tid + 256 * i;
-                int rr, kk;
-                if (kfast) { kk = e % SK; rr = e / SK; }
-                else { rr = e % SR; kk = e / SR; }
-                tile[rr * LD + kk + (kk >> 3)] = v[i];
-            }
+        for (int i = 0; i < 16; ++i) {
+            if (i >= ne) break;
+            const int e = tid + 256 * i;
+            const int rr = g.kfast ? e / g.SK : e % g.SR, kk = g.kfast ? e % g.SK : e / g.SR;
+            tile[rr * LD + kk + (kk >> 3)] = (i & 1) ? make_float2(v[i >> 1].z, v[i >> 1].w)
+                                                     : make_float2(v[i >> 1].x, v[i >> 1].y);
         }
     }
-    tc_bar<BAR>();
+}
+
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// phases 1 and 2 as asynchronous copies: every element of the block goes from
+// global memory straight into its staging-tile slot (8-byte cp.async, no
+// registers held), one commit group per block
+__device__ __forceinline__ void split_gather_async(const SplitParams& p, const SplitGeom& g, const float2* src,
+                                                   const int64_t* roff, const int64_t* koff, float2* tile) {
+    const int tid = threadIdx.x, LD = g.LD;
+    const int ne = g.n / 256;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i >= ne) break;
+        // the element mapping of the pair loads: adjacent lanes take adjacent
+        // pairs along the unit-stride mode (coalesced sectors)
+        int rr, kk;
+        if (p.vec2) {
+            const int pi = tid + 256 * (i >> 1);
+            if (g.kfast) {
+                kk = 2 * (pi % (g.SK / 2)) + (i & 1);
+                rr = pi / (g.SK / 2);
+            } else {
+                rr = 2 * (pi % (g.SR / 2)) + (i & 1);
+                kk = pi / (g.SR / 2);
+            }
+        } else {
+            const int e = tid + 256 * i;
+            rr = g.kfast ? e / g.SK : e % g.SR;
+            kk = g.kfast ? e % g.SK : e / g.SR;
+        }
+        cp_async8(tile + rr * LD + kk + (kk >> 3), src + roff[rr] + koff[kk]);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// phase 3: the staged tile of block `block` into the part planes (and, in
+// FP16x2, the row chunks' scale exponents)
+template <int KIND>
+__device__ __forceinline__ void split_convert(const SplitParams& p, const SplitGeom& g, int64_t block, int z,
+                                              const float2* tile) {
+    using C_ = Cfg<KIND, 64>;
+    const int64_t R = g.R, K = g.K, tiles_k = g.tiles_k;
+    const int SK = g.SK, LD = g.LD, n = g.n;
+    const int64_t r0 = (block / tiles_k) * g.SR, k0 = (block % tiles_k) * SK;
+    const int tid = threadIdx.x;
     constexpr int Q = C_::PLANES;
     const int64_t plane = R * K;
     uint8_t* out = reinterpret_cast<uint8_t*>(p.dst) + (int64_t)z * Q * plane * C_::ELEM;
@@ -666,14 +748,52 @@ __device__ __forceinline__ void split_block(const SplitParams& p, int64_t block,
             }
         }
     }
-    tc_bar<BAR>();  // the tile buffer may be refilled after this
+}
+
+// One block through registers (the standalone split kernel: many CTAs per
+// SM keep the memory system busy).
+template <int KIND, int BAR>
+__device__ __forceinline__ void split_one_block(const SplitParams& p, int64_t block, int z, int64_t slice0,
+                                                float2* tile, int64_t* roff, int64_t* koff) {
+    const SplitGeom g = split_geom(p);
+    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, slice0 + z);
+    float4 v[8];
+    split_offsets(p, g, block, roff, koff);
+    tc_bar<BAR>();
+    split_gather(p, g, src, roff, koff, v);
+    split_stage(p, g, v, tile);
+    tc_bar<BAR>();
+    split_convert<KIND>(p, g, block, z, tile);
+    tc_bar<BAR>();  // the tile may be refilled after this
+}
+
+// count consecutive blocks, software-pipelined (one CTA per SM runs them):
+// block i + 1's asynchronous copies are in flight while block i is converted.
+template <int KIND, int BAR>
+__device__ __forceinline__ void split_blocks(const SplitParams& p, int64_t block0, int count, int z, int64_t slice0,
+                                             float2* const (&tile)[2], int64_t* const (&roff)[2],
+                                             int64_t* const (&koff)[2]) {
+    const SplitGeom g = split_geom(p);
+    const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, slice0 + z);
+    split_offsets(p, g, block0, roff[0], koff[0]);
+    tc_bar<BAR>();
+    split_gather_async(p, g, src, roff[0], koff[0], tile[0]);
+    for (int i = 0; i < count; ++i) {
+        const int j = i & 1;
+        if (i + 1 < count) split_offsets(p, g, block0 + i + 1, roff[j ^ 1], koff[j ^ 1]);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        tc_bar<BAR>();  // tile[j] and the next block's offsets complete
+        if (i + 1 < count) split_gather_async(p, g, src, roff[j ^ 1], koff[j ^ 1], tile[j ^ 1]);
+        split_convert<KIND>(p, g, block0 + i, z, tile[j]);
+    }
+    tc_bar<BAR>();  // the tiles may be refilled after this
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(256) k_split_operand(const __grid_constant__ SplitParams p) {
     extern __shared__ float2 tile[];
     __shared__ int64_t roff[128], koff[256];
-    split_block<KIND, 0>(p, blockIdx.x, blockIdx.z, p.slice0, tile, roff, koff);
+    split_one_block<KIND, 0>(p, blockIdx.x, blockIdx.z, p.slice0, tile, roff, koff);
 }
 
 // ------------------------------------------------------------ K-split reduction
@@ -803,12 +923,14 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
     const int tid = threadIdx.x, warp = tid >> 5;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     // scratch of the task types, all at the start of the dynamic shared memory:
-    // the split tile at 0 and its offset tables after the largest tile
-    constexpr int kSplitOffBytes = 40 * 1024;
-    static_assert(kSplitTileBytesMax <= kSplitOffBytes && kSplitOffBytes + (128 + 256) * 8 <= SMEM_PIPE,
+    // the split's two staging tiles, then its two pairs of offset tables
+    constexpr int kSplitTileSlot = 40 * 1024;
+    static_assert(kSplitTileBytesMax <= kSplitTileSlot && 2 * kSplitTileSlot + 2 * (128 + 256) * 8 <= SMEM_PIPE,
                   "split scratch fits the ring");
-    int64_t* split_roff = reinterpret_cast<int64_t*>(smem + kSplitOffBytes);
-    int64_t* split_koff = split_roff + 128;
+    float2* const split_tile[2] = {reinterpret_cast<float2*>(smem), reinterpret_cast<float2*>(smem + kSplitTileSlot)};
+    int64_t* const split_roff[2] = {reinterpret_cast<int64_t*>(smem + 2 * kSplitTileSlot),
+                                    reinterpret_cast<int64_t*>(smem + 2 * kSplitTileSlot) + 384};
+    int64_t* const split_koff[2] = {split_roff[0] + 128, split_roff[1] + 128};
     double2* root_red = reinterpret_cast<double2*>(smem);
     int64_t(*root_ta)[256] = reinterpret_cast<int64_t(*)[256]>(smem + 4096);
     int64_t(*root_tb)[256] = reinterpret_cast<int64_t(*)[256]>(smem + 4096 + 5 * 256 * 8);
@@ -832,12 +954,14 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
     const uint32_t tmem = TC ? sh.tmem_base : 0u;
     const uint64_t wait_ns = P.wait_ns ? P.wait_ns : 10000000000ull;
     TcPipe pipe;
+    uint64_t t_wait0 = 0, t_run0 = 0;  // thread 0, for the optional profile
     for (;;) {
         if (tid == 0) {
             int t = atomicAdd(P.ticket, 1);
             if (t < P.ntasks) {
                 const PersistTask& tk = P.tasks[t];
                 const uint64_t t0 = global_ns();
+                t_wait0 = t0;
                 for (int w = 0; w < 3 && t >= 0; ++w) {
                     const int c = tk.wait[w];
                     if (c < 0) continue;
@@ -854,6 +978,7 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
                         __nanosleep(256);
                     }
                 }
+                t_run0 = global_ns();
             }
             task_sh = t;
         }
@@ -872,9 +997,8 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
             case PT_SPLIT:
                 if constexpr (TC) {
                     if (tid < 256) {
-                        for (int b = 0; b < tk.count; ++b)
-                            split_block<KIND, 1>(P.split[tk.idx], tk.item + b, tk.z, slice0,
-                                                 reinterpret_cast<float2*>(smem), split_roff, split_koff);
+                        split_blocks<KIND, 1>(P.split[tk.idx], tk.item, tk.count, tk.z, slice0, split_tile,
+                                              split_roff, split_koff);
                         asm volatile("fence.proxy.async.global;" ::: "memory");
                     }
                 }
@@ -963,6 +1087,12 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
             if (sh.abort) atomicExch(P.err, kErrTimeout);
             atomicSub(P.counters + tk.signal, 1);
             if (tk.signal2 >= 0) atomicSub(P.counters + tk.signal2, 1);
+            if (P.prof && tk.type >= 0 && tk.type < 8) {
+                const uint64_t t1 = global_ns();
+                atomicAdd(P.prof + 3 * tk.type, (unsigned long long)(t1 - t_run0));
+                atomicAdd(P.prof + 3 * tk.type + 1, 1ull);
+                atomicAdd(P.prof + 3 * tk.type + 2, (unsigned long long)(t_run0 - t_wait0));
+            }
         }
         if (sh.abort) break;
     }

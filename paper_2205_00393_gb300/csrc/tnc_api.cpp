@@ -231,6 +231,7 @@ struct tnc_net {
     int persist_test_stall = 0;      // tests only: one task waits on a counter nothing signals
     std::map<std::string, std::unique_ptr<DeviceWorkList>> worklists;
     double timed_persist_tc_cmacs = 0.0;  // tensor-core share of the timed persistent launches
+    unsigned long long* d_prof = nullptr;  // "persist_profile": per task type time, count, wait
 
     ~tnc_net() {
         if (d_leaves) cudaFree(d_leaves);
@@ -240,6 +241,7 @@ struct tnc_net {
         if (d_pg) cudaFree(d_pg);
         if (d_stem) cudaFree(d_stem);
         if (ws_own) cudaFree(ws_own);
+        if (d_prof) cudaFree(d_prof);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
 };
@@ -1438,13 +1440,15 @@ tnc_status wl_upload(const WorkList& W, DeviceWorkList& D, int* err, uint64_t wa
 }
 
 // Reset the counters and the ticket, then launch (stream-ordered; capturable).
-cudaError_t wl_launch(const DeviceWorkList& D, int mode, int64_t slice0, const int64_t* rs0, cudaStream_t s) {
+cudaError_t wl_launch(const DeviceWorkList& D, int mode, int64_t slice0, const int64_t* rs0, cudaStream_t s,
+                      unsigned long long* prof) {
     cudaError_t e = cudaMemcpyAsync(D.prm.counters, D.init, D.n_counters * sizeof(int), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.prm.ticket, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     tnc::PersistParams p = D.prm;
     p.slice0 = slice0;
     p.rs0 = rs0;
+    p.prof = prof;
     return tnc::launch_persist(p, mode, s);
 }
 
@@ -1995,7 +1999,7 @@ tnc_status many_run(ManyCall& mc, cudaStream_t s) {
     mc.kernels = 0;
     if (!mc.wls.empty()) {
         for (size_t r = 0; r < mc.wls.size(); ++r) {
-            CUDA_TRY(wl_launch(*mc.wls[r], mc.mode, 0, mc.d_rs0 + (int64_t)r * n, s));
+            CUDA_TRY(wl_launch(*mc.wls[r], mc.mode, 0, mc.d_rs0 + (int64_t)r * n, s, mc.nets[0]->d_prof));
             mc.kernels += 1;
         }
         return TNC_OK;
@@ -2488,7 +2492,7 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
                 const int b = (int)std::min<int64_t>(nb, hi - s0);
                 CUDA_TRY(timed_begin(net, -1, K_PERSIST, b, s, wl->cmacs));
                 if (net->timing) net->timed_persist_tc_cmacs += wl->tc_cmacs;
-                CUDA_TRY(wl_launch(*wl, mode, s0, nullptr, s));
+                CUDA_TRY(wl_launch(*wl, mode, s0, nullptr, s, net->d_prof));
                 CUDA_TRY(timed_end(net, s));
             }
             net->inv_key = net->cache_invariants ? ikey : std::string();
@@ -2674,6 +2678,16 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "persist_wait_ms") {
         if (value < 0 || value > 600000) return fail(TNC_E_INVALID, "persist_wait_ms must be in [0, 600000]");
         net->persist_wait_ns = (uint64_t)value * 1000000ull;
+    } else if (k == "persist_profile") {
+        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "persist_profile must be 0 or 1");
+        if (value && !net->d_prof) {
+            CUDA_TRY(cudaMalloc(&net->d_prof, tnc::kPersistProfWords * sizeof(unsigned long long)));
+            CUDA_TRY(cudaMemset(net->d_prof, 0, tnc::kPersistProfWords * sizeof(unsigned long long)));
+        } else if (!value && net->d_prof) {
+            CUDA_TRY(cudaDeviceSynchronize());
+            CUDA_TRY(cudaFree(net->d_prof));
+            net->d_prof = nullptr;
+        }
     } else if (k == "persist_test_stall") {
         net->persist_test_stall = value != 0;
     } else if (k == "stem_cap_log2") {
@@ -2715,6 +2729,10 @@ tnc_status tnc_set_timing(tnc_net_t net, int enable) {
     net->timed.clear();
     net->launches = 0;
     net->timed_persist_tc_cmacs = 0.0;
+    if (net->d_prof) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(cudaMemset(net->d_prof, 0, tnc::kPersistProfWords * sizeof(unsigned long long)));
+    }
     return TNC_OK;
 }
 
@@ -2877,7 +2895,7 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
             << (uintptr_t)outs_c128[i] << ":" << (uintptr_t)net->ws_user << ":" << net->ws_user_bytes << ":"
             << net->persistent << ":" << net->persist_wait_ns << ":" << net->plane_cap_log2 << ":" << g_tune_version
             << ":" << net->force_choice << ":" << net->tc_group_m << ":" << net->tc_spin_limit << ":"
-            << net->tc_row_bytes;
+            << net->tc_row_bytes << ":" << (uintptr_t)net->d_prof;
     }
     tnc_status st;
     // device copies of leaf data must be current before a cached sequence replays
@@ -3025,6 +3043,16 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
     }
     o << ",\"persistent\":" << net->persistent << ",\"timed_persist_tc_cmacs\":" << std::setprecision(17)
       << net->timed_persist_tc_cmacs;
+    if (net->d_prof) {  // [run ns, tasks, wait ns] per task type since tnc_set_timing
+        unsigned long long h[tnc::kPersistProfWords];
+        if (cudaDeviceSynchronize() == cudaSuccess &&
+            cudaMemcpy(h, net->d_prof, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            o << ",\"persist_profile\":[";
+            for (int t = 0; t < tnc::kPersistProfWords / 3; ++t)
+                o << (t ? "," : "") << "[" << h[3 * t] << "," << h[3 * t + 1] << "," << h[3 * t + 2] << "]";
+            o << "]";
+        }
+    }
     o << "}";
     std::string s = o.str();
     if (s.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small: need " + std::to_string(s.size() + 1));
