@@ -1364,15 +1364,35 @@ void wl_append(WorkList& W, const WorkList& Wi) {
     W.tc_cmacs += Wi.tc_cmacs;
 }
 
-// Orders the tasks of several networks by their level within their network
-// (stable, so each network keeps its own order): the CTAs take level L of
-// every network before level L + 1 of any. Every wait still names tasks
-// earlier in the list, since a network's tasks only wait on its own earlier
-// ones.
+// Phase of a task type within its level: operand splits and root chunks
+// first, then FP32 tiles (which wait on nothing of their level), then the
+// tensor-core tiles (waiting on the splits), then reductions of tiles or
+// chunks. A task only waits on tasks of an earlier phase of its level or on
+// the level before.
+int wl_phase(int type) {
+    switch (type) {
+        case tnc::PT_SPLIT:
+        case tnc::PT_ROOT: return 0;
+        case tnc::PT_GEMM: return 1;
+        case tnc::PT_TC: return 2;
+        case tnc::PT_KRED: return 3;
+        default: return 4;
+    }
+}
+
+// Orders the tasks (of one or several networks) by their level within their
+// network, then by phase (stable, so each network keeps its own order
+// otherwise): the CTAs take level L of every network before level L + 1 of
+// any, and every split of a level well before the tiles that wait on it.
+// Every wait still names tasks earlier in the list, since a task only waits
+// on its own network's earlier levels and earlier phases of its level.
 void wl_interleave_levels(WorkList& W) {
     std::vector<size_t> ord(W.tasks.size());
     for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
-    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return W.level[a] < W.level[b]; });
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+        if (W.level[a] != W.level[b]) return W.level[a] < W.level[b];
+        return wl_phase(W.tasks[a].type) < wl_phase(W.tasks[b].type);
+    });
     std::vector<tnc::PersistTask> t(ord.size());
     std::vector<int> l(ord.size());
     for (size_t i = 0; i < ord.size(); ++i) {
@@ -1554,6 +1574,7 @@ DeviceWorkList* contract_worklist(tnc_net* net, const Arena& ar, char* ws, int b
     if (it != net->worklists.end()) return it->second.get();
     WorkList W;
     if (!wl_network(net, ar, ws, b, mode, with_inv, 0, out, W)) return nullptr;
+    wl_interleave_levels(W);
     if (net->persist_test_stall) {  // a task that waits on a counter no task decrements
         const int never = W.new_counter(1);
         const int c = W.new_counter(1);
