@@ -538,6 +538,94 @@ def many_bench(args):
     return 0
 
 
+def bitstrings_bench(args):
+    """Correlated amplitudes (Sec. 1 and 6.2): B closed bitstrings of the
+    30-qubit circuit (64 open amplitudes each). Path "stem" (default): the
+    time-ordered stem path, whose projection vectors come last, unsliced (the
+    2^30-element state before the projections is shared by every bitstring);
+    path "greedy": the greedy path sliced to 2^27 elements, every bitstring
+    over the first --slices-per-step slices. Times one tnc_contract_variants
+    call over the B bitstrings (the shared part computed once) against
+    ordinary contractions of single bitstrings (each recomputing it; timed on
+    min(B, 4) bitstrings and scaled to B)."""
+    import torch
+    from tnc_inputs import bitstring_variants, random_bitstrings, stem_path
+    from paper_2205_00393_gb300 import Network
+    torch.cuda.set_device(0)
+    B = args.bitstrings
+    c, ref_net = build_network()
+    net = Network.from_tn(ref_net)
+    if args.bitstring_path == "stem":
+        net.set_path(stem_path(ref_net, c))
+        S = []
+        ns = 1
+    else:
+        net.set_path(net.greedy_path())
+        S = net.find_slices(WORKLOAD["target_log2"], WORKLOAD["sa_seed"])
+        ns = args.slices_per_step
+    net.set_slices(S)
+    mode = MODES[args.mode]
+    bits = random_bitstrings(c, B, 11)
+    leaves, data = bitstring_variants(c, bits)
+    net.set_leaf_variants(leaves, data)
+    sbits = len(S)
+    stream = torch.cuda.current_stream()
+    out = torch.empty((B, net.n_out), dtype=torch.complex128, device="cuda")
+    if mode != 0 and not args.no_autotune:
+        net.autotune(mode, 0)
+
+    def shared():
+        net.contract_variants(0, B, 0, ns, mode, out=out)
+
+    n_un = min(B, 4)
+
+    def unshared():
+        for v in range(n_un):
+            net.contract((v << sbits), (v << sbits) + ns, mode, out=out[v])
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / args.steps
+
+    net.set_option("cache_invariants", 0)
+    t_shared = timed(shared)
+    t_unshared = timed(unshared) * B / n_un
+    # work of one call: shared part once plus every bitstring's own part
+    net.set_timing(True)
+    shared()
+    torch.cuda.synchronize()
+    c_shared = sum(r["cmacs"] for r in net.last_timings()[0])
+    net.set_timing(True)
+    net.contract(0, ns, mode, out=out[0])
+    torch.cuda.synchronize()
+    c_one = sum(r["cmacs"] for r in net.last_timings()[0])
+    net.set_timing(False)
+    line = {"metric": "correlated amplitudes of B bitstrings: effective complex TFLOPS (every bitstring's full "
+                      "contraction counted)",
+            "value": 8 * B * c_one / t_shared / 1e12, "unit": UNIT, "bitstrings": B,
+            "bitstring_slices_per_s": B * ns / t_shared,
+            "ms_per_call_shared": 1e3 * t_shared, "ms_per_call_unshared": 1e3 * t_unshared,
+            "speedup_shared_vs_unshared": t_unshared / t_shared,
+            "cmacs_per_call_shared": c_shared, "cmacs_per_bitstring_unshared": c_one,
+            "shared_fraction_of_one_bitstring": 1.0 - (c_shared - c_one) / ((B - 1) * c_one) if B > 1 else None,
+            "unshared_timed_on_bitstrings": n_un,
+            "mode": args.mode, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "rqc-5x6-14cyc-seed2-open6, %s path%s" % (
+                           args.bitstring_path, "" if S else ", unsliced"),
+                       "slices_per_bitstring": ns, "n_slices": net.n_slices, "sliced": len(S),
+                       "bitstring_seed": 11, "open_amplitudes_per_bitstring": net.n_out}}
+    print(json.dumps(line))
+    return 0
+
+
 def c53_bench(args):
     """53-qubit lattice (6x9 grid minus one site), 20 cycles (seed 3), one
     amplitude, sliced to 2^30-element intermediates: a fixed subset of slices
@@ -833,6 +921,10 @@ def main():
                     help="42-qubit gradient configuration (adjoint vs finite differences) instead")
     ap.add_argument("--many", action="store_true",
                     help="time the batched uneven workload of many circuits instead")
+    ap.add_argument("--bitstrings", type=int, default=0,
+                    help="time B correlated bitstrings of the 30-qubit workload (leaf variants) instead")
+    ap.add_argument("--bitstring-path", default="stem", choices=["stem", "greedy"],
+                    help="--bitstrings: contraction path (stem: projections last, unsliced)")
     ap.add_argument("--stem", action="store_true",
                     help="time fused stem groups against separate launches on a 28-qubit stem path instead")
     ap.add_argument("--stem-grid", default="4x7", help="--stem: grid of the circuit (ROWSxCOLS)")
@@ -866,6 +958,8 @@ def main():
         return backward_bench(args)
     if args.stem:
         return stem_bench(args)
+    if args.bitstrings:
+        return bitstrings_bench(args)
     if args.many:
         return many_bench(args)
     if args.grad42:

@@ -86,6 +86,35 @@ tnc_status tnc_create_network(int n_tensors, const int* ranks,
  * the next contraction. */
 tnc_status tnc_set_tensor_data(tnc_net_t net, int tensor, const float* data_c64);
 
+/* Leaf variants: batches of correlated amplitudes (Sec. 1 and Sec. 6.2, the
+ * "1M correlated samples" workload), e.g. B closed bitstrings of one circuit.
+ * The n leaves leaf_ids[i] (the projection vectors of the closed qubits) take
+ * n_variants data copies each: data_c64[i] points to n_variants x (the leaf's
+ * elements) interleaved complex64 values in host memory, copy v first-index
+ * major, copied at once. Copy v of every listed leaf forms variant v; the
+ * other leaves are common to all variants. Variant v's slice s has slice id
+ * v * 2^|S| + s, so tnc_contract over [v 2^|S| + lo, v 2^|S| + hi) contracts
+ * variant v, and every subtree without a variant leaf (and without a sliced
+ * index) is slice-invariant: computed once and shared by all variants. Up to
+ * 2^24 variants; |S| plus ceil(log2 n_variants) must stay within 62 bits and
+ * a leaf's sliced modes plus variant bits within 16. n = 0 removes the
+ * variants. The adjoint pass (tnc_contract_backward) takes no variants
+ * (TNC_E_STATE). Errors: TNC_E_INVALID for a bad leaf, repeated leaf, NULL
+ * data or count. */
+tnc_status tnc_set_leaf_variants(tnc_net_t net, int n, const int* leaf_ids, int64_t n_variants,
+                                 const float* const* data_c64);
+
+/* Contract variants [v_lo, v_hi) (of tnc_set_leaf_variants), each over its
+ * slices [lo, hi) of [0, 2^|S|), into out_c128 (device): (v_hi - v_lo) blocks
+ * of 2^(open qubits) complex128 values, variant v_lo first, each overwritten.
+ * The slice-invariant tensors are computed by the first variant and reused
+ * by the others (unless "cache_invariants" is on and they are still valid
+ * from an earlier call, every call computes them once; the option itself is
+ * left as it was). Errors: TNC_E_STATE without variants; TNC_E_INVALID for a range out
+ * of bounds; the errors of tnc_contract. */
+tnc_status tnc_contract_variants(tnc_net_t net, int64_t v_lo, int64_t v_hi, int64_t lo, int64_t hi, int mode,
+                                 double* out_c128, void* stream);
+
 /* Bytes of all leaves packed back to back in leaf order (complex64). */
 tnc_status tnc_leaf_bytes(tnc_net_t net, size_t* bytes);
 
@@ -146,9 +175,11 @@ tnc_status tnc_set_workspace(tnc_net_t net, void* dev_ptr, size_t bytes);
  * allReduce becomes an on-device FP64 reduction in a fixed order).
  *  out_c128  device pointer, 2 * 2^(sum of log2 dims of open indices) doubles,
  *            overwritten with the result in open_ids order.
+ * With leaf variants (tnc_set_leaf_variants) the slice ids run over
+ * [0, 2^(|S| + ceil(log2 n_variants))): variant v's slices start at v 2^|S|.
  * Errors: TNC_E_STATE before tnc_set_path; TNC_E_INVALID if the range is not
- * within [0, 2^min(|S|, 62)] or mode is unknown; TNC_E_CUDA / TNC_E_OOM from
- * the device. */
+ * within [0, 2^min(|S| + variant bits, 62)] or mode is unknown; TNC_E_CUDA /
+ * TNC_E_OOM from the device. */
 tnc_status tnc_contract(tnc_net_t net, int64_t slice_lo, int64_t slice_hi, int mode,
                         double* out_c128, void* stream);
 
@@ -290,7 +321,7 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value);
  * flip the choice. The choice is recorded per (mode, log2 M, log2 N, log2 K)
  * in a table shared by all networks of the process (results are the same up
  * to rounding either way). Later contractions of any network follow the
- * table. */
+ * table. A plan without a tensor-core-eligible contraction returns at once. */
 tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream);
 
 /* The tuning table as JSON: [[mode, log2 M, log2 N, log2 K, choice], ...]

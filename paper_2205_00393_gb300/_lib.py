@@ -47,6 +47,10 @@ def load_library():
         "tnc_create_network": [ctypes.c_int, P(ctypes.c_int), P(c_i64p), ctypes.c_int64, c_i64p,
                                P(P(ctypes.c_float)), ctypes.c_int, c_i64p, P(ctypes.c_void_p)],
         "tnc_set_tensor_data": [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_float)],
+        "tnc_set_leaf_variants": [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
+                                  P(P(ctypes.c_float))],
+        "tnc_contract_variants": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
         "tnc_leaf_bytes": [ctypes.c_void_p, P(ctypes.c_size_t)],
         "tnc_upload_leaves": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
         "tnc_greedy_path": [ctypes.c_void_p, P(ctypes.c_int)],
@@ -248,6 +252,34 @@ class Network:
             out = torch.empty(self.n_out, dtype=torch.complex128, device="cuda")
         st = self._lib.tnc_contract(self._h, int(lo), int(hi), int(mode), ctypes.c_void_p(out.data_ptr()),
                                     _stream_ptr(stream))
+        _check(self._lib, st)
+        return out
+
+    def set_leaf_variants(self, leaf_ids, data):
+        """Leaf variants (tnc_set_leaf_variants): data[i] is an array of shape
+        (n_variants, *leaf_shape) for leaf leaf_ids[i]; [] removes them."""
+        n = len(leaf_ids)
+        if n == 0:
+            _check(self._lib, self._lib.tnc_set_leaf_variants(self._h, 0, None, 0, None))
+            return
+        arrs = [np.ascontiguousarray(np.asarray(d, dtype=np.complex64)) for d in data]
+        nv = arrs[0].shape[0]
+        if any(a.shape[0] != nv for a in arrs):
+            raise ValueError("every variant leaf needs the same number of copies")
+        ids = (ctypes.c_int * n)(*[int(i) for i in leaf_ids])
+        ptrs = (ctypes.POINTER(ctypes.c_float) * n)(*[a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in arrs])
+        _check(self._lib, self._lib.tnc_set_leaf_variants(self._h, n, ids, int(nv), ptrs))
+
+    def contract_variants(self, v_lo, v_hi, lo=0, hi=None, mode=FP32, out=None, stream=None):
+        """Variants [v_lo, v_hi), each summed over its slices [lo, hi): a
+        complex128 CUDA tensor of shape (v_hi - v_lo, 2^n_open)."""
+        import torch
+        if hi is None:
+            hi = self.n_slices
+        if out is None:
+            out = torch.empty((v_hi - v_lo, self.n_out), dtype=torch.complex128, device="cuda")
+        st = self._lib.tnc_contract_variants(self._h, int(v_lo), int(v_hi), int(lo), int(hi), int(mode),
+                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
         _check(self._lib, st)
         return out
 

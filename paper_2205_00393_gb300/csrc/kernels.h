@@ -269,6 +269,9 @@ struct PersistParams {
     int64_t slice0;
     uint64_t wait_ns;       // bound of one dependency wait (0: 10 s)
     uint32_t spin_limit;    // bound of one tensor-core pipeline wait (0: default)
+    // result of a single-network work list, given at launch (null: the
+    // AccParams / SumTaskParams outputs recorded in the list)
+    double2* out0;
     // optional profile (null: off): per task type t, prof[3t] global-timer ns
     // from the end of its dependency waits to the end of the task, summed over
     // CTAs, prof[3t + 1] tasks, prof[3t + 2] ns spent in its dependency waits

@@ -1057,6 +1057,7 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
                 break;
             case PT_ACC: {
                 const AccParams& ap = P.acc[tk.idx];
+                double2* const dst = P.out0 ? P.out0 : ap.out;
                 const int64_t R = 1ll << ap.pp.obits;
                 for (int64_t r = tid; r < R; r += NT_) {
                     const int64_t src = f32dev::bits_offset(r, ap.pp.ostride, ap.pp.obits, 0);
@@ -1066,12 +1067,13 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
                         acc.x += v.x;
                         acc.y += v.y;
                     }
-                    ap.out[r].x += acc.x;
-                    ap.out[r].y += acc.y;
+                    dst[r].x += acc.x;
+                    dst[r].y += acc.y;
                 }
             } break;
             case PT_SUM: {
                 const SumTaskParams& sp = P.sum[tk.idx];
+                double2* const dst = P.out0 ? P.out0 : sp.out;
                 const int64_t R = 1ll << sp.sp.obits;
                 for (int64_t r = tid; r < R; r += NT_) {
                     const int64_t off = f32dev::bits_offset(r, sp.sp.ostride, sp.sp.obits, 0);
@@ -1083,8 +1085,8 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
                         acc.x += v.x;
                         acc.y += v.y;
                     }
-                    sp.out[r].x += acc.x;
-                    sp.out[r].y += acc.y;
+                    dst[r].x += acc.x;
+                    dst[r].y += acc.y;
                 }
             } break;
             default:

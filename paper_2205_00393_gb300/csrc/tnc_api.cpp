@@ -177,6 +177,15 @@ struct tnc_net {
     int64_t total_leaf_elems = 0;
     // device
     float2* d_leaves = nullptr;
+    // leaf variants (tnc_set_leaf_variants): stacked copies of some leaves,
+    // copy v addressed by the slice-id bits above those of the sliced indices
+    int variant_bits = 0;
+    int64_t n_variants = 0;
+    std::vector<int64_t> var_off;   // per leaf: element offset in the variant buffer, -1 for an ordinary leaf
+    std::vector<float> host_var;    // interleaved complex64, [leaf][variant][elements]
+    float2* d_var = nullptr;
+    size_t d_var_elems = 0;
+    bool var_dirty = false;
     int* d_err = nullptr;           // device error word of bounded waits
     bool dev_dirty = true;
     // path and slices
@@ -242,6 +251,7 @@ struct tnc_net {
         if (d_stem) cudaFree(d_stem);
         if (ws_own) cudaFree(ws_own);
         if (d_prof) cudaFree(d_prof);
+        if (d_var) cudaFree(d_var);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
 };
@@ -301,8 +311,16 @@ void build_plan(tnc_net* net) {
                 P.str[v].emplace_back(full[p], st);
             }
         }
+        if (!net->var_off.empty() && net->var_off[v] >= 0) {
+            // a variant leaf: copy number = slice-id bits [|S|, |S| + variant_bits)
+            const int base = (int)net->S_sorted.size();
+            if (base + net->variant_bits > 62)
+                throw tnc::PlanError("sliced indices and variant bits exceed 62 slice-id bits");
+            for (int j = 0; j < net->variant_bits; ++j) P.sl[v].emplace_back(base + j, net->leaf_elems[v] << j);
+            P.per_slice[v] = 1;
+        }
         if ((int)P.sl[v].size() > tnc::kMaxSliceBits)
-            throw tnc::PlanError("leaf " + std::to_string(v) + " has more than 16 sliced modes");
+            throw tnc::PlanError("leaf " + std::to_string(v) + " has more than 16 sliced modes and variant bits");
     }
     for (size_t i = 0; i < T.children.size(); ++i) {
         const int v = net->n_leaves + (int)i;
@@ -647,7 +665,8 @@ tnc::Operand operand(const tnc_net* net, const Arena& ar, char* ws, int v, int64
     const Plan& P = net->plan;
     tnc::Operand op{};
     if (v < net->n_leaves) {
-        op.ptr = net->d_leaves + net->leaf_off[v];
+        const bool var = !net->var_off.empty() && net->var_off[v] >= 0;
+        op.ptr = var ? net->d_var + net->var_off[v] : net->d_leaves + net->leaf_off[v];
         op.batch_stride = 0;
         op.n_sl = (int)P.sl[v].size();
         for (int j = 0; j < op.n_sl; ++j) {
@@ -771,7 +790,27 @@ tnc_status ensure_leaves(tnc_net* net, cudaStream_t st) {
         CUDA_TRY(cudaStreamSynchronize(st));  // pageable source: keep the host copy stable
         net->dev_dirty = false;
     }
+    if (net->var_dirty) {
+        const size_t elems = net->host_var.size() / 2;
+        if (elems > net->d_var_elems) {
+            if (net->d_var) CUDA_TRY(cudaFree(net->d_var));
+            net->d_var = nullptr;
+            net->d_var_elems = 0;
+            CUDA_TRY(cudaMalloc(&net->d_var, elems * 8));
+            net->d_var_elems = elems;
+        }
+        if (elems) {
+            CUDA_TRY(cudaMemcpyAsync(net->d_var, net->host_var.data(), elems * 8, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        net->var_dirty = false;
+    }
     return TNC_OK;
+}
+
+// Slice ids a call may address: the 2^|S| slices of every leaf variant.
+int64_t slice_space(const tnc_net* net) {
+    return 1ll << std::min<size_t>(net->S_sorted.size() + net->variant_bits, 62);
 }
 
 // Event pair around one launch when timing is on; returns the pool slot.
@@ -1461,7 +1500,7 @@ tnc_status wl_upload(const WorkList& W, DeviceWorkList& D, int* err, uint64_t wa
 
 // Reset the counters and the ticket, then launch (stream-ordered; capturable).
 cudaError_t wl_launch(const DeviceWorkList& D, int mode, int64_t slice0, const int64_t* rs0, cudaStream_t s,
-                      unsigned long long* prof) {
+                      unsigned long long* prof, double* out0) {
     cudaError_t e = cudaMemcpyAsync(D.prm.counters, D.init, D.n_counters * sizeof(int), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.prm.ticket, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -1469,6 +1508,7 @@ cudaError_t wl_launch(const DeviceWorkList& D, int mode, int64_t slice0, const i
     p.slice0 = slice0;
     p.rs0 = rs0;
     p.prof = prof;
+    p.out0 = reinterpret_cast<double2*>(out0);
     return tnc::launch_persist(p, mode, s);
 }
 
@@ -1483,10 +1523,13 @@ bool wl_validate(const tnc_net* net, const WorkList& W, const char* ws, size_t w
     const size_t lv_bytes = (size_t)net->total_leaf_elems * 8;
     const char* ob = reinterpret_cast<const char*>(out);
     const size_t out_bytes = (size_t)16 << net->plan.obits;
+    const char* vb = reinterpret_cast<const char*>(net->d_var);
+    const size_t vb_bytes = net->host_var.size() * 4;
     auto inside = [&](const void* p, int64_t bytes, const char* what) {
         const char* c = static_cast<const char*>(p);
         const bool ok = bytes >= 0 && ((c >= ws && c + bytes <= ws + ws_bytes) || (c >= lv && c + bytes <= lv + lv_bytes) ||
-                                       (c >= ob && c + bytes <= ob + out_bytes));
+                                       (c >= ob && c + bytes <= ob + out_bytes) ||
+                                       (vb && c >= vb && c + bytes <= vb + vb_bytes));
         if (!ok) *why = std::string("work list range outside its buffers: ") + what;
         return ok;
     };
@@ -1566,8 +1609,9 @@ bool wl_validate(const tnc_net* net, const WorkList& W, const char* ws, size_t w
 DeviceWorkList* contract_worklist(tnc_net* net, const Arena& ar, char* ws, int b, int mode, bool with_inv,
                                   double* out, cudaStream_t s, tnc_status* st) {
     *st = TNC_OK;
+    // the result pointer is not part of the list: launches pass it (out0)
     const std::string key = net->group_key + "|" + std::to_string(b) + ":" + std::to_string(with_inv ? 1 : 0) + ":" +
-                            std::to_string((uintptr_t)out) + ":" + std::to_string(net->tc_spin_limit) + ":" +
+                            std::to_string(net->tc_spin_limit) + ":" +
                             std::to_string(net->tc_test_stall) + ":" + std::to_string(net->persist_test_stall) + ":" +
                             std::to_string(net->persist_wait_ns) + ":" + std::to_string(net->tc_group_m);
     auto it = net->worklists.find(key);
@@ -2020,7 +2064,7 @@ tnc_status many_run(ManyCall& mc, cudaStream_t s) {
     mc.kernels = 0;
     if (!mc.wls.empty()) {
         for (size_t r = 0; r < mc.wls.size(); ++r) {
-            CUDA_TRY(wl_launch(*mc.wls[r], mc.mode, 0, mc.d_rs0 + (int64_t)r * n, s, mc.nets[0]->d_prof));
+            CUDA_TRY(wl_launch(*mc.wls[r], mc.mode, 0, mc.d_rs0 + (int64_t)r * n, s, mc.nets[0]->d_prof, nullptr));
             mc.kernels += 1;
         }
         return TNC_OK;
@@ -2331,6 +2375,71 @@ tnc_status tnc_create_network(int n_tensors, const int* ranks, const int64_t* co
     return TNC_OK;
 }
 
+tnc_status tnc_set_leaf_variants(tnc_net_t net, int n, const int* leaf_ids, int64_t n_variants,
+                                 const float* const* data_c64) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (n == 0) {  // back to ordinary leaves
+        net->var_off.clear();
+        net->host_var.clear();
+        net->variant_bits = 0;
+        net->n_variants = 0;
+        net->plan.valid = false;
+        net->inv_key.clear();
+        return TNC_OK;
+    }
+    if (n < 0 || n > net->n_leaves || !leaf_ids || !data_c64) return fail(TNC_E_INVALID, "bad variant leaf list");
+    if (n_variants < 1 || n_variants > (1ll << 24)) return fail(TNC_E_INVALID, "n_variants must be in [1, 2^24]");
+    int m = 0;
+    while ((1ll << m) < n_variants) ++m;
+    std::vector<int64_t> off(net->n_leaves, -1);
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const int leaf = leaf_ids[i];
+        if (leaf < 0 || leaf >= net->n_leaves) return fail(TNC_E_INVALID, "variant leaf out of range");
+        if (off[leaf] >= 0) return fail(TNC_E_INVALID, "variant leaf repeated");
+        if (!data_c64[i]) return fail(TNC_E_INVALID, "NULL variant data");
+        off[leaf] = total;
+        total += net->leaf_elems[leaf] << m;
+    }
+    if (total > (1ll << 34)) return fail(TNC_E_INVALID, "variant data above 2^34 elements");
+    std::vector<float> host((size_t)total * 2, 0.0f);  // copies past n_variants stay zero
+    for (int i = 0; i < n; ++i) {
+        const int leaf = leaf_ids[i];
+        std::memcpy(host.data() + 2 * off[leaf], data_c64[i], (size_t)n_variants * net->leaf_elems[leaf] * 8);
+    }
+    net->var_off = std::move(off);
+    net->host_var = std::move(host);
+    net->variant_bits = m;
+    net->n_variants = n_variants;
+    net->var_dirty = true;
+    net->plan.valid = false;
+    net->inv_key.clear();
+    return TNC_OK;
+}
+
+tnc_status tnc_contract_variants(tnc_net_t net, int64_t v_lo, int64_t v_hi, int64_t lo, int64_t hi, int mode,
+                                 double* out_c128, void* stream) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    if (!out_c128) return fail(TNC_E_INVALID, "NULL output");
+    tnc_status st = ensure_plan(net);
+    if (st != TNC_OK) return st;
+    if (!net->n_variants) return fail(TNC_E_STATE, "no leaf variants (call tnc_set_leaf_variants)");
+    if (v_lo < 0 || v_hi < v_lo || v_hi > net->n_variants) return fail(TNC_E_INVALID, "variant range out of bounds");
+    const int sbits = (int)std::min<size_t>(net->S_sorted.size(), 62);
+    const int64_t ns = 1ll << sbits;
+    if (lo < 0 || hi < lo || hi > ns) return fail(TNC_E_INVALID, "slice range outside [0, 2^|S|]");
+    const int64_t n_out = 1ll << net->plan.obits;
+    // the slice-invariant tensors are computed by the first variant and kept
+    // in the workspace for the others
+    const int keep = net->cache_invariants;
+    if (!keep) net->inv_key.clear();  // computed afresh by this call's first variant
+    net->cache_invariants = 1;
+    for (int64_t v = v_lo; v < v_hi && st == TNC_OK; ++v)
+        st = tnc_contract(net, (v << sbits) + lo, (v << sbits) + hi, mode, out_c128 + 2 * (v - v_lo) * n_out, stream);
+    net->cache_invariants = keep;
+    return st;
+}
+
 tnc_status tnc_set_tensor_data(tnc_net_t net, int tensor, const float* data_c64) {
     if (!net || !data_c64) return fail(TNC_E_INVALID, "NULL argument");
     if (tensor < 0 || tensor >= net->n_leaves) return fail(TNC_E_INVALID, "tensor out of range");
@@ -2456,8 +2565,9 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
-    const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
-    if (lo < 0 || hi < lo || hi > n_slices) return fail(TNC_E_INVALID, "slice range outside [0, 2^|S|]");
+    const int64_t n_slices = slice_space(net);
+    if (lo < 0 || hi < lo || hi > n_slices)
+        return fail(TNC_E_INVALID, "slice range outside [0, 2^(|S| + variant bits)]");
     cudaStream_t s = (cudaStream_t)stream;
     const Plan& P = net->plan;
     const int64_t R = 1ll << P.obits;
@@ -2513,7 +2623,7 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
                 const int b = (int)std::min<int64_t>(nb, hi - s0);
                 CUDA_TRY(timed_begin(net, -1, K_PERSIST, b, s, wl->cmacs));
                 if (net->timing) net->timed_persist_tc_cmacs += wl->tc_cmacs;
-                CUDA_TRY(wl_launch(*wl, mode, s0, nullptr, s, net->d_prof));
+                CUDA_TRY(wl_launch(*wl, mode, s0, nullptr, s, net->d_prof, out_c128));
                 CUDA_TRY(timed_end(net, s));
             }
             net->inv_key = net->cache_invariants ? ikey : std::string();
@@ -2587,8 +2697,11 @@ tnc_status tnc_autotune(tnc_net_t net, int mode, int64_t slice, void* stream) {
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
+    const int64_t n_slices = slice_space(net);
     if (slice < 0 || slice >= n_slices) return fail(TNC_E_INVALID, "slice out of range");
+    bool any = false;  // nothing to choose without a tensor-core-eligible contraction
+    for (const NodePlan& np : net->plan.nodes) any |= tc_node(mode, np.mb, np.nb, np.kb, np.is_root);
+    if (!any) return TNC_OK;
     const int R = 1 << net->plan.obits;
     double* out = nullptr;
     CUDA_TRY(cudaMalloc(&out, (size_t)R * 16));
@@ -2785,6 +2898,8 @@ tnc_status tnc_contract_backward(tnc_net_t net, int64_t lo, int64_t hi, int mode
     if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
     tnc_status st = ensure_plan(net);
     if (st != TNC_OK) return st;
+    if (net->variant_bits || net->n_variants)
+        return fail(TNC_E_STATE, "the adjoint pass does not take leaf variants (tnc_set_leaf_variants)");
     const int64_t n_slices = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
     if (lo < 0 || hi < lo || hi > n_slices) return fail(TNC_E_INVALID, "slice range outside [0, 2^|S|]");
     cudaStream_t s = (cudaStream_t)stream;
@@ -2907,9 +3022,10 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
         if (!outs_c128[i]) return fail(TNC_E_INVALID, "NULL output");
         tnc_status st = ensure_plan(net);
         if (st != TNC_OK) return st;
-        const int64_t ns = 1ll << std::min<size_t>(net->S_sorted.size(), 62);
+        const int64_t ns = slice_space(net);
         if (slice_lo[i] < 0 || slice_hi[i] < slice_lo[i] || slice_hi[i] > ns)
-            return fail(TNC_E_INVALID, "slice range of network " + std::to_string(i) + " outside [0, 2^|S|]");
+            return fail(TNC_E_INVALID, "slice range of network " + std::to_string(i) +
+                                           " outside [0, 2^(|S| + variant bits)]");
         for (int j = 0; j < i; ++j)
             if (nets[j] == net) return fail(TNC_E_INVALID, "a network appears twice");
         key << "|" << net->uid << ":" << net->plan.version << ":" << slice_lo[i] << ":" << slice_hi[i] << ":"

@@ -11,11 +11,12 @@ arithmetic; both the oracle and the library consume what it produces.
 
 from .gates import sqrt_x, sqrt_y, sqrt_w, fsim, hadamard, cnot, cz, s_gate, identity2
 from .circuits import Circuit, Gate, grid_rqc, lattice_53q_rqc, coupler_layers
-from .network import TensorNetwork, circuit_to_network
+from .network import TensorNetwork, circuit_to_network, projection_leaves, random_bitstrings, bitstring_variants
 from .paths import stem_path
 
 __all__ = [
     "sqrt_x", "sqrt_y", "sqrt_w", "fsim", "hadamard", "cnot", "cz", "s_gate",
     "identity2", "Circuit", "Gate", "grid_rqc", "lattice_53q_rqc",
     "coupler_layers", "TensorNetwork", "circuit_to_network", "stem_path",
+    "projection_leaves", "random_bitstrings", "bitstring_variants",
 ]

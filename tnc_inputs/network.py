@@ -76,3 +76,35 @@ def circuit_to_network(circuit, bitstring=None):
     open_ids = tuple(wire[q] for q in sorted(open_set))
     dims = np.full(next_id, 2, dtype=np.int64)
     return TensorNetwork(tensors, indices, dims, open_ids, leaf_gate)
+
+
+def projection_leaves(circuit):
+    """Leaf ids of the <x_q| projection vectors of ``circuit_to_network(circuit)``
+    and their qubits, in qubit order (closed qubits only)."""
+    open_set = set(circuit.open_qubits)
+    first = circuit.n_qubits + len(circuit.gates)
+    closed = [q for q in range(circuit.n_qubits) if q not in open_set]
+    return [first + j for j in range(len(closed))], closed
+
+
+def random_bitstrings(circuit, n, seed):
+    """n seeded bitstrings (uint8, shape (n, n_qubits)) over the circuit's
+    qubits; open qubits are 0 (they are summed over as outputs, not fixed)."""
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 2, size=(n, circuit.n_qubits)).astype(np.uint8)
+    bits[:, list(circuit.open_qubits)] = 0
+    return bits
+
+
+def bitstring_variants(circuit, bitstrings):
+    """Variant data for the projection leaves: for each closed qubit q, an
+    array of shape (n, 2) whose row v is the one-hot vector <b_v[q]|. Returns
+    (leaf ids, list of arrays), the arguments of Network.set_leaf_variants."""
+    leaves, closed = projection_leaves(circuit)
+    bits = np.asarray(bitstrings, dtype=np.int64)
+    data = []
+    for q in closed:
+        a = np.zeros((bits.shape[0], 2), dtype=np.complex64)
+        a[np.arange(bits.shape[0]), bits[:, q]] = 1.0
+        data.append(a)
+    return leaves, data

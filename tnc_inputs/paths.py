@@ -54,3 +54,4 @@ def stem_path(network, circuit):
     for leaf in range(nq + n_gates, n_leaves):  # projection vectors of closed qubits
         stem = join(stem, leaf)
     return path
+
