@@ -287,10 +287,11 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *  "stem_coalesce_bits" 0..6 (default 3): the lowest-stride modes of a
  *                  group's input and output stem that stay inner, so that
  *                  each CTA reads and writes runs of 2^value elements
- *  "persistent"    0 or 1 (default 1): the persistent executor. A call whose
- *                  contractions all fit it (no fused stem group in use, no
- *                  tensor-core contraction cut into row or K panels) runs
- *                  each batch of slices as ONE launch of a work-list kernel
+ *  "persistent"    0, 1 or 2 (default 2): the executor. 1: the persistent
+ *                  executor. A call whose contractions all fit it (no fused
+ *                  stem group in use, no tensor-core contraction cut into row
+ *                  or K panels) runs each batch of slices as ONE launch of a
+ *                  work-list kernel
  *                  with one CTA per SM: the tasks (FP32 GEMM tiles, operand
  *                  split blocks, 128 x 128 tensor-core tiles, K-split
  *                  reductions, root chunks and sums) are taken in list order
@@ -298,7 +299,12 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  for the tasks that produce its inputs and for the previous
  *                  tree level. Results equal the per-level launches' up to
  *                  the order of FP32 additions in a K split; other calls, and
- *                  0, use one launch per tree level
+ *                  0, use one launch per tree level. 2: the persistent
+ *                  executor when the per-level launches of a batch would
+ *                  carry less than 2^31 complex multiply-accumulates each on
+ *                  average (launch-bound calls), else one launch per level
+ *                  (for tnc_contract_many: over the whole call, unless every
+ *                  network has 1)
  *  "persist_wait_ms" 0..600000 (default 0 = 10 s): bound of one dependency
  *                  wait of the persistent executor; a wait that runs out
  *                  stops every CTA and tnc_check_device reports TNC_E_TIMEOUT

@@ -50,7 +50,8 @@ constexpr int TM = 128, TN = 128;                 // complex output tile
 constexpr int SMEM_PIPE = 192 * 1024;             // shared memory for the TMA ring
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kErrTimeout = 4;
-constexpr int KC_ELEMS = 256;                     // K per TMEM chunk (and per FP16x2 scale)
+constexpr int KC_ELEMS = 256;                     // K per FP16x2 scale chunk (whole chunks per CTA)
+constexpr int KD_ELEMS = 128;                     // K per TMEM accumulation (drained into registers)
 
 // KIND 0: three BF16 parts (6 pairs), kind::f16; 1: two TF32 parts (3 pairs),
 // kind::tf32; 2: two BF16 parts (3 pairs), kind::f16; 3: two FP16 parts of
@@ -197,13 +198,15 @@ __host__ __device__ constexpr uint32_t instr_desc(bool negate_a) {
 __constant__ int kPairsBF16[6][2] = {{1, 1}, {0, 2}, {2, 0}, {0, 1}, {1, 0}, {0, 0}};
 __constant__ int kPairs2[3][2] = {{0, 1}, {1, 0}, {0, 0}};
 
-// K is processed in chunks of KC_ELEMS. Each chunk accumulates in one of two
+// K is processed in chunks of KD_ELEMS. Each chunk accumulates in one of two
 // TMEM buffers of 256 columns (Cr in the first 128, Ci in the last 128); when
 // a chunk is complete the epilogue warps move it into FP32 registers while
 // the tensor cores work on the next chunk in the other buffer. The tensor
 // core's accumulation into TMEM does not round to nearest, so its error grows
-// linearly with the number of accumulated MMAs; short chunks bound that
-// growth and the register sums across chunks round to nearest.
+// linearly with the number of accumulated MMAs: with four real products per
+// complex product, every accumulator element takes 2 x (part pairs) MMAs per
+// 16 (TF32: 8) of K, so short chunks bound that growth, and the register sums
+// across chunks round to nearest. The FP16x2 scales cover KC_ELEMS = 2 chunks.
 constexpr int EPI_WARPS = 8;   // warps 0-7: epilogue (warp w: TMEM lanes 32*(w%4), columns 64*(w/4))
 constexpr int EPI_LDW = 66;    // float2 per row of a warp's staged 32 x 64 output block (2 of padding)
 static_assert(EPI_WARPS * 32 * EPI_LDW * 8 <= SMEM_PIPE, "staged epilogue fits the pipeline ring");
@@ -265,7 +268,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* tmA, const CUtensorMa
     const int za = p.a_shared ? 0 : z, zb = p.b_shared ? 0 : z;  // batch entry of each operand's planes
     const int nkb = (int)((K >> p.ksplit_bits) / C_::BK);         // k-blocks of this K split
     const int kb_off = ky * nkb;
-    const int kpc = nkb < KC_ELEMS / C_::BK ? nkb : KC_ELEMS / C_::BK;  // k-blocks per chunk
+    const int kpc = nkb < KD_ELEMS / C_::BK ? nkb : KD_ELEMS / C_::BK;  // k-blocks per chunk
     const int nchunks = nkb / kpc;
     volatile int* abort_flag = &sh.abort;
     const uint32_t spin = p.spin_limit ? p.spin_limit : kSpinLimit;
@@ -364,7 +367,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* tmA, const CUtensorMa
         }
         // split FP16x2: per-chunk scale exponents of this lane's row and of the warp's 64 columns;
         // the columns' factors 2^-e go through a warp-private table in shared memory
-        const int64_t nch = K / (K < KC_ELEMS ? K : KC_ELEMS);  // chunks over the whole K of the planes
+        const int64_t sk = K < KC_ELEMS ? K : KC_ELEMS;  // K per scale chunk
+        const int64_t nch = K / sk;                       // scale chunks over the whole K of the planes
         const int8_t* ea_row = nullptr;
         const int8_t* eb_col = nullptr;
         if constexpr (KIND == 3) {
@@ -384,7 +388,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* tmA, const CUtensorMa
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int64_t cg = (int64_t)ky * nchunks + c;  // chunk index over the planes' K
+            // scale chunk of this TMEM chunk (chunk index over the planes' K x its K / scale chunk's K)
+            const int64_t cg = ((int64_t)ky * nchunks + c) * (kpc * C_::BK) / sk;
             float sa = 1.f;
             if constexpr (KIND == 3) {
                 sa = pow2f(-(int)ea_row[cg * M]);

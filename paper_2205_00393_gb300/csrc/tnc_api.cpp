@@ -235,7 +235,7 @@ struct tnc_net {
     std::vector<TimedLaunch> timed;
     int64_t launches = 0;
     // persistent executor (one launch per slice batch); its device work lists by key
-    int persistent = 1;
+    int persistent = 2;  // 0 per-level launches, 1 persistent kernel, 2 automatic choice
     uint64_t persist_wait_ns = 0;    // bound of one dependency wait (0: 10 s)
     int persist_test_stall = 0;      // tests only: one task waits on a counter nothing signals
     std::map<std::string, std::unique_ptr<DeviceWorkList>> worklists;
@@ -1341,6 +1341,41 @@ bool persist_eligible(tnc_net* net) {
            !net->tuning;
 }
 
+// Launches and complex multiply-accumulates of one batch of b slices on the
+// per-level executor (the slice-invariant levels included when with_inv):
+// one grouped launch per level for its FP32 contractions, three per
+// tensor-core contraction (two operand splits and the GEMM), two for the
+// final contraction.
+void level_cost(tnc_net* net, int mode, int64_t b, bool with_inv, double* launches, double* cmacs) {
+    const Plan& P = net->plan;
+    for (bool per : {false, true}) {
+        if (!per && !with_inv) continue;
+        for (const Group& g : level_groups(net, mode, per)) {
+            if (!g.fp32.empty()) *launches += 1;
+            for (int v : g.tc) {
+                const NodePlan& np = P.nodes[v - net->n_leaves];
+                *launches += shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root) ? 3 : 1;
+            }
+            for (auto* list : {&g.fp32, &g.tc})
+                for (int v : *list) {
+                    const NodePlan& np = P.nodes[v - net->n_leaves];
+                    *cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * (per ? b : 1);
+                }
+        }
+    }
+    for (const NodePlan& np : P.nodes)
+        if (np.is_root) {
+            *launches += 2;
+            *cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * b;
+        }
+}
+
+// The automatic executor choice: the persistent kernel when the per-level
+// launches would carry less than 2^31 complex multiply-accumulates each on
+// average (about 60 us of tensor-core work), i.e. when launch gaps and tail
+// effects, not the contractions, would dominate.
+constexpr double kPersistAutoCmacsPerLaunch = 2147483648.0;
+
 // Tasks of one network for a batch b: the slice-invariant levels (if with_inv),
 // the per-slice levels and the final contraction.
 bool wl_network(tnc_net* net, const Arena& ar, char* ws, int b, int mode, bool with_inv, int netidx, double* out,
@@ -2273,8 +2308,16 @@ tnc_status many_build(ManyCall& mc, cudaStream_t s) {
     // list with every network's tasks, levels interleaved; slice ids per
     // network come from the round's row of the device table d_rs0. A network
     // it cannot run keeps the whole call on the merged level launches.
-    bool pers = true;
-    for (tnc_net* net : mc.nets) pers &= net->persistent != 0;
+    bool pers = true, forced = true;
+    for (tnc_net* net : mc.nets) {
+        pers &= net->persistent != 0;
+        forced &= net->persistent == 1;
+    }
+    if (pers && !forced) {  // automatic choice over the whole call
+        double launches = 0, cmacs = 0;
+        for (int i = 0; i < n; ++i) level_cost(mc.nets[i], mc.mode, mc.nb[i], true, &launches, &cmacs);
+        pers = cmacs < kPersistAutoCmacsPerLaunch * std::max(launches, 1.0);
+    }
     for (int r = 0; r < R && pers; ++r) {
         WorkList W;
         for (int i = 0; i < n && pers; ++i) {
@@ -2607,7 +2650,14 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     // contractions in the first one (unless cached). Every batch's work list is
     // prepared before the first launch, so a call that it cannot run falls back
     // to the launches below as a whole.
-    if (persist_eligible(net)) {
+    bool use_persist = persist_eligible(net);
+    if (use_persist && net->persistent == 2) {
+        const bool inv_cached = net->cache_invariants && net->inv_key == ikey;
+        double launches = 0, cmacs = 0;
+        level_cost(net, mode, nb, !inv_cached, &launches, &cmacs);
+        use_persist = cmacs < kPersistAutoCmacsPerLaunch * std::max(launches, 1.0);
+    }
+    if (use_persist) {
         const bool inv_cached = net->cache_invariants && net->inv_key == ikey;
         std::vector<std::pair<DeviceWorkList*, int64_t>> rounds;
         bool ok = true;
@@ -2807,7 +2857,7 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
         net->plane_cap_log2 = (int)value;
         net->group_key.clear();
     } else if (k == "persistent") {
-        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "persistent must be 0 or 1");
+        if (value < 0 || value > 2) return fail(TNC_E_INVALID, "persistent must be 0, 1 or 2");
         net->persistent = (int)value;
     } else if (k == "persist_wait_ms") {
         if (value < 0 || value > 600000) return fail(TNC_E_INVALID, "persist_wait_ms must be in [0, 600000]");

@@ -113,3 +113,21 @@ def test_persistent_wait_timeout(lib):
     got = net.contract(0, net.n_slices, 2).cpu().numpy()
     net.check_device()
     assert floored_rel_err(got, tn.contract(ref_net, path, S), 12) <= 1e-4
+
+
+def test_automatic_executor_choice(lib):
+    """Default ("persistent" = 2): the 12-qubit call (16 slices, contractions
+    of at most a few thousand MACs) is launch-bound and runs as one
+    persistent launch; two slices of the 30-qubit workload (contractions of
+    2^38 MACs) run one launch per tree level."""
+    _, net, _, _ = _grid(3, 4, 8, 1, 0, 8)
+    net.set_timing(True)
+    net.contract(0, net.n_slices, 2)
+    assert [r["kind"] for r in net.last_timings()[0]] == [9]
+    _, big, _, _ = _grid(5, 6, 14, 2, 6, 27)
+    big.set_timing(True)
+    big.contract(0, 2, 4)
+    kinds = {r["kind"] for r in big.last_timings()[0]}
+    big.set_timing(False)
+    big.check_device()
+    assert 9 not in kinds and 3 in kinds
