@@ -701,7 +701,6 @@ def grad42_bench(args):
     exact because the amplitude is linear in every gate matrix."""
     import torch
     from tnc_inputs import circuit_to_network, grid_rqc
-    from oracle import gradient
     from paper_2205_00393_gb300.torch_fn import CircuitAmplitudes
     torch.cuda.set_device(0)
     c = grid_rqc(6, 7, 12, 5)
@@ -711,7 +710,8 @@ def grad42_bench(args):
     mode = MODES[args.mode]  # FP32 by default: complex64 forward, FP32 adjoint
     amp = CircuitAmplitudes(tn_, fsim, target_log2=30, seed=7, lo=0, hi=n_sl, mode=mode,
                             budget_bytes=80 << 30)
-    params = torch.tensor(gradient.circuit_params(c), dtype=torch.float64, requires_grad=True)
+    params = torch.tensor(np.array([g.params for g in c.gates if g.name == "fsim"], dtype=np.float64),
+                          dtype=torch.float64, requires_grad=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     a = amp(params)
@@ -847,6 +847,9 @@ def stem_bench(args):
     stream = torch.cuda.current_stream()
     out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
     res = {}
+    # both on the per-level executor: the fused groups run there, and the
+    # unfused baseline is the same contractions as separate per-level launches
+    net.set_option("persistent", 0)
     for name, cap in (("fused", 12), ("unfused", 0)):
         net.set_option("stem_cap_log2", cap)
         ws = torch.empty(net.workspace_bytes(1), dtype=torch.uint8, device="cuda")

@@ -301,8 +301,10 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  the order of FP32 additions in a K split; other calls, and
  *                  0, use one launch per tree level. 2: the persistent
  *                  executor when the per-level launches of a batch would
- *                  carry less than 2^31 complex multiply-accumulates each on
- *                  average (launch-bound calls), else one launch per level
+ *                  carry less than 60 us of work each on average (a
+ *                  contraction estimated at the larger of its flops at 300
+ *                  TFLOP/s and its 8 (MK + KN + MN) bytes per slice at 6
+ *                  TB/s: launch-bound calls), else one launch per level
  *                  (for tnc_contract_many: over the whole call, unless every
  *                  network has 1)
  *  "persist_wait_ms" 0..600000 (default 0 = 10 s): bound of one dependency

@@ -1341,13 +1341,19 @@ bool persist_eligible(tnc_net* net) {
            !net->tuning;
 }
 
-// Launches and complex multiply-accumulates of one batch of b slices on the
-// per-level executor (the slice-invariant levels included when with_inv):
-// one grouped launch per level for its FP32 contractions, three per
-// tensor-core contraction (two operand splits and the GEMM), two for the
-// final contraction.
-void level_cost(tnc_net* net, int mode, int64_t b, bool with_inv, double* launches, double* cmacs) {
+// Launches and estimated seconds of one batch of b slices on the per-level
+// executor (the slice-invariant levels included when with_inv): one grouped
+// launch per level for its FP32 contractions, three per tensor-core
+// contraction (two operand splits and the GEMM), two for the final
+// contraction. A contraction's time is estimated as the larger of its flops
+// at 300 TFLOP/s and its operand and result bytes, 8 (MK + KN + MN) per
+// slice, at 6 TB/s.
+void level_cost(tnc_net* net, int mode, int64_t b, bool with_inv, double* launches, double* seconds) {
     const Plan& P = net->plan;
+    auto node_s = [](const NodePlan& np, double bb) {
+        const double M = std::ldexp(1.0, np.mb), N = std::ldexp(1.0, np.nb), K = std::ldexp(1.0, np.kb);
+        return std::max(8.0 * M * N * K * bb / 3e14, 8.0 * (M * K + K * N + M * N) * bb / 6e12);
+    };
     for (bool per : {false, true}) {
         if (!per && !with_inv) continue;
         for (const Group& g : level_groups(net, mode, per)) {
@@ -1357,24 +1363,21 @@ void level_cost(tnc_net* net, int mode, int64_t b, bool with_inv, double* launch
                 *launches += shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root) ? 3 : 1;
             }
             for (auto* list : {&g.fp32, &g.tc})
-                for (int v : *list) {
-                    const NodePlan& np = P.nodes[v - net->n_leaves];
-                    *cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * (per ? b : 1);
-                }
+                for (int v : *list) *seconds += node_s(P.nodes[v - net->n_leaves], per ? (double)b : 1.0);
         }
     }
     for (const NodePlan& np : P.nodes)
         if (np.is_root) {
             *launches += 2;
-            *cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * b;
+            *seconds += node_s(np, (double)b);
         }
 }
 
 // The automatic executor choice: the persistent kernel when the per-level
-// launches would carry less than 2^31 complex multiply-accumulates each on
-// average (about 60 us of tensor-core work), i.e. when launch gaps and tail
-// effects, not the contractions, would dominate.
-constexpr double kPersistAutoCmacsPerLaunch = 2147483648.0;
+// launches would carry less than 60 us of estimated work each on average,
+// i.e. when launch gaps and tail effects, not the contractions, would
+// dominate.
+constexpr double kPersistAutoSecondsPerLaunch = 60e-6;
 
 // Tasks of one network for a batch b: the slice-invariant levels (if with_inv),
 // the per-slice levels and the final contraction.
@@ -2314,9 +2317,9 @@ tnc_status many_build(ManyCall& mc, cudaStream_t s) {
         forced &= net->persistent == 1;
     }
     if (pers && !forced) {  // automatic choice over the whole call
-        double launches = 0, cmacs = 0;
-        for (int i = 0; i < n; ++i) level_cost(mc.nets[i], mc.mode, mc.nb[i], true, &launches, &cmacs);
-        pers = cmacs < kPersistAutoCmacsPerLaunch * std::max(launches, 1.0);
+        double launches = 0, seconds = 0;
+        for (int i = 0; i < n; ++i) level_cost(mc.nets[i], mc.mode, mc.nb[i], true, &launches, &seconds);
+        pers = seconds < kPersistAutoSecondsPerLaunch * std::max(launches, 1.0);
     }
     for (int r = 0; r < R && pers; ++r) {
         WorkList W;
@@ -2653,9 +2656,9 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     bool use_persist = persist_eligible(net);
     if (use_persist && net->persistent == 2) {
         const bool inv_cached = net->cache_invariants && net->inv_key == ikey;
-        double launches = 0, cmacs = 0;
-        level_cost(net, mode, nb, !inv_cached, &launches, &cmacs);
-        use_persist = cmacs < kPersistAutoCmacsPerLaunch * std::max(launches, 1.0);
+        double launches = 0, seconds = 0;
+        level_cost(net, mode, nb, !inv_cached, &launches, &seconds);
+        use_persist = seconds < kPersistAutoSecondsPerLaunch * std::max(launches, 1.0);
     }
     if (use_persist) {
         const bool inv_cached = net->cache_invariants && net->inv_key == ikey;
