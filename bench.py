@@ -557,6 +557,8 @@ def bitstrings_bench(args):
     net = Network.from_tn(ref_net)
     if args.bitstring_path == "stem":
         net.set_path(stem_path(ref_net, c))
+        if args.stem_coalesce_bits is not None:
+            net.set_option("stem_coalesce_bits", args.stem_coalesce_bits)
         S = []
         ns = 1
     else:
@@ -841,6 +843,8 @@ def stem_bench(args):
     tn_ = circuit_to_network(c).as_complex64()
     net = Network.from_tn(tn_)
     net.set_path(stem_path(tn_, c))
+    if args.stem_coalesce_bits is not None:
+        net.set_option("stem_coalesce_bits", args.stem_coalesce_bits)
     stats = net.stats()
     groups = stats["stem_groups"]
     flops = node_flops(stats, 1)
@@ -891,7 +895,8 @@ def stem_bench(args):
                                           "peak_source": "hbm copy %s (MEASURED_PEAKS.json)" % peak_src}},
             "fused": res["fused"], "unfused": res["unfused"],
             "config": {"workload": "rqc-%s-12cyc-seed4-open4 time-ordered stem path, not sliced" % args.stem_grid,
-                       "max_log2_size": stats["max_log2_size"], "mode": "fp32 (narrow steps run on CUDA cores)"}}
+                       "max_log2_size": stats["max_log2_size"], "mode": "fp32 (narrow steps run on CUDA cores)",
+                       "stem_coalesce_bits": args.stem_coalesce_bits}}
     print(json.dumps(line))
     return 0
 
@@ -931,6 +936,8 @@ def main():
     ap.add_argument("--stem", action="store_true",
                     help="time fused stem groups against separate launches on a 28-qubit stem path instead")
     ap.add_argument("--stem-grid", default="4x7", help="--stem: grid of the circuit (ROWSxCOLS)")
+    ap.add_argument("--stem-coalesce-bits", type=int, default=None,
+                    help="--stem, --bitstrings: the stem_coalesce_bits option (default: the library's)")
     ap.add_argument("--backward", action="store_true",
                     help="time the adjoint pass (leaf environments of all fSim gates) instead")
     ap.add_argument("--single-node", default=None,
