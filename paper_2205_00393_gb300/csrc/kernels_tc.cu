@@ -20,7 +20,7 @@
 //         Cr += Ar Br,  Cr += (-Ai) Bi  (the MMA's negate-A bit),
 //         Ci += Ar Bi,  Ci += Ai Br,
 //     so the complex tile lives in 256 TMEM columns and two such buffers
-//     alternate per 256-wide K chunk; eight epilogue warps move each chunk's
+//     alternate per 128-wide K chunk; eight epilogue warps move each chunk's
 //     Cr, Ci into FP32 registers while the tensor cores fill the other
 //     buffer, and finally write C.
 //
@@ -206,7 +206,8 @@ __constant__ int kPairs2[3][2] = {{0, 1}, {1, 0}, {0, 0}};
 // linearly with the number of accumulated MMAs: with four real products per
 // complex product, every accumulator element takes 2 x (part pairs) MMAs per
 // 16 (TF32: 8) of K, so short chunks bound that growth, and the register sums
-// across chunks round to nearest. The FP16x2 scales cover KC_ELEMS = 2 chunks.
+// across chunks round to nearest. One FP16x2 scale chunk (KC_ELEMS of K)
+// spans two accumulation chunks.
 constexpr int EPI_WARPS = 8;   // warps 0-7: epilogue (warp w: TMEM lanes 32*(w%4), columns 64*(w/4))
 constexpr int EPI_LDW = 66;    // float2 per row of a warp's staged 32 x 64 output block (2 of padding)
 static_assert(EPI_WARPS * 32 * EPI_LDW * 8 <= SMEM_PIPE, "staged epilogue fits the pipeline ring");
