@@ -266,6 +266,34 @@ def cpu_threads():
         return os.cpu_count()
 
 
+def oracle_c1_seconds(threads=None):
+    """Seconds the FP64 oracle takes for every slice (16) of the 12-qubit 3x4
+    circuit (8 cycles, seed 1, t = 8), in a fresh interpreter so that the BLAS
+    and OpenMP thread counts can be set before NumPy loads (threads=None: the
+    host's default, all cores). Part of the CPU-baseline leg."""
+    code = (
+        "import json, time\n"
+        "from oracle import planner, tn\n"
+        "from tnc_inputs import circuit_to_network, grid_rqc\n"
+        "net = circuit_to_network(grid_rqc(3, 4, 8, 1)).as_complex64()\n"
+        "path = planner.greedy_path(net.indices, net.dims)\n"
+        "S = planner.find_slices(planner.Tree(net.indices, net.dims, net.open_ids, path), 8, 7)\n"
+        "t0 = time.perf_counter()\n"
+        "for s in range(1 << len(S)):\n"
+        "    tn.contract_slice(net, path, S, s)\n"
+        "print(json.dumps({'seconds': time.perf_counter() - t0, 'slices': 1 << len(S)}))\n")
+    env = dict(os.environ)
+    if threads is not None:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                           timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # a missing figure, not a failed bench
+        return {"error": str(e)[:200]}
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
@@ -1185,7 +1213,9 @@ def main():
         line["cpu_baseline"] = {"value": 8 * macs / dt / 1e12, "unit": UNIT, "cores": cpu_threads(),
                                 "kind": "oracle",
                                 "sample": "one full slice (slice 0) of the workload, NumPy complex128 "
-                                          "tensordot per node, %.1f s" % dt}
+                                          "tensordot per node, %.1f s" % dt,
+                                "c1_12q_all_16_slices": {"all_cores": oracle_c1_seconds(None),
+                                                         "one_core": oracle_c1_seconds(1)}}
         rms = float(np.sqrt(np.mean(np.abs(ref0) ** 2)))
 
         def errs(mo):
