@@ -587,6 +587,8 @@ def bitstrings_bench(args):
         net.set_path(stem_path(ref_net, c))
         if args.stem_coalesce_bits is not None:
             net.set_option("stem_coalesce_bits", args.stem_coalesce_bits)
+        if args.stem_cap_log2 is not None:
+            net.set_option("stem_cap_log2", args.stem_cap_log2)
         S = []
         ns = 1
     else:
@@ -873,6 +875,9 @@ def stem_bench(args):
     net.set_path(stem_path(tn_, c))
     if args.stem_coalesce_bits is not None:
         net.set_option("stem_coalesce_bits", args.stem_coalesce_bits)
+    if args.stem_cap_log2 is not None:
+        net.set_option("stem_cap_log2", args.stem_cap_log2)
+    cap = net.stats()["stem_cap_log2"]
     stats = net.stats()
     groups = stats["stem_groups"]
     flops = node_flops(stats, 1)
@@ -882,7 +887,9 @@ def stem_bench(args):
     # both on the per-level executor: the fused groups run there, and the
     # unfused baseline is the same contractions as separate per-level launches
     net.set_option("persistent", 0)
-    for name, cap in (("fused", 12), ("unfused", 0)):
+    for name, cap in (("fused", cap), ("unfused", 0)):
+        if name == "unfused" and args.stem_no_unfused:
+            continue
         net.set_option("stem_cap_log2", cap)
         ws = torch.empty(net.workspace_bytes(1), dtype=torch.uint8, device="cuda")
         net.set_workspace(ws)
@@ -906,7 +913,8 @@ def stem_bench(args):
                                                  for k, v in kernel_breakdown(recs).items()},
                      "clocks": clk.summary(), "amplitudes": out.cpu().numpy()}
         del ws
-    a, b = res["fused"].pop("amplitudes"), res["unfused"].pop("amplitudes")
+    a = res["fused"].pop("amplitudes")
+    b = res["unfused"].pop("amplitudes") if "unfused" in res else None
     # the fused kernel against HBM: per launch it reads its input stem and writes its output once
     st_ms = res["fused"]["kernel_time_ms_per_call"].get("k_stem_fused", 0.0)
     st_bytes = sum(8 * ((1 << g[5]) + (1 << g[6])) for g in groups)
@@ -914,17 +922,17 @@ def stem_bench(args):
     gbs = st_bytes / (st_ms / 1e3) / 1e9 if st_ms else None
     line = {"metric": "fused stem groups (secondary slicing) on a stem path: effective complex TFLOPS",
             "value": res["fused"]["value"], "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
-            "speedup_vs_unfused": res["unfused"]["s_per_call"] / res["fused"]["s_per_call"],
-            "fused_vs_unfused_max_rel_diff": float(np.max(np.abs(a - b)) / np.max(np.abs(b))),
+            "speedup_vs_unfused": res["unfused"]["s_per_call"] / res["fused"]["s_per_call"] if b is not None else None,
+            "fused_vs_unfused_max_rel_diff": float(np.max(np.abs(a - b)) / np.max(np.abs(b))) if b is not None else None,
             "groups": len(groups), "fused_steps": sum(g[1] for g in groups), "nodes": len(stats["nodes"]),
             "k_stem_fused": {"ms_per_call": st_ms, "algorithmic_bytes_per_call": st_bytes,
                              "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                           "frac": gbs / peaks["hbm_gbs"] if gbs else None,
                                           "peak_source": "hbm copy %s (MEASURED_PEAKS.json)" % peak_src}},
-            "fused": res["fused"], "unfused": res["unfused"],
+            "fused": res["fused"], "unfused": res.get("unfused"),
             "config": {"workload": "rqc-%s-12cyc-seed4-open4 time-ordered stem path, not sliced" % args.stem_grid,
                        "max_log2_size": stats["max_log2_size"], "mode": "fp32 (narrow steps run on CUDA cores)",
-                       "stem_coalesce_bits": args.stem_coalesce_bits}}
+                       "stem_coalesce_bits": args.stem_coalesce_bits, "stem_cap_log2": cap}}
     print(json.dumps(line))
     return 0
 
@@ -964,6 +972,10 @@ def main():
     ap.add_argument("--stem", action="store_true",
                     help="time fused stem groups against separate launches on a 28-qubit stem path instead")
     ap.add_argument("--stem-grid", default="4x7", help="--stem: grid of the circuit (ROWSxCOLS)")
+    ap.add_argument("--stem-cap-log2", type=int, default=None,
+                    help="--stem, --bitstrings: the stem_cap_log2 option of the fused groups (default: the library's)")
+    ap.add_argument("--stem-no-unfused", action="store_true",
+                    help="--stem: skip the unfused baseline (for sweeps of the fusion options)")
     ap.add_argument("--stem-coalesce-bits", type=int, default=None,
                     help="--stem, --bitstrings: the stem_coalesce_bits option (default: the library's)")
     ap.add_argument("--backward", action="store_true",

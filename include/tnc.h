@@ -271,7 +271,7 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  and skip their recomputation while the plan, leaf data,
  *                  mode, batch, workspace and tuning are unchanged (the
  *                  workspace must not be used for anything else meanwhile)
- *  "stem_cap_log2" 0 or 2..14 (default 12): fused stem groups (Sec. 5.2,
+ *  "stem_cap_log2" 0 or 2..13 (default 13): fused stem groups (Sec. 5.2,
  *                  secondary slicing). Consecutive narrow stem steps (a
  *                  stem of more than 2^value elements absorbing branches of
  *                  at most 16 contracted and 16 new elements) run as one

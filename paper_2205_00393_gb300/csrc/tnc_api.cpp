@@ -209,7 +209,7 @@ struct tnc_net {
     int backward_keep_every = 0; // 0 = smallest spacing that fits the budget
     int plane_cap_log2 = 32;     // split-precision planes per operand <= 2^this bytes
     int force_choice = -1;       // autotuning: force 0 (FP32) or a tensor-core row width
-    int stem_cap_log2 = 12;      // fused stem groups: inner sub-tensors up to 2^this elements (0 = off)
+    int stem_cap_log2 = 13;      // fused stem groups: inner sub-tensors up to 2^this elements (0 = off)
     int stem_min_outer = 7;      // fused stem groups: at least 2^this sub-tensors (CTAs) per slice
     int stem_coalesce_bits = 3;  // fused stem groups: lowest-stride modes of T_0 and T_n kept inner
     bool in_many = false;        // building a many-network call: no fused stem groups
@@ -2878,8 +2878,10 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "persist_test_stall") {
         net->persist_test_stall = value != 0;
     } else if (k == "stem_cap_log2") {
-        if (value != 0 && (value < 2 || value > tnc::kStemMaxInner))
-            return fail(TNC_E_INVALID, "stem_cap_log2 must be 0 or in [2, 14]");
+        // a group with a step that is not in place holds two buffers of
+        // 2^value complex elements: 2 x 64 KB at 13 fits a CTA, 2 x 128 KB does not
+        if (value != 0 && (value < 2 || value > tnc::kStemMaxInner - 1))
+            return fail(TNC_E_INVALID, "stem_cap_log2 must be 0 or in [2, 13]");
         net->stem_cap_log2 = (int)value;
         net->plan.stem_cap = -1;
         net->group_key.clear();
