@@ -48,8 +48,8 @@ def test_fig9_secondary_slicing_group(libtnc):
 def test_groups_on_a_stem_path(libtnc):
     """On the time-ordered stem path of a 20-qubit circuit every contraction
     is a narrow stem step; groups cover consecutive steps, each with at least
-    2^7 outer assignments and inner sub-tensors within the default 2^12, most
-    of them several steps long."""
+    2^7 outer assignments and inner sub-tensors within the default cap
+    (2^13 elements), most of them several steps long."""
     from paper_2205_00393_gb300 import Network
     from tnc_inputs import circuit_to_network, grid_rqc, stem_path
     c = grid_rqc(4, 5, 10, 11, n_open=4)
@@ -61,7 +61,8 @@ def test_groups_on_a_stem_path(libtnc):
     assert groups, "expected fused groups on a stem path"
     firsts = [g[0] for g in groups]
     assert len(set(firsts)) == len(firsts)
+    assert st["stem_cap_log2"] == 13
     for first, n, nu, inner, per_slice, _, _ in groups:
-        assert n >= 1 and nu >= 7 and inner <= 12 and per_slice == 0
+        assert n >= 1 and nu >= 7 and inner <= 13 and per_slice == 0
     assert sum(1 for g in groups if g[1] >= 4) >= len(groups) // 2
     assert sum(g[1] for g in groups) >= len(st["nodes"]) // 2
