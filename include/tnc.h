@@ -278,10 +278,13 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  launch when every tensor of the sub-path, without the stem
  *                  modes that live through all of its steps, fits 2^value
  *                  elements: one CTA per assignment of those long-lived modes
- *                  keeps its sub-tensor in shared memory across the steps. A
- *                  narrow step that starts no longer group runs alone in the
- *                  same kernel. 0 turns fusion off: every contraction then
- *                  runs on the GEMM kernels (tnc_contract_many never fuses)
+ *                  keeps its sub-tensor in shared memory across the steps
+ *                  (a group with a step whose contracted and new elements
+ *                  differ holds two buffers and stays within 2^min(value, 12)
+ *                  elements). A narrow step that starts no longer group runs
+ *                  alone in the same kernel. 0 turns fusion off: every
+ *                  contraction then runs on the GEMM kernels
+ *                  (tnc_contract_many never fuses)
  *  "stem_min_outer_log2" 0..30 (default 7): a fused group needs at least
  *                  2^value sub-tensors (CTAs) per slice
  *  "stem_coalesce_bits" 0..6 (default 3): the lowest-stride modes of a

@@ -424,6 +424,8 @@ bool stem_step(const tnc_net* net, const NodePlan& np) {
            (int)net->plan.layout[np.A].size() > net->stem_cap_log2;
 }
 
+constexpr int kStemTwoBufferCap = 12;
+
 void plan_stems(tnc_net* net) {
     Plan& P = net->plan;
     const int cap = std::min(net->stem_cap_log2, tnc::kStemMaxInner);
@@ -473,7 +475,16 @@ void plan_stems(tnc_net* net) {
                 if (!Us.count(m)) ++inner;
             mx = std::max(mx, inner);
         }
-        if (mx > cap || (int)U.size() < net->stem_min_outer || U.size() > 30) return false;
+        // a step that is not in place (contracted and new elements differ) makes
+        // the kernel hold two buffers of the inner size: such groups stay within
+        // 2^kStemTwoBufferCap elements, so that three CTAs still share an SM
+        bool two = false;
+        for (size_t j = i; j < i + n; ++j) {
+            const NodePlan& np = P.nodes[chain[j]];
+            two |= !(np.kb == np.nb && np.kb > 0);
+        }
+        const int lim = two ? std::min(cap, kStemTwoBufferCap) : cap;
+        if (mx > lim || (int)U.size() < net->stem_min_outer || U.size() > 30) return false;
         g = StemGroupPlan();
         g.steps.assign(chain.begin() + i, chain.begin() + i + n);
         g.in = P.nodes[chain[i]].A;
