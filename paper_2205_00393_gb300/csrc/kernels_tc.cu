@@ -774,33 +774,45 @@ __device__ __forceinline__ void split_one_block(const SplitParams& p, int64_t bl
 }
 
 // count consecutive blocks, software-pipelined (one CTA per SM runs them):
-// the asynchronous copies of blocks i + 1 and i + 2 are in flight while block
-// i is converted, through a ring of three staging tiles and offset tables.
-// Every iteration commits one copy group (empty past the last block), so
-// "all but the newest group complete" means block i has landed.
-template <int KIND, int BAR>
+// the asynchronous copies of blocks i + 1 .. i + D - 1 are in flight while
+// block i is converted, through a ring of D staging tiles and offset tables.
+// Every block slot commits one copy group (empty past the last block), so
+// "all but the newest D - 2 groups complete" means block i has landed.
+constexpr int kSplitRing = 4;
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Slot q of the ring: its staging tile at tile0 + q * tile_stride (float2)
+// and its offset tables at off0 + 384 q (128 row offsets, then 256 k offsets).
+template <int KIND, int BAR, int D>
 __device__ __forceinline__ void split_blocks(const SplitParams& p, int64_t block0, int count, int z, int64_t slice0,
-                                             float2* const (&tile)[3], int64_t* const (&roff)[3],
-                                             int64_t* const (&koff)[3]) {
+                                             float2* tile0, int tile_stride, int64_t* off0) {
+    static_assert(D >= 2, "at least one block ahead");
+    auto tile = [&](int q) { return tile0 + q * tile_stride; };
+    auto roff = [&](int q) { return off0 + 384 * q; };
+    auto koff = [&](int q) { return off0 + 384 * q + 128; };
     const SplitGeom g = split_geom(p);
     const float2* src = p.src.ptr + z * p.src.batch_stride + slice_offset(p.src, slice0 + z);
-    split_offsets(p, g, block0, roff[0], koff[0]);
-    if (count > 1) split_offsets(p, g, block0 + 1, roff[1], koff[1]);
+    for (int q = 0; q < D - 1 && q < count; ++q) split_offsets(p, g, block0 + q, roff(q), koff(q));
     tc_bar<BAR>();
-    split_gather_async(p, g, src, roff[0], koff[0], tile[0]);
-    if (count > 1) split_gather_async(p, g, src, roff[1], koff[1], tile[1]);
-    else asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int i = 0; i < count; ++i) {
-        const int j = i % 3, j2 = (i + 2) % 3;
-        // slot j2 held block i - 1: its copies were read before the last barrier
-        if (i + 2 < count) split_offsets(p, g, block0 + i + 2, roff[j2], koff[j2]);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        tc_bar<BAR>();  // tile[j] and block i + 2's offsets complete
-        if (i + 2 < count) split_gather_async(p, g, src, roff[j2], koff[j2], tile[j2]);
+    for (int q = 0; q < D - 1; ++q) {
+        if (q < count) split_gather_async(p, g, src, roff(q), koff(q), tile(q));
         else asm volatile("cp.async.commit_group;" ::: "memory");
-        split_convert<KIND>(p, g, block0 + i, z, tile[j]);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    for (int i = 0; i < count; ++i) {
+        const int j = i % D, jn = (i + D - 1) % D;
+        // slot jn held block i - 1: its copies were read before the last barrier
+        if (i + D - 1 < count) split_offsets(p, g, block0 + i + D - 1, roff(jn), koff(jn));
+        cp_async_wait<D - 2>();
+        tc_bar<BAR>();  // tile j and block i + D - 1's offsets complete
+        if (i + D - 1 < count) split_gather_async(p, g, src, roff(jn), koff(jn), tile(jn));
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        split_convert<KIND>(p, g, block0 + i, z, tile(j));
+    }
+    cp_async_wait<0>();
     tc_bar<BAR>();  // the tiles may be refilled after this
 }
 
@@ -938,17 +950,15 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
     const int tid = threadIdx.x, warp = tid >> 5;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
     // scratch of the task types, all at the start of the dynamic shared memory:
-    // the split's three staging tiles, then its three pairs of offset tables
+    // the split's kSplitRing staging tiles, then as many pairs of offset tables
     constexpr int kSplitTileSlot = 40 * 1024;
+    constexpr int D = kSplitRing;
     using CK = Cfg<(KIND < 0 ? 0 : KIND), 64>;  // the dynamic shared memory of the tensor-core variants
     static_assert(kSplitTileBytesMax <= kSplitTileSlot &&
-                      3 * kSplitTileSlot + 3 * (128 + 256) * 8 <= CK::STAGES * CK::STAGE_BYTES,
+                      D * kSplitTileSlot + D * (128 + 256) * 8 <= CK::STAGES * CK::STAGE_BYTES,
                   "split scratch fits the ring");
-    float2* const split_tile[3] = {reinterpret_cast<float2*>(smem), reinterpret_cast<float2*>(smem + kSplitTileSlot),
-                                   reinterpret_cast<float2*>(smem + 2 * kSplitTileSlot)};
-    int64_t* const split_off0 = reinterpret_cast<int64_t*>(smem + 3 * kSplitTileSlot);
-    int64_t* const split_roff[3] = {split_off0, split_off0 + 384, split_off0 + 768};
-    int64_t* const split_koff[3] = {split_roff[0] + 128, split_roff[1] + 128, split_roff[2] + 128};
+    float2* const split_tile0 = reinterpret_cast<float2*>(smem);
+    int64_t* const split_off0 = reinterpret_cast<int64_t*>(smem + D * kSplitTileSlot);
     double2* root_red = reinterpret_cast<double2*>(smem);
     int64_t(*root_ta)[256] = reinterpret_cast<int64_t(*)[256]>(smem + 4096);
     int64_t(*root_tb)[256] = reinterpret_cast<int64_t(*)[256]>(smem + 4096 + 5 * 256 * 8);
@@ -1015,8 +1025,8 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
             case PT_SPLIT:
                 if constexpr (TC) {
                     if (tid < 256) {
-                        split_blocks<KIND, 1>(P.split[tk.idx], tk.item, tk.count, tk.z, slice0, split_tile,
-                                              split_roff, split_koff);
+                        split_blocks<KIND, 1, D>(P.split[tk.idx], tk.item, tk.count, tk.z, slice0, split_tile0,
+                                                 kSplitTileSlot / (int)sizeof(float2), split_off0);
                         asm volatile("fence.proxy.async.global;" ::: "memory");
                     }
                 }
