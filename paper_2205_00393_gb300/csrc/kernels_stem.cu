@@ -109,22 +109,19 @@ __global__ void __launch_bounds__(NT, 4) k_stem_fused(const StemParams* __restri
         }
     const float2* src = p.in.ptr + z * p.in.batch_stride + slice_offset(p.in, s) + ib;
     {
-        // element e = tid + NT * j: the low 8 bits are this thread's, decoded once;
-        // eight loads in flight before their shared-memory stores
+        // element e = tid + NT * j: the low 8 bits are this thread's, decoded
+        // once; every element goes straight to shared memory as an 8-byte
+        // asynchronous copy, all of them in flight before the wait
         const int n_in = p.n_in, lo_bits = n_in < 8 ? n_in : 8;
         const int64_t lo = bits_dec((uint32_t)tid, p.istr, lo_bits);
         const int cnt = (1 << n_in) > NT ? (1 << n_in) / NT : 1;
-        if (tid < (1 << n_in)) {
-            for (int j0 = 0; j0 < cnt; j0 += 8) {
-                float2 v[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (j0 + q < cnt) v[q] = src[lo + bits_dec((uint32_t)(j0 + q), p.istr + 8, n_in - lo_bits)];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (j0 + q < cnt) cur[tid + NT * (j0 + q)] = v[q];
+        if (tid < (1 << n_in))
+            for (int j = 0; j < cnt; ++j) {
+                const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(cur + tid + NT * j));
+                const float2* g = src + lo + bits_dec((uint32_t)j, p.istr + 8, n_in - lo_bits);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(g) : "memory");
             }
-        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
     for (int i = 0; i < p.nsteps; ++i) {
