@@ -1,4 +1,4 @@
-// Internal interface between the host executor (tnc_api.cpp) and the CUDA
+// Internal interface between the host executors (host_*.cpp) and the CUDA
 // kernels. Not part of the public C ABI.
 //
 // Tensors are complex64 arrays whose dimensions are all 2 internally: an index
