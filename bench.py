@@ -1135,10 +1135,15 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "c64-fp32", "bf16": "c64 via 3x bf16 split, fp32 accum",
-                  "tf32": "c64 via 2x tf32 split, fp32 accum",
-                  "bf16x2": "c64 via 2x bf16 split, fp32 accum",
-                  "fp16x2": "c64 via 2x fp16 split of the 2^e-scaled operand, fp32 accum"}[args.mode],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16x3/f32", "tf32": "tf32x2/f32", "bf16x2": "bf16x2/f32",
+                  "fp16x2": "f16x2/f32"}[args.mode],
+        "arithmetic": {"fp32": "complex64 products and sums in FP32 on the CUDA cores",
+                       "bf16": "complex64 operands split into 3 BF16 parts, 6 part pairs on the tensor cores, FP32 accumulation",
+                       "tf32": "complex64 operands split into 2 TF32 parts, 3 part pairs on the tensor cores, FP32 accumulation",
+                       "bf16x2": "complex64 operands split into 2 BF16 parts, 3 part pairs on the tensor cores, FP32 accumulation",
+                       "fp16x2": "complex64 operands scaled by 2^e per row (column) and 256 of K, split into 2 FP16 parts, "
+                                 "3 part pairs on the tensor cores, FP32 accumulation"}[args.mode],
         "data": "synthetic",
         "s_per_1024_slices": T / n_sl_tot * 1024,
         "gpu_s_per_1024_slices": T * world / n_sl_tot * 1024,
