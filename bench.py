@@ -319,8 +319,9 @@ def reference_arm(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
         "data": "synthetic", "s_per_1024_slices": T / args.steps * 1024,
-        "config": {"workload": workload_name(), "slices_per_step": 1, "n_slices": 1 << len(S),
-                   "mode": "oracle-fp64"},
+        "config": {"workload": workload_name(), "n_slices": 1 << len(S), "sliced": len(S),
+                   "eq3_overhead": round(float(tree.overhead(S)), 5)},
+        "mode": "oracle-fp64", "slices_per_step": 1, "parallelism": "host CPU",
         "cpu_baseline": {"value": tflops, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                          "sample": "one full slice (all pairwise contractions) per step, NumPy complex128"},
         "e2e": {"value": tflops, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1147,10 +1148,10 @@ def main():
         "data": "synthetic",
         "s_per_1024_slices": T / n_sl_tot * 1024,
         "gpu_s_per_1024_slices": T * world / n_sl_tot * 1024,
-        "config": {"workload": workload_name(), "mode": args.mode, "slices_per_step": B,
-                   "n_slices": n_slices, "sliced": len(S), "eq3_overhead": stats["overhead"],
-                   "l2": "working set > L2 (1 GiB intermediates), no flush",
-                   "parallelism": "slices sharded over ranks" if world > 1 else "1 GPU"},
+        "config": {"workload": workload_name(), "n_slices": n_slices, "sliced": len(S),
+                   "eq3_overhead": round(float(stats["overhead"]), 5)},
+        "mode": args.mode, "slices_per_step": B, "l2": "working set > L2 (1 GiB intermediates), no flush",
+        "parallelism": "slices sharded over ranks" if world > 1 else "1 GPU",
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launches,
         "executor": executor_of(by_kind),
         "sharded_sum_check": shard_check, "peaks_probed": probed,
