@@ -659,6 +659,55 @@ def bitstrings_bench(args):
     return 0
 
 
+def persist_demo(args):
+    """The two executors on a mid-size network: the 24-qubit 4x6 grid circuit
+    (12 cycles, seed 3, last 4 qubits open), greedy path sliced to 2^20
+    elements, 8 slices per call in split BF16 (tensor-core and FP32
+    contractions mixed). Times one persistent launch per call against one
+    launch per tree level."""
+    import torch
+    from tnc_inputs import circuit_to_network, grid_rqc
+    from paper_2205_00393_gb300 import Network
+    torch.cuda.set_device(0)
+    c = grid_rqc(4, 6, 12, 3, n_open=4)
+    net = Network.from_tn(circuit_to_network(c).as_complex64())
+    net.set_path(net.greedy_path())
+    net.set_slices(net.find_slices(20, 7))
+    stats = net.stats()
+    mode = MODES[args.mode]
+    B = args.slices_per_step
+    stream = torch.cuda.current_stream()
+    out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
+    res = {}
+    for name, p in (("persistent", 1), ("per_level", 0)):
+        net.set_option("persistent", p)
+        for i in range(args.warmup):
+            net.contract((i * B) % net.n_slices, (i * B) % net.n_slices + B, mode, out=out)
+        torch.cuda.synchronize()
+        net.set_timing(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.steps):
+            lo = (i * B) % net.n_slices
+            net.contract(lo, lo + B, mode, out=out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        T = ev0.elapsed_time(ev1) / 1e3 / args.steps
+        recs, nl = net.last_timings()
+        net.set_timing(False)
+        res[name] = {"ms_per_call": 1e3 * T, "value": node_flops(stats, B) / T / 1e12,
+                     "kernels_per_call": nl / args.steps,
+                     "kernel_ms_per_call": {KIND_NAMES.get(k, str(k)): v["ms"] / args.steps
+                                            for k, v in kernel_breakdown(recs).items()}}
+    line = {"metric": "persistent vs per-level executor: effective complex TFLOPS", "unit": UNIT,
+            "value": res["persistent"]["value"], "mode": args.mode, "steps": args.steps, "warmup": args.warmup,
+            "speedup_persistent_vs_per_level": res["per_level"]["ms_per_call"] / res["persistent"]["ms_per_call"],
+            "executors": res,
+            "config": {"workload": "rqc-4x6-12cyc-seed3-open4-t20", "slices_per_step": B, "n_slices": net.n_slices}}
+    print(json.dumps(line))
+    return 0
+
+
 def c53_bench(args):
     """53-qubit lattice (6x9 grid minus one site), 20 cycles (seed 3), one
     amplitude, sliced to 2^30-element intermediates: a fixed subset of slices
@@ -966,6 +1015,8 @@ def main():
                     help="42-qubit gradient configuration (adjoint vs finite differences) instead")
     ap.add_argument("--many", action="store_true",
                     help="time the batched uneven workload of many circuits instead")
+    ap.add_argument("--persist-demo", action="store_true",
+                    help="time the persistent executor against per-level launches on a 24-qubit network instead")
     ap.add_argument("--bitstrings", type=int, default=0,
                     help="time B correlated bitstrings of the 30-qubit workload (leaf variants) instead")
     ap.add_argument("--bitstring-path", default="stem", choices=["stem", "greedy"],
@@ -988,12 +1039,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.slices_per_step is None:
-        plain = not (args.grad42 or args.c53 or args.many or args.backward or args.single_node or args.stem)
-        args.slices_per_step = 4 if plain else 2
+        plain = not (args.grad42 or args.c53 or args.many or args.backward or args.single_node or args.stem or
+                     args.persist_demo)
+        args.slices_per_step = 4 if plain else (8 if args.persist_demo else 2)
     if args.mode is None:
         if args.grad42:
             args.mode = "fp32"
-        elif args.single_node or args.backward or args.many or args.impl == "reference":
+        elif args.single_node or args.backward or args.many or args.persist_demo or args.impl == "reference":
             args.mode = "bf16"
         else:
             args.mode = "fp16x2"
@@ -1011,6 +1063,8 @@ def main():
         return stem_bench(args)
     if args.bitstrings:
         return bitstrings_bench(args)
+    if args.persist_demo:
+        return persist_demo(args)
     if args.many:
         return many_bench(args)
     if args.grad42:
