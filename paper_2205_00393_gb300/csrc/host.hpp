@@ -141,6 +141,7 @@ struct DeviceWorkList {
     size_t n_counters = 0;
     double cmacs = 0.0;     // complex multiply-accumulates of one launch
     double tc_cmacs = 0.0;  // the part of them on the tensor cores
+    bool tensor_tasks = false;  // any split, tensor-core tile or K-split task (else the FP32 variant runs it)
     ~DeviceWorkList() {
         if (mem) cudaFree(mem);
     }

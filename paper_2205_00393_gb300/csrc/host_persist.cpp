@@ -378,6 +378,7 @@ tnc_status wl_upload(const WorkList& W, DeviceWorkList& D, int* err, uint64_t wa
     D.n_counters = W.counters.size();
     D.cmacs = W.cmacs;
     D.tc_cmacs = W.tc_cmacs;
+    D.tensor_tasks = !W.split.empty() || !W.tc.empty() || !W.kred.empty();
     return TNC_OK;
 }
 
@@ -392,7 +393,9 @@ cudaError_t wl_launch(const DeviceWorkList& D, int mode, int64_t slice0, const i
     p.rs0 = rs0;
     p.prof = prof;
     p.out0 = reinterpret_cast<double2*>(out0);
-    return tnc::launch_persist(p, mode, s);
+    // a list without tensor-core work runs on the FP32 variant: two 256-thread
+    // CTAs per SM instead of one CTA holding the tensor-core pipeline
+    return tnc::launch_persist(p, D.tensor_tasks ? mode : TNC_FP32, s);
 }
 
 // Host-side check of a work list before its first launch: every range a task
