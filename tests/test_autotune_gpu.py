@@ -2,7 +2,6 @@
 fills the process-wide table (choices 0 = FP32, 32 / 64 = tensor-core row
 width); results after tuning still match the FP32 path."""
 
-import numpy as np
 import pytest
 
 from .test_parity_tc_gpu import _three_leaf

@@ -4,7 +4,6 @@ MMA thread waits on is never completed). The kernel must record
 TNC_E_TIMEOUT, release its tensor memory and return; the context must stay
 usable, and the next contraction must be correct."""
 
-import numpy as np
 import pytest
 
 from oracle import tn

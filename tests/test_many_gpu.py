@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from tnc_inputs import circuit_to_network, grid_rqc
-from oracle import planner, tn
+from oracle import tn
 
 from ._util import floored_rel_err
 

@@ -5,7 +5,6 @@ algebraic identities, the simulator through a Kronecker-product construction
 of the full unitary and through closed-form states (GHZ, identity, Clifford).
 """
 
-import itertools
 
 import numpy as np
 import pytest

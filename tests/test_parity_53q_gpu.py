@@ -3,7 +3,6 @@ element intermediates: one slice in split BF16 and split TF32 on the tensor
 cores against the GPU FP32 path (the FP64 oracle cannot run at this size:
 2^44 complex multiply-accumulates and 8 GiB tensors per slice)."""
 
-import numpy as np
 import pytest
 
 from tnc_inputs import circuit_to_network, lattice_53q_rqc

@@ -2,7 +2,6 @@
 sliced to 2^27-element intermediates), one slice against the FP64 oracle,
 in the launch configuration the benchmark times."""
 
-import numpy as np
 import pytest
 
 from tnc_inputs import circuit_to_network, grid_rqc

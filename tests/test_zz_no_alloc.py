@@ -34,7 +34,7 @@ def _pair(seed, m_log2, n_log2, k_log2):
 def test_noalloc_matches_contract(libtnc, m_log2, n_log2, k_log2):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2205_00393_gb300 import Network, TNCError
+    from paper_2205_00393_gb300 import Network
     a, b = _pair(1234 + k_log2, m_log2, n_log2, k_log2)
     M, N, K = a.shape[0], b.shape[1], a.shape[1]
     # the same contraction through tnc_contract: indices m (dim M), k (K), n (N)
