@@ -662,8 +662,9 @@ def persist_demo(args):
     """The two executors on a mid-size network: the 24-qubit 4x6 grid circuit
     (12 cycles, seed 3, last 4 qubits open), greedy path sliced to 2^20
     elements, 8 slices per call in split BF16 (tensor-core and FP32
-    contractions mixed). Times one persistent launch per call against one
-    launch per tree level."""
+    contractions mixed). Times one persistent launch per call, with per-entry
+    dependencies and with the level chain, against one launch per tree
+    level."""
     import torch
     from tnc_inputs import circuit_to_network, grid_rqc
     from paper_2205_00393_gb300 import Network
@@ -678,8 +679,9 @@ def persist_demo(args):
     stream = torch.cuda.current_stream()
     out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
     res = {}
-    for name, p in (("persistent", 1), ("per_level", 0)):
+    for name, p, deps in (("persistent", 1, 1), ("persistent_level_chain", 1, 0), ("per_level", 0, 1)):
         net.set_option("persistent", p)
+        net.set_option("persist_deps", deps)
         for i in range(args.warmup):
             net.contract((i * B) % net.n_slices, (i * B) % net.n_slices + B, mode, out=out)
         torch.cuda.synchronize()
@@ -701,6 +703,8 @@ def persist_demo(args):
     line = {"metric": "persistent vs per-level executor: effective complex TFLOPS", "unit": UNIT,
             "value": res["persistent"]["value"], "mode": args.mode, "steps": args.steps, "warmup": args.warmup,
             "speedup_persistent_vs_per_level": res["per_level"]["ms_per_call"] / res["persistent"]["ms_per_call"],
+            "speedup_deps_vs_level_chain": (res["persistent_level_chain"]["ms_per_call"] /
+                                            res["persistent"]["ms_per_call"]),
             "executors": res,
             "config": {"workload": "rqc-4x6-12cyc-seed3-open4-t20", "slices_per_step": B, "n_slices": net.n_slices}}
     print(json.dumps(line))

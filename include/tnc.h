@@ -245,9 +245,13 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
  * of every fused stem group for the current options, and
  * "tc_cuts": per split mode, [node index, A row-panel bits, B row-panel bits,
  * K-panel bits, K-split bits] of every tensor-core-eligible contraction for
- * the last batch size ("tc_cut_batch"); "persistent" (the option) and
- * "timed_persist_tc_cmacs": the complex multiply-accumulates that timed
- * persistent launches (since tnc_set_timing) ran on the tensor cores. */
+ * the last batch size ("tc_cut_batch"); "persistent" and "persist_deps" (the
+ * options); "last_persist_deps": 1 if the last persistent tnc_contract ran
+ * with per-entry dependencies; "last_workspace": [bytes of the reusing
+ * layout, bytes without reuse (0 if not considered)] for the last
+ * tnc_contract batch; "timed_persist_tc_cmacs": the complex
+ * multiply-accumulates that timed persistent launches (since
+ * tnc_set_timing) ran on the tensor cores. */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 
 /* Tuning options of the tensor-core GEMM (no effect on results):
@@ -299,8 +303,8 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  split blocks, 128 x 128 tensor-core tiles, K-split
  *                  reductions, root chunks and sums) are taken in list order
  *                  from an atomic ticket and each waits, on device counters,
- *                  for the tasks that produce its inputs and for the previous
- *                  tree level. Results equal the per-level launches' up to
+ *                  for the tasks that produce its inputs (see
+ *                  "persist_deps"). Results equal the per-level launches' up to
  *                  the order of FP32 additions in a K split; other calls, and
  *                  0, use one launch per tree level. 2: the persistent
  *                  executor when the per-level launches of a batch would
@@ -310,6 +314,18 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  TB/s: launch-bound calls), else one launch per level
  *                  (for tnc_contract_many: over the whole call, unless every
  *                  network has 1)
+ *  "persist_deps"  0 or 1 (default 1): with 1, a tnc_contract batch run by
+ *                  the persistent executor gives every tensor and temporary
+ *                  of the batch bytes of their own for the launch when that
+ *                  fits (the caller's workspace, or an own one of at most the
+ *                  larger of 1 GiB and the reusing layout's size), and a task
+ *                  of batch entry z then waits only on entry z of what it
+ *                  reads, so tree levels of different entries overlap. With
+ *                  0, or when it does not fit, the workspace reuses the bytes
+ *                  of dead tensors and every task also waits for the whole
+ *                  previous tree level. tnc_workspace_bytes reports the
+ *                  reusing layout; tnc_stats "last_workspace" gives both
+ *                  sizes for the last call. tnc_contract_many always reuses.
  *  "persist_wait_ms" 0..600000 (default 0 = 10 s): bound of one dependency
  *                  wait of the persistent executor; a wait that runs out
  *                  stops every CTA and tnc_check_device reports TNC_E_TIMEOUT

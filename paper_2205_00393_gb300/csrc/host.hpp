@@ -109,6 +109,7 @@ struct Arena {
     int64_t root_scratch_off = -1; // FP64 partials or FP32 per-slice root
     int64_t peak = 0;
     int64_t batch = 1;             // slices per batch the per-slice temporaries are sized for
+    bool reuse = true;             // memory of dead tensors reused by later levels
 };
 
 // Level groups: nodes whose inputs are ready at the same time run in one
@@ -234,6 +235,10 @@ struct tnc_net {
     int persistent = 2;  // 0 per-level launches, 1 persistent kernel, 2 automatic choice
     uint64_t persist_wait_ns = 0;    // bound of one dependency wait (0: 10 s)
     int persist_test_stall = 0;      // tests only: one task waits on a counter nothing signals
+    int persist_deps = 1;            // per-slice node dependencies (no level chain) when their arena fits
+    bool last_persist_deps = false;  // whether the last persistent call ran with them
+    size_t last_arena_bytes[2] = {0, 0};  // last tnc_contract batch: reusing arena, arena without reuse (0: not needed)
+    mutable std::map<std::string, Arena> arena_cache;  // plan_arena results by their inputs
     std::map<std::string, std::unique_ptr<DeviceWorkList>> worklists;
     double timed_persist_tc_cmacs = 0.0;  // tensor-core share of the timed persistent launches
     unsigned long long* d_prof = nullptr;  // "persist_profile": per task type time, count, wait
@@ -287,7 +292,10 @@ struct WorkList {
     }
     // tree-level chain of the network being emitted: tasks wait on the
     // previous level's counter and also count down the current level's;
-    // level[i] is task i's level number within its network
+    // level[i] is task i's level number within its network. Without the chain
+    // (chain false: an arena without reuse, every tensor written once per
+    // launch) tasks wait only on the counters of their own inputs.
+    bool chain = true;
     int lvl_prev = -1, lvl_cur = -1, lvl_no = -1;
     std::vector<int> level;
     bool no_slot = false;  // a task had no wait slot left for the level chain
@@ -303,10 +311,10 @@ struct WorkList {
         t.wait[1] = w1;
         t.wait[2] = w2;
         t.signal = signal;
-        t.signal2 = lvl_cur;
+        t.signal2 = chain ? lvl_cur : -1;
         // a slot left free takes the previous level (a task of a level waits
         // for the whole level before it: the workspace reuses memory across levels)
-        if (lvl_prev >= 0) {
+        if (chain && lvl_prev >= 0) {
             bool have = false;
             for (int q = 0; q < 3; ++q) have |= t.wait[q] == lvl_prev;
             for (int q = 0; q < 3 && !have; ++q)
@@ -316,12 +324,13 @@ struct WorkList {
                 }
             no_slot |= !have;
         }
-        if (lvl_cur >= 0) ++counters[lvl_cur];
+        if (chain && lvl_cur >= 0) ++counters[lvl_cur];
         tasks.push_back(t);
         level.push_back(lvl_no);
     }
     void begin_level() {
         ++lvl_no;
+        if (!chain) return;
         lvl_prev = lvl_cur;
         lvl_cur = new_counter(0);
     }
@@ -346,7 +355,8 @@ int64_t full_planes_bytes(int mode, int rb, int kb, int64_t batch);
 TcCut tc_cut(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch);
 int64_t tc_bytes_a(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch);
 int64_t tc_bytes_b(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch);
-Arena plan_arena(const tnc_net* net, int64_t nb, int mode);
+Arena plan_arena(const tnc_net* net, int64_t nb, int mode, bool reuse = true);
+std::string group_key_of(const tnc_net* net, int mode, int64_t nb, const char* ws, bool reuse);
 int64_t cut_batch(const Arena& ar, const NodePlan& np, int64_t b);
 tnc::Operand operand(const tnc_net* net, const Arena& ar, char* ws, int v, int64_t nb);
 tnc::GemmParams gemm_params(const tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int64_t nb);

@@ -9,34 +9,58 @@ namespace tnc_host {
 // A work list is the whole computation of one launch: every contraction of a
 // slice batch (and, in the first batch of a call, the slice-invariant ones)
 // broken into tasks, in level order so that every task only waits on tasks
-// before it (see kernels.h). Per node, one counter counts the tasks of its
-// last stage; a task waits on the counters of the nodes that produce its
-// inputs in the same launch.
-
-
+// before it (see kernels.h). A stage of a contraction (operand splits, tiles,
+// K-split sums) counts its tasks down on counters; a task waits on the
+// counters of the stage before it and of the contractions producing its
+// inputs. On an arena that reuses memory across levels, each stage has one
+// counter and a level chain makes every task wait for the whole level before
+// it (its inputs included). On an arena without reuse, each stage has one
+// counter per batch entry and a task of entry z waits only on entry z of what
+// it reads, so the levels of different entries overlap.
 
 constexpr int kSplitBlocksPerTask = 16;
 
+// Counters of a stage of per_z tasks per batch entry over nz entries: one per
+// entry without the level chain, else one for the stage. of(c, z) names entry
+// z's (a single counter serves every entry).
+static std::vector<int> wl_stage(WorkList& W, int64_t per_z, int nz) {
+    std::vector<int> c;
+    if (W.chain) c.push_back(W.new_counter((int)(per_z * nz)));
+    else
+        for (int z = 0; z < nz; ++z) c.push_back(W.new_counter((int)per_z));
+    return c;
+}
+static int of(const std::vector<int>& c, int z) { return c.size() == 1 ? c[0] : c[z]; }
+
+// The counter a task of entry z waits on before reading tensor v: the last
+// stage of v's contraction when this launch produces v and no level chain
+// orders it; -1 otherwise (a leaf, a cached invariant, or the chain waits).
+static int wl_input(const WorkList& W, const std::map<int, std::vector<int>>& ctr, int v, int z) {
+    if (W.chain) return -1;
+    auto it = ctr.find(v);
+    return it == ctr.end() ? -1 : of(it->second, z);
+}
+
 // Tasks of one non-root contraction np for batch b into W; ctr maps a tensor
-// produced in this launch to its counter. False if the contraction needs row
-// or K panels (not run by the persistent executor).
+// produced in this launch to the counters of its last stage. False if the
+// contraction needs row or K panels (not run by the persistent executor).
 bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b, int mode, int netidx, WorkList& W,
-             std::map<int, int>& ctr) {
+             std::map<int, std::vector<int>>& ctr) {
     const Plan& P = net->plan;
     tnc::GemmParams g = gemm_params(net, ar, ws, np, b);
     g.C = reinterpret_cast<float2*>(ws + ar.off[np.v]);
     g.c_batch_stride = np.per_slice ? tensor_bytes(P, np.v) / 8 : 0;
-    // inputs come from earlier tree levels, which the level chain already waits for
-    const int wa = -1, wb = -1;
     W.cmacs += std::ldexp(1.0, np.mb + np.nb + np.kb) * b;
     const int choice = shape_choice(net, mode, np.mb, np.nb, np.kb, np.is_root);
     if (!choice) {
         const int gi = (int)W.gemm.size();
         W.gemm.push_back(g);
         const int64_t tiles = tnc::gemm_f32_tiles(np.mb, np.nb);
-        const int c = W.new_counter((int)(tiles * b));
+        const std::vector<int> c = wl_stage(W, tiles, b);
         for (int z = 0; z < b; ++z)
-            for (int64_t t = 0; t < tiles; ++t) W.task(tnc::PT_GEMM, gi, t, z, netidx, 0, wa, wb, -1, c);
+            for (int64_t t = 0; t < tiles; ++t)
+                W.task(tnc::PT_GEMM, gi, t, z, netidx, 0, wl_input(W, ctr, np.A, z), wl_input(W, ctr, np.B, z), -1,
+                       of(c, z));
         ctr[np.v] = c;
         return true;
     }
@@ -46,6 +70,8 @@ bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
     const size_t i = np.v - net->n_leaves;
     char* pa = ws + ar.planes_a[i];
     char* pb = ws + ar.planes_b[i];
+    // an operand with neither batch stride nor sliced indices is the same for
+    // every entry (a leaf or a slice-invariant tensor): split once
     const bool a_shared = b > 1 && g.A.batch_stride == 0 && g.A.n_sl == 0;
     const bool b_shared = b > 1 && g.B.batch_stride == 0 && g.B.n_sl == 0;
     int8_t* sexp_a = nullptr;
@@ -54,8 +80,8 @@ bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
         sexp_a = reinterpret_cast<int8_t*>(pa + plane_data_bytes(mode, g.mb, g.kb, b));
         sexp_b = reinterpret_cast<int8_t*>(pb + plane_data_bytes(mode, g.nb, g.kb, b));
     }
-    auto split = [&](const tnc::Operand& src, int rb, const int64_t* rs, const int64_t* ks, void* dst, int8_t* sexp,
-                     int nz, int wsrc) {
+    auto split = [&](const tnc::Operand& src, int src_v, int rb, const int64_t* rs, const int64_t* ks, void* dst,
+                     int8_t* sexp, int nz) {
         tnc::SplitParams sp{};
         sp.src = src;
         sp.rb = rb;
@@ -65,20 +91,20 @@ bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
         sp.dst = dst;
         sp.sexp = sexp;
         const int64_t blocks = tnc::tc_split_prepare(sp);
-        if (blocks <= 0) return -2;
+        if (blocks <= 0) return std::vector<int>();
         const int si = (int)W.split.size();
         W.split.push_back(sp);
         const int64_t per = (blocks + kSplitBlocksPerTask - 1) / kSplitBlocksPerTask;
-        const int c = W.new_counter((int)(per * nz));
+        const std::vector<int> c = wl_stage(W, per, nz);
         for (int z = 0; z < nz; ++z)
             for (int64_t q = 0; q < blocks; q += kSplitBlocksPerTask)
-                W.task(tnc::PT_SPLIT, si, q, z, netidx,
-                       (int)std::min<int64_t>(kSplitBlocksPerTask, blocks - q), wsrc, -1, -1, c);
+                W.task(tnc::PT_SPLIT, si, q, z, netidx, (int)std::min<int64_t>(kSplitBlocksPerTask, blocks - q),
+                       wl_input(W, ctr, src_v, z), -1, -1, of(c, z));
         return c;
     };
-    const int ca = split(g.A, g.mb, g.am, g.ak, pa, sexp_a, a_shared ? 1 : b, wa);
-    const int cb = split(g.B, g.nb, g.bn, g.bk, pb, sexp_b, b_shared ? 1 : b, wb);
-    if (ca == -2 || cb == -2) return false;
+    const std::vector<int> ca = split(g.A, np.A, g.mb, g.am, g.ak, pa, sexp_a, a_shared ? 1 : b);
+    const std::vector<int> cb = split(g.B, np.B, g.nb, g.bn, g.bk, pb, sexp_b, b_shared ? 1 : b);
+    if (ca.empty() || cb.empty()) return false;
     tnc::TcGemmParams tp{};
     tp.mb = g.mb;
     tp.nb = g.nb;
@@ -103,9 +129,9 @@ bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
     const int ti = (int)W.tc.size();
     W.tc.push_back(nd);
     const int64_t tiles = tnc::tc_node_tiles(tp);
-    const int ct = W.new_counter((int)(tiles * b));
+    const std::vector<int> ct = wl_stage(W, tiles, b);
     for (int z = 0; z < b; ++z)
-        for (int64_t t = 0; t < tiles; ++t) W.task(tnc::PT_TC, ti, t, z, netidx, 0, ca, cb, -1, ct);
+        for (int64_t t = 0; t < tiles; ++t) W.task(tnc::PT_TC, ti, t, z, netidx, 0, of(ca, z), of(cb, z), -1, of(ct, z));
     if (!cut.ks) {
         ctr[np.v] = ct;
         return true;
@@ -123,20 +149,19 @@ bool wl_node(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
     const int ki = (int)W.kred.size();
     W.kred.push_back(kp);
     const int64_t chunks = (kp.mn2 + 16383) / 16384;
-    const int ck = W.new_counter((int)(chunks * b));
+    const std::vector<int> ck = wl_stage(W, chunks, b);
     for (int z = 0; z < b; ++z)
-        for (int64_t q = 0; q < chunks; ++q) W.task(tnc::PT_KRED, ki, q, z, netidx, 0, ct, -1, -1, ck);
+        for (int64_t q = 0; q < chunks; ++q) W.task(tnc::PT_KRED, ki, q, z, netidx, 0, of(ct, z), -1, -1, of(ck, z));
     ctr[np.v] = ck;
     return true;
 }
 
 // Tasks of the final contraction of network netidx for batch b: FP64 chunk
 // sums then their ordered sum into out (at most 64 outputs), or an FP32 root
-// tensor then its FP64 slice sum.
+// tensor then its FP64 slice sum. The sum waits for every entry.
 bool wl_root(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b, int netidx, double* out, WorkList& W,
-             std::map<int, int>& ctr) {
+             std::map<int, std::vector<int>>& ctr) {
     const Plan& P = net->plan;
-    const int wa = -1, wb = -1;  // the level chain waits for the inputs
     tnc::GemmParams g = gemm_params(net, ar, ws, np, b);
     tnc::PermParams pp{};
     pp.obits = P.obits;
@@ -157,7 +182,9 @@ bool wl_root(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
         W.acc.push_back(ap);
         const int cr = W.new_counter(b * np.chunks);
         for (int z = 0; z < b; ++z)
-            for (int c = 0; c < np.chunks; ++c) W.task(tnc::PT_ROOT, ri, c, z, netidx, ai, wa, wb, -1, cr);
+            for (int c = 0; c < np.chunks; ++c)
+                W.task(tnc::PT_ROOT, ri, c, z, netidx, ai, wl_input(W, ctr, np.A, z), wl_input(W, ctr, np.B, z), -1,
+                       cr);
         const int cdone = W.new_counter(1);
         W.task(tnc::PT_ACC, ai, 0, 0, netidx, 0, cr, -1, -1, cdone);
         return true;
@@ -169,7 +196,8 @@ bool wl_root(tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int b,
     const int64_t tiles = tnc::gemm_f32_tiles(np.mb, np.nb);
     const int cg = W.new_counter((int)(tiles * b));
     for (int z = 0; z < b; ++z)
-        for (int64_t t = 0; t < tiles; ++t) W.task(tnc::PT_GEMM, gi, t, z, netidx, 0, wa, wb, -1, cg);
+        for (int64_t t = 0; t < tiles; ++t)
+            W.task(tnc::PT_GEMM, gi, t, z, netidx, 0, wl_input(W, ctr, np.A, z), wl_input(W, ctr, np.B, z), -1, cg);
     tnc::SumTaskParams st{};
     st.sp.src.ptr = g.C;
     st.sp.src.batch_stride = g.c_batch_stride;
@@ -228,8 +256,9 @@ void level_cost(tnc_net* net, int mode, int64_t b, bool with_inv, double* launch
 // the per-slice levels and the final contraction.
 bool wl_network(tnc_net* net, const Arena& ar, char* ws, int b, int mode, bool with_inv, int netidx, double* out,
                 WorkList& W) {
-    std::map<int, int> ctr;
+    std::map<int, std::vector<int>> ctr;
     const Plan& P = net->plan;
+    W.chain = ar.reuse;
     W.lvl_prev = W.lvl_cur = W.lvl_no = -1;
     for (bool per : {false, true}) {
         if (!per && !with_inv) continue;

@@ -316,8 +316,25 @@ int64_t tc_bytes_b(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t
     return tc_cut(net, mode, mb, nb, kb, batch).b_bytes;
 }
 
-// First-fit simulation of the workspace for a batch of `nb` slices.
-Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
+static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool reuse);
+
+// First-fit simulation of the workspace for a batch of `nb` slices, cached
+// by everything it reads: the plan, the kernel choices and the options that
+// shape groups and tensor-core temporaries.
+Arena plan_arena(const tnc_net* net, int64_t nb, int mode, bool reuse) {
+    const std::string key = std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string(reuse ? 1 : 0) +
+                            ":" + std::to_string(net->plan.version) + ":" + std::to_string(g_tune_version) + ":" +
+                            std::to_string(net->force_choice) + ":" + std::to_string(net->tc_row_bytes) + ":" +
+                            std::to_string(net->tuning ? 1 : 0) + ":" + std::to_string(net->in_many ? 1 : 0) + ":" +
+                            std::to_string(net->stem_cap_log2) + ":" + std::to_string(net->plan.stem_cap) + ":" +
+                            std::to_string(net_plane_cap_log2(net));
+    auto it = net->arena_cache.find(key);
+    if (it != net->arena_cache.end()) return it->second;
+    if (net->arena_cache.size() >= 64) net->arena_cache.clear();
+    return net->arena_cache[key] = plan_arena_uncached(net, nb, mode, reuse);
+}
+
+static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool reuse) {
     const Plan& P = net->plan;
     const tnc::Tree& T = *net->tree;
     Arena ar;
@@ -338,7 +355,11 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
         top = std::max(top, off + len);
         return off;
     };
-    auto release = [&](int64_t off) { used.erase(off); };
+    // without reuse every tensor and temporary keeps its bytes for the whole
+    // launch, so tasks of different levels may run at the same time
+    auto release = [&](int64_t off) {
+        if (reuse) used.erase(off);
+    };
     auto tc_planes = [&](const NodePlan& np, int64_t b) {
         const size_t i = np.v - net->n_leaves;
         ar.planes_a[i] = alloc(tc_bytes_a(net, mode, np.mb, np.nb, np.kb, b));
@@ -394,6 +415,7 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode) {
     }
     ar.peak = top;
     ar.batch = nb;
+    ar.reuse = reuse;
     return ar;
 }
 
@@ -632,12 +654,18 @@ std::vector<Group> level_groups(const tnc_net* net, int mode, bool per_slice) {
 
 // Build (or reuse) the level groups and upload their parameter table for this
 // plan, mode, batch and workspace.
+// Key of the launch groups (and persistent work lists) of a call: they address
+// the workspace at the offsets of its arena.
+std::string group_key_of(const tnc_net* net, int mode, int64_t nb, const char* ws, bool reuse) {
+    return std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string((uintptr_t)ws) + ":" +
+           std::to_string(net->plan.version) + ":" + std::to_string(g_tune_version) + ":" +
+           std::to_string(net->force_choice) + ":" + std::to_string(net->tuning ? 1 : 0) + ":" +
+           std::to_string(stem_fusion(net) ? net->stem_cap_log2 : 0) + ":" + std::to_string(net->plane_cap_log2) +
+           ":" + std::to_string(reuse ? 1 : 0);
+}
+
 tnc_status ensure_groups(tnc_net* net, const Arena& ar, char* ws, int mode, int64_t nb, cudaStream_t s) {
-    std::string key = std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string((uintptr_t)ws) +
-                      ":" + std::to_string(net->plan.version) + ":" + std::to_string(g_tune_version) + ":" +
-                      std::to_string(net->force_choice) + ":" + std::to_string(net->tuning ? 1 : 0) + ":" +
-                      std::to_string(stem_fusion(net) ? net->stem_cap_log2 : 0) + ":" +
-                      std::to_string(net->plane_cap_log2);
+    const std::string key = group_key_of(net, mode, nb, ws, ar.reuse);
     if (key == net->group_key) return TNC_OK;
     // the persistent work lists address this arena: built again on next use
     net->worklists.clear();

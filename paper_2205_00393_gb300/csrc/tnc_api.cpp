@@ -313,22 +313,52 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
         ws = (char*)net->ws_own;
     }
     net->last_batch = nb;
-    const Arena ar = plan_arena(net, nb, mode);
     CUDA_TRY(cudaMemsetAsync(net->d_err, 0, sizeof(int), s));
 
-    if ((st = ensure_groups(net, ar, ws, mode, nb, s)) != TNC_OK) return st;
-    const std::string ikey = net->group_key + "|" + std::to_string(net->leaf_version);
     // persistent executor: one launch per batch of slices, the slice-invariant
-    // contractions in the first one (unless cached). Every batch's work list is
-    // prepared before the first launch, so a call that it cannot run falls back
-    // to the launches below as a whole.
+    // contractions in the first one (unless cached). Its tasks wait only on
+    // their own inputs when the arena without memory reuse fits: the given
+    // workspace, or an own one of at most the larger of 1 GiB and what the
+    // reusing arena needs.
     bool use_persist = persist_eligible(net);
+    Arena ar_flat;
+    bool deps = false;
+    net->last_arena_bytes[0] = (size_t)plan_arena(net, nb, mode).peak;
+    net->last_arena_bytes[1] = 0;
+    if (use_persist && net->persist_deps) {
+        ar_flat = plan_arena(net, nb, mode, false);
+        net->last_arena_bytes[1] = (size_t)ar_flat.peak;
+        const size_t cap = net->ws_user ? net->ws_user_bytes : std::max<size_t>(net->last_arena_bytes[0], (size_t)1 << 30);
+        deps = (size_t)ar_flat.peak <= cap;
+    }
+    const bool grow = deps && !net->ws_user && net->ws_own_bytes < (size_t)ar_flat.peak;
     if (use_persist && net->persistent == 2) {
-        const bool inv_cached = net->cache_invariants && net->inv_key == ikey;
+        const std::string k = group_key_of(net, mode, nb, ws, !deps) + "|" + std::to_string(net->leaf_version);
+        const bool inv_cached = !grow && net->cache_invariants && net->inv_key == k;
         double launches = 0, seconds = 0;
         level_cost(net, mode, nb, !inv_cached, &launches, &seconds);
         use_persist = seconds < kPersistAutoSecondsPerLaunch * std::max(launches, 1.0);
     }
+    deps = deps && use_persist;
+    if (deps && grow) {  // a failed allocation keeps the reusing arena
+        void* p = nullptr;
+        if (cudaMalloc(&p, (size_t)ar_flat.peak) == cudaSuccess) {
+            if (net->ws_own) CUDA_TRY(cudaFree(net->ws_own));
+            net->ws_own = p;
+            net->ws_own_bytes = (size_t)ar_flat.peak;
+            ws = (char*)net->ws_own;
+        } else {
+            (void)cudaGetLastError();
+            deps = false;
+        }
+    }
+    const Arena ar = deps ? ar_flat : plan_arena(net, nb, mode);
+
+    if ((st = ensure_groups(net, ar, ws, mode, nb, s)) != TNC_OK) return st;
+    const std::string ikey = net->group_key + "|" + std::to_string(net->leaf_version);
+    // Every batch's work list is prepared before the first launch, so a call
+    // that the persistent executor cannot run falls back to the launches
+    // below as a whole.
     if (use_persist) {
         const bool inv_cached = net->cache_invariants && net->inv_key == ikey;
         std::vector<std::pair<DeviceWorkList*, int64_t>> rounds;
@@ -349,6 +379,7 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
                 CUDA_TRY(timed_end(net, s));
             }
             net->inv_key = net->cache_invariants ? ikey : std::string();
+            net->last_persist_deps = deps;
             return TNC_OK;
         }
     }
@@ -531,6 +562,9 @@ tnc_status tnc_set_option(tnc_net_t net, const char* key, int64_t value) {
     } else if (k == "persistent") {
         if (value < 0 || value > 2) return fail(TNC_E_INVALID, "persistent must be 0, 1 or 2");
         net->persistent = (int)value;
+    } else if (k == "persist_deps") {
+        if (value != 0 && value != 1) return fail(TNC_E_INVALID, "persist_deps must be 0 or 1");
+        net->persist_deps = (int)value;
     } else if (k == "persist_wait_ms") {
         if (value < 0 || value > 600000) return fail(TNC_E_INVALID, "persist_wait_ms must be in [0, 600000]");
         net->persist_wait_ns = (uint64_t)value * 1000000ull;
@@ -684,7 +718,9 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
     } else {
         o << ",\"plan_error\":\"" << perr << "\"";
     }
-    o << ",\"persistent\":" << net->persistent << ",\"timed_persist_tc_cmacs\":" << std::setprecision(17)
+    o << ",\"persistent\":" << net->persistent << ",\"persist_deps\":" << net->persist_deps
+      << ",\"last_persist_deps\":" << (net->last_persist_deps ? 1 : 0) << ",\"last_workspace\":["
+      << net->last_arena_bytes[0] << "," << net->last_arena_bytes[1] << "],\"timed_persist_tc_cmacs\":" << std::setprecision(17)
       << net->timed_persist_tc_cmacs;
     if (net->d_prof) {  // [run ns, tasks, wait ns] per task type since tnc_set_timing
         unsigned long long h[tnc::kPersistProfWords];

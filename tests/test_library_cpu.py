@@ -197,10 +197,10 @@ def test_option_validation():
     good = {"tc_row_bytes": [32, 64], "tc_group_m": [1, 64],
             "tc_plane_cap_log2": [16, 40], "backward_keep_every": [0, 64], "cache_invariants": [0, 1],
             "tc_spin_limit": [0, 1 << 20], "tc_test_stall": [0], "stem_cap_log2": [0, 2, 13],
-            "persistent": [0, 1, 2]}
+            "persistent": [0, 1, 2], "persist_deps": [0, 1]}
     bad = {"tc_row_bytes": [16, 128], "tc_group_m": [0, 65], "tc_pair": [0, 1], "tc_multicast": [0, 1],
            "tc_plane_cap_log2": [15, 41], "backward_keep_every": [-1, 65], "tc_spin_limit": [-1], "no_such_key": [1],
-           "stem_cap_log2": [1, 14], "persistent": [-1, 3]}
+           "stem_cap_log2": [1, 14], "persistent": [-1, 3], "persist_deps": [-1, 2]}
     for k, vals in good.items():
         for v in vals:
             net.set_option(k, v)

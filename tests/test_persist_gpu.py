@@ -2,9 +2,11 @@
 per SM takes tasks (FP32 tiles, operand splits, tensor-core tiles, K-split
 reductions, final-contraction chunks and their ordered sums) from a device
 work list, each waiting on counters of the contractions that produce its
-inputs. It runs the same arithmetic in the same order as the separate
-launches, so results are bit-identical to them, and they match the FP64
-oracle. A dependency wait that runs out reports TNC_E_TIMEOUT without a
+inputs: per batch entry when every tensor of the batch has bytes of its own
+("persist_deps", the default when that fits), else per stage behind a chain
+of tree levels. Either way it runs the same arithmetic in the same order as
+the separate launches, so results are bit-identical to them, and they match
+the FP64 oracle. A dependency wait that runs out reports TNC_E_TIMEOUT without a
 fault (no task ever signals the counter it waits on) and leaves the context
 usable."""
 
@@ -28,14 +30,18 @@ def lib(libtnc):
     return libtnc
 
 
-def _run(net, lo, hi, mode, persistent):
+def _run(net, lo, hi, mode, persistent, deps=1, expect=None):
     net.set_option("persistent", persistent)
+    net.set_option("persist_deps", deps)
     net.set_timing(True)
     got = net.contract(lo, hi, mode).cpu().numpy()
     recs, n = net.last_timings()
     net.set_timing(False)
     net.check_device()
-    return got, [r["kind"] for r in recs]
+    kinds = [r["kind"] for r in recs]
+    if 9 in kinds:
+        assert net.stats()["last_persist_deps"] == (deps if expect is None else expect)
+    return got, kinds
 
 
 def _grid(rows, cols, cycles, seed, n_open, t):
@@ -50,10 +56,11 @@ def _grid(rows, cols, cycles, seed, n_open, t):
     return ref_net, net, path, S
 
 
+@pytest.mark.parametrize("deps", [1, 0])
 @pytest.mark.parametrize("mode", [0, 2, 4])
-def test_persistent_equals_launches_12q(lib, mode):
+def test_persistent_equals_launches_12q(lib, mode, deps):
     ref_net, net, path, S = _grid(3, 4, 8, 1, 0, 8)
-    per, kinds = _run(net, 0, net.n_slices, mode, 1)
+    per, kinds = _run(net, 0, net.n_slices, mode, 1, deps)
     assert kinds == [9], kinds  # one launch per batch (all 16 slices in one batch)
     leg, kinds0 = _run(net, 0, net.n_slices, mode, 0)
     assert 9 not in kinds0
@@ -62,38 +69,59 @@ def test_persistent_equals_launches_12q(lib, mode):
     assert floored_rel_err(per, ref, 12) <= (1e-5 if mode == 0 else 1e-4)
 
 
+@pytest.mark.parametrize("deps", [1, 0])
 @pytest.mark.parametrize("mode", [2, 4, 1, 0])
-def test_persistent_equals_launches_24q_tensor_cores(lib, mode):
+def test_persistent_equals_launches_24q_tensor_cores(lib, mode, deps):
     """24-qubit 4x6 grid, 12 cycles, 4 open qubits, t = 20: tensor-core
     contractions (splits, tiles) and small FP32 ones; slices [1, 5) in one
     batch, then [0, 3) and [3, 7) with invariants cached."""
     ref_net, net, path, S = _grid(4, 6, 12, 3, 4, 20)
-    per, kinds = _run(net, 1, 5, mode, 1)
+    per, kinds = _run(net, 1, 5, mode, 1, deps)
     leg, _ = _run(net, 1, 5, mode, 0)
     assert kinds.count(9) >= 1 and set(kinds) == {9}, kinds
     assert np.array_equal(per, leg)
     ref = tn.contract(ref_net, path, S, slices=range(1, 5))
     assert floored_rel_err(per, ref, 24) <= (1e-5 if mode == 0 else 1e-4)
     net.set_option("cache_invariants", 1)
-    a, _ = _run(net, 0, 3, mode, 1)
-    b, _ = _run(net, 3, 7, mode, 1)
+    a, _ = _run(net, 0, 3, mode, 1, deps)
+    b, _ = _run(net, 3, 7, mode, 1, deps)
     net.set_option("cache_invariants", 0)
     c, _ = _run(net, 0, 7, mode, 0)
     assert float(np.max(np.abs(a + b - c)) / np.max(np.abs(c))) <= 1e-12
 
 
+@pytest.mark.parametrize("deps", [1, 0])
 @pytest.mark.parametrize("mode", [4, 2])
-def test_persistent_k_splits(lib, mode):
+def test_persistent_k_splits(lib, mode, deps):
     """(2^7, 2^7, 2^16): few output tiles, K split over CTAs; the persistent
     executor runs the split tiles and the K-split reduction as tasks."""
     from paper_2205_00393_gb300 import Network
     net_ref = _three_leaf(401, 7, 7, 16, False)
     net = Network.from_tn(net_ref)
     net.set_path([(0, 1), (2, 3)])
-    per, kinds = _run(net, 0, 1, mode, 1)
+    per, kinds = _run(net, 0, 1, mode, 1, deps)
     leg, kinds0 = _run(net, 0, 1, mode, 0)
     assert kinds == [9] and 7 in kinds0
     assert np.array_equal(per, leg)
+
+
+def test_persistent_deps_need_flat_workspace(lib):
+    """A caller workspace that holds the reusing layout of a batch but not
+    every tensor of it at once: the persistent executor keeps the level
+    chain; one that holds them all gives the per-entry dependencies. Both
+    equal the per-level launches bit for bit."""
+    ref_net, net, path, S = _grid(4, 6, 12, 3, 4, 20)
+    leg, _ = _run(net, 0, 4, 4, 0)
+    _run(net, 0, 4, 4, 1, 1)
+    reuse, flat = net.stats()["last_workspace"]
+    assert flat > reuse > 0
+    for size, deps in ((reuse, 0), (flat, 1)):
+        ws = torch.empty((size + 255) // 256 * 256, dtype=torch.uint8, device="cuda")
+        net.set_workspace(ws)
+        got, kinds = _run(net, 0, 4, 4, 1, 1, expect=deps)
+        assert kinds == [9]
+        assert np.array_equal(got, leg)
+    net.set_workspace(None)
 
 
 def test_persistent_wait_timeout(lib):
