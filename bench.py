@@ -711,6 +711,60 @@ def persist_demo(args):
     return 0
 
 
+def executor_sweep(args):
+    """Both executors on grid circuits from 12 to 30 qubits (greedy paths
+    sliced to 2^8 .. 2^27-element intermediates), FP32 and split FP16x2, 1, 4
+    and 16 slices per call: ms per call of each (CUDA events over a run of
+    calls after 3 warm-up calls) beside the library's estimate of the
+    per-level work (the automatic choice's input: per-level launches and
+    estimated seconds). One JSON line per configuration."""
+    import torch
+    from tnc_inputs import circuit_to_network, grid_rqc
+    from paper_2205_00393_gb300 import Network
+    torch.cuda.set_device(0)
+    specs = [(3, 4, 8, 1, 0, 8), (4, 4, 10, 2, 2, 12), (4, 5, 12, 3, 3, 16), (4, 6, 12, 3, 4, 20),
+             (5, 5, 12, 4, 4, 20), (5, 6, 12, 5, 4, 22), (5, 6, 14, 2, 6, 24), (5, 6, 14, 2, 6, 27)]
+    stream = torch.cuda.current_stream()
+    for (r, c, cyc, seed, n_open, t) in specs:
+        net = Network.from_tn(circuit_to_network(grid_rqc(r, c, cyc, seed, n_open=n_open)).as_complex64())
+        net.set_path(net.greedy_path())
+        net.set_slices(net.find_slices(t, 7))
+        out = torch.empty(net.n_out, dtype=torch.complex128, device="cuda")
+        for mode in (0, 4):
+            for B in (1, 4, 16):
+                if B > net.n_slices or (t >= 24 and B > 1) or (t >= 27 and mode == 0):
+                    continue
+                ms, deps = {}, None
+                for name, p in (("persistent", 1), ("per_level", 0)):
+                    net.set_option("persistent", p)
+                    calls = 12 if t < 24 else 4
+                    for _ in range(3):
+                        net.contract(0, B, mode, out=out)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for i in range(calls):
+                        lo = (i * B) % net.n_slices
+                        net.contract(lo, lo + B, mode, out=out)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    net.check_device()
+                    ms[name] = e0.elapsed_time(e1) / calls
+                    if p == 1:
+                        deps = net.stats()["last_persist_deps"]
+                net.set_option("persistent", 2)
+                launches, est_s = net.stats()["level_cost"][str(mode)]
+                print(json.dumps({"metric": "executor sweep: ms per call", "workload":
+                                  "rqc-%dx%d-%dcyc-seed%d-open%d-t%d" % (r, c, cyc, seed, n_open, t),
+                                  "mode": {v: k for k, v in MODES.items()}[mode], "slices_per_call": B,
+                                  "per_level_launches": launches, "estimated_us_per_launch": 1e6 * est_s / max(launches, 1),
+                                  "ms_persistent": ms["persistent"], "ms_per_level": ms["per_level"],
+                                  "per_level_over_persistent": ms["per_level"] / ms["persistent"],
+                                  "persist_deps": deps}), flush=True)
+        del net
+    return 0
+
+
 def c53_bench(args):
     """53-qubit lattice (6x9 grid minus one site), 20 cycles (seed 3), one
     amplitude, sliced to 2^30-element intermediates: a fixed subset of slices
@@ -1018,6 +1072,8 @@ def main():
                     help="42-qubit gradient configuration (adjoint vs finite differences) instead")
     ap.add_argument("--many", action="store_true",
                     help="time the batched uneven workload of many circuits instead")
+    ap.add_argument("--executor-sweep", action="store_true",
+                    help="time both executors on grid circuits of 12 to 30 qubits (calibrates the automatic choice)")
     ap.add_argument("--persist-demo", action="store_true",
                     help="time the persistent executor against per-level launches on a 24-qubit network instead")
     ap.add_argument("--bitstrings", type=int, default=0,
@@ -1068,6 +1124,8 @@ def main():
         return bitstrings_bench(args)
     if args.persist_demo:
         return persist_demo(args)
+    if args.executor_sweep:
+        return executor_sweep(args)
     if args.many:
         return many_bench(args)
     if args.grad42:

@@ -231,7 +231,7 @@ tnc_status tnc_check_device(tnc_net_t net, void* stream);
  * persistent executor can run each of them, every round of slice batches is
  * instead ONE launch of the work-list kernel holding all networks' tasks,
  * ordered by tree level (level L of every network before level L + 1 of any);
- * each network waits only on its own levels. A dependency wait that runs out
+ * each network's tasks wait only on its own tasks ("persist_deps"). A dependency wait that runs out
  * is then reported through the first network's tnc_check_device.
  * Every network needs at most 64 outputs and at least two tensors. A network
  * may appear once. Destroying a network drops the cached sequences using it. */
@@ -308,10 +308,11 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  the order of FP32 additions in a K split; other calls, and
  *                  0, use one launch per tree level. 2: the persistent
  *                  executor when the per-level launches of a batch would
- *                  carry less than 60 us of work each on average (a
+ *                  carry less than 0.1 us of work each on average (a
  *                  contraction estimated at the larger of its flops at 300
  *                  TFLOP/s and its 8 (MK + KN + MN) bytes per slice at 6
- *                  TB/s: launch-bound calls), else one launch per level
+ *                  TB/s: calls of tiny contractions only, where launch gaps
+ *                  are all the time), else one launch per level
  *                  (for tnc_contract_many: over the whole call, unless every
  *                  network has 1)
  *  "persist_deps"  0 or 1 (default 1): with 1, a tnc_contract batch run by
@@ -325,7 +326,9 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  *                  of dead tensors and every task also waits for the whole
  *                  previous tree level. tnc_workspace_bytes reports the
  *                  reusing layout; tnc_stats "last_workspace" gives both
- *                  sizes for the last call. tnc_contract_many always reuses.
+ *                  sizes for the last call. tnc_contract_many does the same
+ *                  per network, its own workspace capped at the larger of
+ *                  256 MiB and the reusing layout.
  *  "persist_wait_ms" 0..600000 (default 0 = 10 s): bound of one dependency
  *                  wait of the persistent executor; a wait that runs out
  *                  stops every CTA and tnc_check_device reports TNC_E_TIMEOUT

@@ -171,9 +171,54 @@ tnc_status many_build(ManyCall& mc, cudaStream_t s) {
         }
         mc.nb[i] = nb;
         mc.wss[i] = ws;
+    }
+    // persistent executor when every network has it on: forced, or the
+    // automatic choice over the whole call
+    bool pers = true, forced = true;
+    for (tnc_net* net : mc.nets) {
+        pers &= net->persistent != 0;
+        forced &= net->persistent == 1;
+    }
+    if (pers && !forced) {
+        double launches = 0, seconds = 0;
+        for (int i = 0; i < n; ++i) level_cost(mc.nets[i], mc.mode, mc.nb[i], true, &launches, &seconds);
+        pers = seconds < kPersistAutoSecondsPerLaunch * std::max(launches, 1.0);
+    }
+    for (int i = 0; i < n; ++i) {
+        tnc_net* net = mc.nets[i];
+        const int64_t nb = mc.nb[i];
+        // a network whose tensors all fit at once (its own workspace of at most
+        // the larger of 256 MiB and the reusing layout) takes per-entry
+        // dependencies in the persistent lists
+        Arena ar = plan_arena(net, nb, mc.mode);
+        net->last_arena_bytes[0] = (size_t)ar.peak;
+        net->last_arena_bytes[1] = 0;
+        net->last_persist_deps = false;
+        if (pers && net->persist_deps) {
+            const Arena flat = plan_arena(net, nb, mc.mode, false);
+            net->last_arena_bytes[1] = (size_t)flat.peak;
+            const size_t cap = net->ws_user ? net->ws_user_bytes : std::max<size_t>(ar.peak, (size_t)256 << 20);
+            bool fits = (size_t)flat.peak <= cap;
+            if (fits && !net->ws_user && net->ws_own_bytes < (size_t)flat.peak) {
+                void* p = nullptr;
+                if (cudaMalloc(&p, (size_t)flat.peak) == cudaSuccess) {
+                    if (net->ws_own) CUDA_TRY(cudaFree(net->ws_own));
+                    net->ws_own = p;
+                    net->ws_own_bytes = (size_t)flat.peak;
+                    mc.wss[i] = (char*)p;
+                } else {
+                    (void)cudaGetLastError();
+                    fits = false;
+                }
+            }
+            if (fits) {
+                ar = flat;
+                net->last_persist_deps = true;
+            }
+        }
         net->inv_key.clear();
-        mc.arenas[i] = plan_arena(net, nb, mc.mode);
-        if ((st = ensure_groups(net, mc.arenas[i], ws, mc.mode, nb, s)) != TNC_OK) return st;
+        mc.arenas[i] = ar;
+        if ((st = ensure_groups(net, mc.arenas[i], mc.wss[i], mc.mode, nb, s)) != TNC_OK) return st;
         max_inv = std::max(max_inv, (int)net->groups.inv.size());
         max_ps = std::max(max_ps, (int)net->groups.ps.size());
         mc.max_nb = std::max<int>(mc.max_nb, (int)nb);
@@ -285,20 +330,10 @@ tnc_status many_build(ManyCall& mc, cudaStream_t s) {
     CUDA_TRY(up(mc.d_perms, perms.data(), perms.size() * sizeof(tnc::PermParams)));
     CUDA_TRY(up(mc.d_outs, outs.data(), outs.size() * sizeof(double2*)));
     CUDA_TRY(cudaStreamSynchronize(s));
-    // persistent executor (when every network has it on): per round one work
-    // list with every network's tasks, levels interleaved; slice ids per
-    // network come from the round's row of the device table d_rs0. A network
-    // it cannot run keeps the whole call on the merged level launches.
-    bool pers = true, forced = true;
-    for (tnc_net* net : mc.nets) {
-        pers &= net->persistent != 0;
-        forced &= net->persistent == 1;
-    }
-    if (pers && !forced) {  // automatic choice over the whole call
-        double launches = 0, seconds = 0;
-        for (int i = 0; i < n; ++i) level_cost(mc.nets[i], mc.mode, mc.nb[i], true, &launches, &seconds);
-        pers = seconds < kPersistAutoSecondsPerLaunch * std::max(launches, 1.0);
-    }
+    // persistent executor: per round one work list with every network's
+    // tasks, levels interleaved; slice ids per network come from the round's
+    // row of the device table d_rs0. A network it cannot run keeps the whole
+    // call on the merged level launches.
     for (int r = 0; r < R && pers; ++r) {
         WorkList W;
         for (int i = 0; i < n && pers; ++i) {
@@ -324,7 +359,10 @@ tnc_status many_build(ManyCall& mc, cudaStream_t s) {
             return st;
         mc.wls.push_back(std::move(D));
     }
-    if (!pers) mc.wls.clear();
+    if (!pers) {
+        mc.wls.clear();
+        for (tnc_net* net : mc.nets) net->last_persist_deps = false;
+    }
     return TNC_OK;
 }
 
@@ -356,7 +394,7 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
             << (uintptr_t)outs_c128[i] << ":" << (uintptr_t)net->ws_user << ":" << net->ws_user_bytes << ":"
             << net->persistent << ":" << net->persist_wait_ns << ":" << net->plane_cap_log2 << ":" << g_tune_version
             << ":" << net->force_choice << ":" << net->tc_group_m << ":" << net->tc_spin_limit << ":"
-            << net->tc_row_bytes << ":" << (uintptr_t)net->d_prof;
+            << net->tc_row_bytes << ":" << (uintptr_t)net->d_prof << ":" << net->persist_deps;
     }
     tnc_status st;
     // device copies of leaf data must be current before a cached sequence replays

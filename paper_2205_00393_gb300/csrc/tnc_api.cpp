@@ -325,6 +325,7 @@ tnc_status tnc_contract(tnc_net_t net, int64_t lo, int64_t hi, int mode, double*
     bool deps = false;
     net->last_arena_bytes[0] = (size_t)plan_arena(net, nb, mode).peak;
     net->last_arena_bytes[1] = 0;
+    net->last_persist_deps = false;
     if (use_persist && net->persist_deps) {
         ar_flat = plan_arena(net, nb, mode, false);
         net->last_arena_bytes[1] = (size_t)ar_flat.peak;
@@ -689,6 +690,16 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
         // how each tensor-core-eligible contraction is cut up in the split
         // modes, for the last batch size (1 before any call)
         const int64_t cb = net->last_batch > 0 ? net->last_batch : 1;
+        // the automatic executor choice's estimate for that batch, invariants
+        // included: [per-level launches, estimated seconds] per mode
+        o << ",\"level_cost\":{";
+        for (int mode = TNC_FP32; mode <= TNC_SPLIT_FP16X2; ++mode) {
+            double launches = 0, seconds = 0;
+            level_cost(net, mode, cb, true, &launches, &seconds);
+            o << (mode ? "," : "") << "\"" << mode << "\":[" << launches << "," << seconds
+              << "]";
+        }
+        o << "}";
         o << ",\"tc_cut_batch\":" << cb << ",\"tc_cuts\":{";
         const int cut_modes[4] = {TNC_SPLIT_TF32, TNC_SPLIT_BF16, TNC_SPLIT_BF16X2, TNC_SPLIT_FP16X2};
         for (int mi = 0; mi < 4; ++mi) {

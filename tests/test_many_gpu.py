@@ -44,9 +44,12 @@ def _launches_of_replay(nets, ranges, mode, outs, stream):
     return n
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("persistent,deps", [(0, 1), (1, 1), (1, 0)])
 @pytest.mark.parametrize("mode", [0, 2, 4])
-def test_many_matches_single_and_oracle(libtnc, mode, persistent):
+def test_many_matches_single_and_oracle(libtnc, mode, persistent, deps):
+    """persistent 1 with deps 1: every circuit's tasks wait only on their own
+    inputs per batch entry; deps 0: on the whole previous level of their
+    circuit."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2205_00393_gb300 import contract_many
@@ -54,6 +57,7 @@ def test_many_matches_single_and_oracle(libtnc, mode, persistent):
     nets = [c[2] for c in cs]
     for n in nets:
         n.set_option("persistent", persistent)
+        n.set_option("persist_deps", deps)
     ranges = [(0, n.n_slices) for n in nets]
     ranges[3] = (1, nets[3].n_slices - 1)  # a partial range
     stream = torch.cuda.Stream()
@@ -64,6 +68,8 @@ def test_many_matches_single_and_oracle(libtnc, mode, persistent):
                 o.fill_(float("nan"))
             contract_many(nets, ranges, mode, outs=outs, stream=stream)
             stream.synchronize()
+            if call == 0:
+                assert [n.stats()["last_persist_deps"] for n in nets] == [persistent * deps] * len(nets)
             for (circ, ref, net, path, S), (lo, hi), o in zip(cs, ranges, outs):
                 single = net.contract(lo, hi, mode, stream=stream).cpu().numpy()
                 stream.synchronize()

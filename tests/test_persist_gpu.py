@@ -146,12 +146,18 @@ def test_persistent_wait_timeout(lib):
 def test_automatic_executor_choice(lib):
     """Default ("persistent" = 2): the 12-qubit call (16 slices, contractions
     of at most a few thousand MACs) is launch-bound and runs as one
-    persistent launch; two slices of the 30-qubit workload (contractions of
-    2^38 MACs) run one launch per tree level."""
+    persistent launch; four slices of the 24-qubit circuit (where the
+    per-level launches are faster) and two slices of the 30-qubit workload
+    (contractions of 2^38 MACs) run one launch per tree level."""
     _, net, _, _ = _grid(3, 4, 8, 1, 0, 8)
     net.set_timing(True)
     net.contract(0, net.n_slices, 2)
     assert [r["kind"] for r in net.last_timings()[0]] == [9]
+    _, mid, _, _ = _grid(4, 6, 12, 3, 4, 20)
+    mid.set_timing(True)
+    mid.contract(0, 4, 4)
+    assert 9 not in {r["kind"] for r in mid.last_timings()[0]}
+    mid.set_timing(False)
     _, big, _, _ = _grid(5, 6, 14, 2, 6, 27)
     big.set_timing(True)
     big.contract(0, 2, 4)
