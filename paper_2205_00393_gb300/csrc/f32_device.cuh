@@ -76,6 +76,13 @@ __device__ __forceinline__ void two_sum_into(float& a, float b, float& c) {
     c += e;
 }
 
+// Operand pointer of gemm_tile. Alone in a launch (BAR 0) the operands were
+// written by earlier launches and may be read through the read-only path;
+// inside the persistent executor (BAR 1) other CTAs of the same launch wrote
+// them, so the loads stay on the coherent path.
+template <int BAR> struct OperandPtr { using type = const float2* __restrict__; };
+template <> struct OperandPtr<1> { using type = const float2*; };
+
 // One 64x64 output tile `tile` of slice z (slice id slice0 + z) of the
 // contraction described by p.
 template <int BAR = 0>
@@ -92,8 +99,8 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
     const int64_t tiles_n = (N + BN - 1) / BN;
     const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
     const int64_t s = slice0 + z;
-    const float2* __restrict__ A = p.A.ptr + z * p.A.batch_stride + slice_offset(p.A, s);
-    const float2* __restrict__ B = p.B.ptr + z * p.B.batch_stride + slice_offset(p.B, s);
+    const typename OperandPtr<BAR>::type A = p.A.ptr + z * p.A.batch_stride + slice_offset(p.A, s);
+    const typename OperandPtr<BAR>::type B = p.B.ptr + z * p.B.batch_stride + slice_offset(p.B, s);
 
     if (tid < BM) rowA[tid] = (m0 + tid < M) ? bits_offset(m0 + tid, p.am, p.mb, 0) : 0;
     else if (tid < BM + BN) {

@@ -339,11 +339,12 @@ struct WorkList {
 // The automatic executor choice: the persistent kernel when the per-level
 // launches would carry less than 0.1 us of estimated work each on average.
 // The estimate is nominal (peak rates); measured on GB300, the persistent
-// kernel is ahead on calls whose every contraction is tiny (1.2-1.6x at
-// 12-16 qubits, estimates of at most 0.03 us per launch), level with the
-// per-level launches near 0.1 us, and 15-40% behind above it: there, each
-// launch already runs for tens of microseconds and the one-CTA-per-SM tasks
-// do the same work less efficiently than the separate kernels.
+// kernel is ahead on calls whose every contraction is tiny (1.3-1.8x at
+// 12-16 qubits, estimates of at most 0.03 us per launch), within about 10% of
+// the per-level launches near 0.1 us, and 6-35% behind from 0.4 us up:
+// there, each launch already runs for tens of microseconds and the
+// one-CTA-per-SM tasks do the same work less efficiently than the separate
+// kernels.
 constexpr double kPersistAutoSecondsPerLaunch = 0.1e-6;
 
 // planning, arena, level groups and launches (host_plan.cpp)

@@ -936,12 +936,13 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
-// One CTA per SM. Thread 0 takes the next task in list order, waits (bounded
-// by p.wait_ns of the global timer) until the counters it names reach zero,
-// and the CTA runs it; every thread fences its writes (and, for split planes,
-// hands them to the TMA's async proxy) before thread 0 decrements the task's
-// counter. A wait that runs out, a tensor-core wait that gives up, or an error
-// another CTA has recorded stops every CTA at its next task.
+// One CTA per SM. Thread 0 takes the next task in list order and waits
+// (bounded by p.wait_ns of the global timer) until the counters it names reach
+// zero, while the other threads stage the task's parameters; then the CTA runs
+// it. Split writers hand their planes to the TMA's async proxy; after the
+// CTA's barrier, thread 0 fences and decrements the task's counters. A wait
+// that runs out, a tensor-core wait that gives up, or an error another CTA has
+// recorded stops every CTA at its next task.
 template <int KIND, int NT_>
 __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid_constant__ PersistParams P) {
     extern __shared__ __align__(1024) uint8_t dsmem[];
@@ -983,44 +984,66 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
     const uint64_t wait_ns = P.wait_ns ? P.wait_ns : 10000000000ull;
     TcPipe pipe;
     uint64_t t_wait0 = 0, t_run0 = 0;  // thread 0, for the optional profile
+    // The current task's descriptor, and the parameter entry of an FP32 tile or
+    // a final-contraction chunk, staged in shared memory while thread 0 waits
+    // for the task's inputs: the loads leave the critical path of a dependency.
+    __shared__ PersistTask task_sm;
+    __shared__ int go_sh;  // 0 once thread 0's wait gave up
+    __shared__ __align__(16) uint64_t prm_sm[(sizeof(RootParams) + 7) / 8];
+    static_assert(sizeof(GemmParams) <= sizeof(prm_sm) && sizeof(GemmParams) % 8 == 0 &&
+                      sizeof(RootParams) % 8 == 0 && (sizeof(RootParams) + 7) / 8 <= NT_,
+                  "one 8-byte word of a parameter entry per thread");
     for (;;) {
         if (tid == 0) {
-            int t = atomicAdd(P.ticket, 1);
-            if (t < P.ntasks) {
-                const PersistTask& tk = P.tasks[t];
-                const uint64_t t0 = global_ns();
-                t_wait0 = t0;
-                for (int w = 0; w < 3 && t >= 0; ++w) {
-                    const int c = tk.wait[w];
-                    if (c < 0) continue;
-                    while (ld_acquire(P.counters + c) > 0) {
-                        if (*(volatile int*)P.err) {
-                            t = -1;
-                            break;
-                        }
-                        if (global_ns() - t0 > wait_ns) {
-                            atomicExch(P.err, kErrTimeout);
-                            t = -1;
-                            break;
-                        }
-                        __nanosleep(256);
-                    }
-                }
-                t_run0 = global_ns();
-            }
-            task_sh = t;
+            const int next = atomicAdd(P.ticket, 1);
+            task_sh = next;
+            if (next < P.ntasks) task_sm = P.tasks[next];
         }
         __syncthreads();
-        const int t = task_sh;
-        if (t < 0 || t >= P.ntasks) break;
-        __threadfence();
-        const PersistTask tk = P.tasks[t];
+        if (task_sh >= P.ntasks) break;
+        const PersistTask tk = task_sm;
+        // (not the FP32 variant's tiles: at two CTAs per SM their registers
+        // are tighter, and the staged entry cost more spills than it saved)
+        if ((TC && tk.type == PT_GEMM) || tk.type == PT_ROOT) {
+            const uint64_t* src = tk.type == PT_GEMM ? reinterpret_cast<const uint64_t*>(P.gemm + tk.idx)
+                                                     : reinterpret_cast<const uint64_t*>(P.root + tk.idx);
+            const int words = (tk.type == PT_GEMM ? (int)sizeof(GemmParams) : (int)sizeof(RootParams)) / 8;
+            if (tid < words) prm_sm[tid] = src[tid];
+        }
+        if (tid == 0) {
+            int go = 1;
+            const uint64_t t0 = global_ns();
+            t_wait0 = t0;
+            for (int w = 0; w < 3 && go; ++w) {
+                const int c = tk.wait[w];
+                if (c < 0) continue;
+                // a few polls before backing off with sleeps
+                for (int spin = 0; ld_acquire(P.counters + c) > 0; ++spin) {
+                    if (*(volatile int*)P.err) {
+                        go = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > wait_ns) {
+                        atomicExch(P.err, kErrTimeout);
+                        go = 0;
+                        break;
+                    }
+                    if (spin >= 8) __nanosleep(256);
+                }
+            }
+            t_run0 = global_ns();
+            go_sh = go;
+        }
+        // thread 0's acquire of the inputs' counters, then this barrier, orders
+        // every thread's reads of them after the producers' writes
+        __syncthreads();
+        if (!go_sh) break;
         const int64_t slice0 = P.rs0 ? P.rs0[tk.net] : P.slice0;
         switch (tk.type) {
             case PT_GEMM:
                 if (tid < 256)
-                    f32dev::gemm_tile<1>(P.gemm[tk.idx], tk.item, tk.z, slice0,
-                                         *reinterpret_cast<f32dev::GemmSmem*>(smem));
+                    f32dev::gemm_tile<1>(TC ? *reinterpret_cast<const GemmParams*>(prm_sm) : P.gemm[tk.idx], tk.item,
+                                         tk.z, slice0, *reinterpret_cast<f32dev::GemmSmem*>(smem));
                 break;
             case PT_SPLIT:
                 if constexpr (TC) {
@@ -1063,7 +1086,7 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
             } break;
             case PT_ROOT:  // count: the AccParams entry whose partials this chunk fills
                 if (tid < 256) {
-                    const RootParams& rp = P.root[tk.idx];
+                    const RootParams& rp = *reinterpret_cast<const RootParams*>(prm_sm);
                     const int R = 1 << (rp.g.mb + rp.g.nb);
                     double2* part = const_cast<double2*>(P.acc[tk.count].partials);
                     f32dev::root_chunk<1>(rp, (int)tk.item, tk.z, slice0,
@@ -1108,12 +1131,14 @@ __global__ void __launch_bounds__(NT_, KIND >= 0 ? 1 : 2) k_persist(const __grid
             default:
                 break;
         }
-        __threadfence();
         // this task's generic shared-memory stores (split tiles, GEMM operands,
         // staged outputs) before the next task's TMA writes to the same bytes
         if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
+            // the barrier, then thread 0's fence: every thread's writes of the
+            // task are visible before its counters count down
+            __threadfence();
             if (sh.abort) atomicExch(P.err, kErrTimeout);
             atomicSub(P.counters + tk.signal, 1);
             if (tk.signal2 >= 0) atomicSub(P.counters + tk.signal2, 1);
