@@ -69,7 +69,8 @@ def load_peaks():
 def kernel_traffic(kind_name, mode, cmacs_per_launch):
     """DRAM bytes per launch from the committed ncu capture, scaled by the
     launch's complex multiply-accumulates; valid only for the captured mode and
-    while the kernel source is unchanged (hash recorded beside the figure)."""
+    while the kernel's source files are unchanged (hash of their concatenation
+    recorded beside the figure)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -80,11 +81,12 @@ def kernel_traffic(kind_name, mode, cmacs_per_launch):
         rec = rec.get(mode)
     if not rec or rec.get("mode") != mode:
         return None
-    src = os.path.join(ROOT, rec["source"])
+    srcs = rec["source"] if isinstance(rec["source"], list) else [rec["source"]]
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        blob = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in srcs)
     except OSError:
         return None
+    h = hashlib.sha256(blob).hexdigest()[:16]
     return rec["bytes_per_cmac"] * cmacs_per_launch if h == rec["source_sha"] else None
 
 

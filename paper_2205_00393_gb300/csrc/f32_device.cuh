@@ -159,6 +159,9 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
         }
 
     const int64_t ntiles = (K + BK - 1) / BK;
+    // K is a power of two: below BK, the one k-tile has K nonzero rows and the
+    // zero-padded rest is skipped
+    const int kmax = K < BK ? (int)K : BK;
     gather(0);
     stage_store(0);
     bar_sync<BAR>();
@@ -167,6 +170,7 @@ __device__ __forceinline__ void gemm_tile(const GemmParams& p, int64_t tile, int
         if (t + 1 < ntiles) gather((t + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
+            if (kk >= kmax) break;
             float4 a01 = *reinterpret_cast<const float4*>(&As[st][kk][4 * ty]);
             float4 a23 = *reinterpret_cast<const float4*>(&As[st][kk][4 * ty + 2]);
             float4 b01 = *reinterpret_cast<const float4*>(&Bs[st][kk][0][2 * tx]);
