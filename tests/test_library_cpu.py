@@ -209,3 +209,31 @@ def test_option_validation():
             with pytest.raises(TNCError) as e:
                 net.set_option(k, v)
             assert e.value.status == 1, (k, v)
+
+
+def test_executor_choice_inputs_in_stats():
+    """tnc_stats carries what the automatic executor choice reads (host logic,
+    no GPU): per mode, the per-level launches of a batch and their estimated
+    seconds; the 12-qubit grid circuit's estimate is far below the 0.1 us
+    per launch under which calls run persistent, the 30-qubit workload's far
+    above. The dependency option is reported, and no contraction has run yet
+    (no workspace sizes)."""
+    from paper_2205_00393_gb300 import Network
+    from tnc_inputs import circuit_to_network, grid_rqc
+
+    def planned(r, c, cyc, seed, n_open, t):
+        net = Network.from_tn(circuit_to_network(grid_rqc(r, c, cyc, seed, n_open=n_open)).as_complex64())
+        net.set_path(net.greedy_path())
+        net.set_slices(net.find_slices(t, 7))
+        return net.stats()
+
+    small, big = planned(3, 4, 8, 1, 0, 8), planned(5, 6, 14, 2, 6, 27)
+    for st in (small, big):
+        assert sorted(st["level_cost"]) == ["0", "1", "2", "3", "4"]
+        for launches, seconds in st["level_cost"].values():
+            assert launches >= 1 and seconds > 0
+        assert st["persist_deps"] == 1 and st["last_persist_deps"] == 0 and st["last_workspace"] == [0, 0]
+    per_launch = lambda st, m: st["level_cost"][m][1] / st["level_cost"][m][0]
+    assert per_launch(small, "4") < 0.1e-6 < per_launch(big, "4")
+    # a tensor-core mode launches the operand splits too
+    assert big["level_cost"]["4"][0] > big["level_cost"]["0"][0]
