@@ -239,6 +239,7 @@ struct tnc_net {
     bool last_persist_deps = false;  // whether the last persistent call ran with them
     size_t last_arena_bytes[2] = {0, 0};  // last tnc_contract batch: reusing arena, arena without reuse (0: not needed)
     mutable std::map<std::string, Arena> arena_cache;  // plan_arena results by their inputs
+    std::map<std::string, std::pair<double, double>> cost_cache;  // level_cost results (launches, seconds)
     std::map<std::string, std::unique_ptr<DeviceWorkList>> worklists;
     double timed_persist_tc_cmacs = 0.0;  // tensor-core share of the timed persistent launches
     unsigned long long* d_prof = nullptr;  // "persist_profile": per task type time, count, wait
@@ -362,6 +363,7 @@ int64_t tc_bytes_a(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t
 int64_t tc_bytes_b(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch);
 Arena plan_arena(const tnc_net* net, int64_t nb, int mode, bool reuse = true);
 std::string group_key_of(const tnc_net* net, int mode, int64_t nb, const char* ws, bool reuse);
+std::string plan_key(const tnc_net* net, int mode, int64_t nb);
 int64_t cut_batch(const Arena& ar, const NodePlan& np, int64_t b);
 tnc::Operand operand(const tnc_net* net, const Arena& ar, char* ws, int v, int64_t nb);
 tnc::GemmParams gemm_params(const tnc_net* net, const Arena& ar, char* ws, const NodePlan& np, int64_t nb);

@@ -219,14 +219,32 @@ bool persist_eligible(tnc_net* net) {
            !net->tuning;
 }
 
+static void level_cost_uncached(tnc_net* net, int mode, int64_t b, bool with_inv, double* launches,
+                                double* seconds);
+
 // Launches and estimated seconds of one batch of b slices on the per-level
-// executor (the slice-invariant levels included when with_inv): one grouped
-// launch per level for its FP32 contractions, three per tensor-core
-// contraction (two operand splits and the GEMM), two for the final
-// contraction. A contraction's time is estimated as the larger of its flops
-// at 300 TFLOP/s and its operand and result bytes, 8 (MK + KN + MN) per
-// slice, at 6 TB/s.
+// executor (the slice-invariant levels included when with_inv), added to
+// *launches and *seconds: one grouped launch per level for its FP32
+// contractions, three per tensor-core contraction (two operand splits and the
+// GEMM), two for the final contraction. A contraction's time is estimated as
+// the larger of its flops at 300 TFLOP/s and its operand and result bytes,
+// 8 (MK + KN + MN) per slice, at 6 TB/s. Cached by plan_key, since the
+// automatic executor choice asks for it on every call.
 void level_cost(tnc_net* net, int mode, int64_t b, bool with_inv, double* launches, double* seconds) {
+    const std::string key = plan_key(net, mode, b) + (with_inv ? ":i" : ":p");
+    auto it = net->cost_cache.find(key);
+    if (it == net->cost_cache.end()) {
+        if (net->cost_cache.size() >= 64) net->cost_cache.clear();
+        double l = 0, sec = 0;
+        level_cost_uncached(net, mode, b, with_inv, &l, &sec);
+        it = net->cost_cache.emplace(key, std::make_pair(l, sec)).first;
+    }
+    *launches += it->second.first;
+    *seconds += it->second.second;
+}
+
+static void level_cost_uncached(tnc_net* net, int mode, int64_t b, bool with_inv, double* launches,
+                                double* seconds) {
     const Plan& P = net->plan;
     auto node_s = [](const NodePlan& np, double bb) {
         const double M = std::ldexp(1.0, np.mb), N = std::ldexp(1.0, np.nb), K = std::ldexp(1.0, np.kb);

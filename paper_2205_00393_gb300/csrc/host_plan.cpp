@@ -318,16 +318,21 @@ int64_t tc_bytes_b(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t
 
 static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool reuse);
 
+// Everything the level groups and the arena of a batch of nb slices depend
+// on: the plan, the kernel choices and the options that shape groups and
+// tensor-core temporaries. Key of the host-side caches below.
+std::string plan_key(const tnc_net* net, int mode, int64_t nb) {
+    return std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string(net->plan.version) + ":" +
+           std::to_string(g_tune_version) + ":" + std::to_string(net->force_choice) + ":" +
+           std::to_string(net->tc_row_bytes) + ":" + std::to_string(net->tuning ? 1 : 0) + ":" +
+           std::to_string(net->in_many ? 1 : 0) + ":" + std::to_string(net->stem_cap_log2) + ":" +
+           std::to_string(net->plan.stem_cap) + ":" + std::to_string(net_plane_cap_log2(net));
+}
+
 // First-fit simulation of the workspace for a batch of `nb` slices, cached
-// by everything it reads: the plan, the kernel choices and the options that
-// shape groups and tensor-core temporaries.
+// by plan_key.
 Arena plan_arena(const tnc_net* net, int64_t nb, int mode, bool reuse) {
-    const std::string key = std::to_string(mode) + ":" + std::to_string(nb) + ":" + std::to_string(reuse ? 1 : 0) +
-                            ":" + std::to_string(net->plan.version) + ":" + std::to_string(g_tune_version) + ":" +
-                            std::to_string(net->force_choice) + ":" + std::to_string(net->tc_row_bytes) + ":" +
-                            std::to_string(net->tuning ? 1 : 0) + ":" + std::to_string(net->in_many ? 1 : 0) + ":" +
-                            std::to_string(net->stem_cap_log2) + ":" + std::to_string(net->plan.stem_cap) + ":" +
-                            std::to_string(net_plane_cap_log2(net));
+    const std::string key = plan_key(net, mode, nb) + (reuse ? ":r" : ":f");
     auto it = net->arena_cache.find(key);
     if (it != net->arena_cache.end()) return it->second;
     if (net->arena_cache.size() >= 64) net->arena_cache.clear();
