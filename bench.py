@@ -719,7 +719,8 @@ def executor_sweep(args):
     and 16 slices per call: ms per call of each (CUDA events over a run of
     calls after 3 warm-up calls) beside the library's estimate of the
     per-level work (the automatic choice's input: per-level launches and
-    estimated seconds). One JSON line per configuration."""
+    estimated seconds) and the executor the automatic choice runs. One JSON
+    line per configuration."""
     import torch
     from tnc_inputs import circuit_to_network, grid_rqc
     from paper_2205_00393_gb300 import Network
@@ -754,7 +755,13 @@ def executor_sweep(args):
                     ms[name] = e0.elapsed_time(e1) / calls
                     if p == 1:
                         deps = net.stats()["last_persist_deps"]
+                # what the automatic choice runs for this call
                 net.set_option("persistent", 2)
+                net.set_timing(True)
+                net.contract(0, B, mode, out=out)
+                torch.cuda.synchronize()
+                auto = "persistent" if 9 in {r["kind"] for r in net.last_timings()[0]} else "per_level"
+                net.set_timing(False)
                 launches, est_s = net.stats()["level_cost"][str(mode)]
                 print(json.dumps({"metric": "executor sweep: ms per call", "workload":
                                   "rqc-%dx%d-%dcyc-seed%d-open%d-t%d" % (r, c, cyc, seed, n_open, t),
@@ -762,7 +769,8 @@ def executor_sweep(args):
                                   "per_level_launches": launches, "estimated_us_per_launch": 1e6 * est_s / max(launches, 1),
                                   "ms_persistent": ms["persistent"], "ms_per_level": ms["per_level"],
                                   "per_level_over_persistent": ms["per_level"] / ms["persistent"],
-                                  "persist_deps": deps}), flush=True)
+                                  "automatic_choice": auto, "automatic_choice_is_faster":
+                                  ms[auto] <= min(ms.values()), "persist_deps": deps}), flush=True)
         del net
     return 0
 
