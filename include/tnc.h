@@ -249,10 +249,33 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
  * options); "last_persist_deps": 1 if the last persistent tnc_contract ran
  * with per-entry dependencies; "last_workspace": [bytes of the reusing
  * layout, bytes without reuse (0 if not considered)] for the last
- * tnc_contract batch; "timed_persist_tc_cmacs": the complex
- * multiply-accumulates that timed persistent launches (since
+ * tnc_contract batch; "level_cost": per mode, [per-level launches,
+ * estimated seconds] of that batch with the slice-invariant levels, the
+ * input of the automatic executor choice; "timed_persist_tc_cmacs": the
+ * complex multiply-accumulates that timed persistent launches (since
  * tnc_set_timing) ran on the tensor cores. */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
+
+/* The persistent executor's work list for one batch of `batch` slices
+ * (1..1024) in `mode`, slice-invariant contractions included, for
+ * inspection: the tasks in launch order and the initial counter values. With
+ * deps = 1 the list is built as for an arena without memory reuse
+ * (per-entry dependencies), with 0 as for the reusing arena (level chain);
+ * see the "persist_deps" option. JSON: {"chain": 0|1, "counters": [initial
+ * value per counter], "tasks": [[type, parameter index, item, batch entry,
+ * wait counter 0, 1, 2 (-1: none), counter signalled, second counter
+ * signalled (-1: none), tree level], ...]} with the task types of the
+ * executor (0 FP32 tile, 1 split blocks, 2 tensor-core tile, 3 K-split
+ * reduction, 4 final-contraction chunk, 5 ordered sum of the chunks, 6 slice
+ * sum of a root tensor). A task may start once every counter it waits on is
+ * zero; each task decrements the counters it signals once. Nothing runs and
+ * no device memory is touched: the addresses in the list refer to a stand-in
+ * workspace. Host logic; FP32 mode needs no GPU, the split modes need the
+ * CUDA driver to encode the tensor maps of their contractions.
+ * Errors: TNC_E_INVALID for a bad argument or a too small json capacity;
+ * TNC_E_STATE before tnc_set_path, with fused stem groups in use, or when a
+ * contraction cannot run in the executor (row or K panels). */
+tnc_status tnc_worklist_json(tnc_net_t net, int64_t batch, int mode, int deps, char* json, size_t cap);
 
 /* Tuning options of the tensor-core GEMM (no effect on results):
  *  "tc_row_bytes"  32 or 64 (default 64): bytes of K per tile row and

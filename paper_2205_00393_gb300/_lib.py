@@ -63,6 +63,8 @@ def load_library():
         "tnc_contract": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                          ctypes.c_void_p, ctypes.c_void_p],
         "tnc_stats": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
+        "tnc_worklist_json": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
+                              ctypes.c_size_t],
         "tnc_set_timing": [ctypes.c_void_p, ctypes.c_int],
         "tnc_check_device": [ctypes.c_void_p, ctypes.c_void_p],
         "tnc_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p],
@@ -360,4 +362,11 @@ class Network:
         cap = 1 << 22
         buf = ctypes.create_string_buffer(cap)
         _check(self._lib, self._lib.tnc_stats(self._h, buf, cap))
+        return json.loads(buf.value.decode())
+
+    def worklist(self, batch, mode=FP32, deps=1):
+        """The persistent executor's work list for one batch (tnc_worklist_json)."""
+        cap = 1 << 26
+        buf = ctypes.create_string_buffer(cap)
+        _check(self._lib, self._lib.tnc_worklist_json(self._h, int(batch), int(mode), int(deps), buf, cap))
         return json.loads(buf.value.decode())

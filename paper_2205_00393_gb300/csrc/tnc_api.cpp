@@ -750,6 +750,38 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
     return TNC_OK;
 }
 
+tnc_status tnc_worklist_json(tnc_net_t net, int64_t batch, int mode, int deps, char* json, size_t cap) {
+    if (!net || !json) return fail(TNC_E_INVALID, "NULL argument");
+    if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
+    if (batch < 1 || batch > 1024) return fail(TNC_E_INVALID, "batch must be in [1, 1024]");
+    if (deps != 0 && deps != 1) return fail(TNC_E_INVALID, "deps must be 0 or 1");
+    tnc_status st = ensure_plan(net);
+    if (st != TNC_OK) return st;
+    if (net->plan.nodes.empty() || (stem_fusion(net) && !net->plan.stems.empty()) || net->tuning)
+        return fail(TNC_E_STATE, "the persistent executor does not run this network (fused stem groups in use?)");
+    // the list addresses an arena at a stand-in base: nothing is read or written
+    const Arena ar = plan_arena(net, batch, mode, deps == 0);
+    char* const base = reinterpret_cast<char*>(uintptr_t(1) << 40);
+    WorkList W;
+    if (!wl_network(net, ar, base, (int)batch, mode, true, 0, nullptr, W))
+        return fail(TNC_E_STATE, "no work list: a contraction needs panels, or tensor maps need the CUDA driver");
+    wl_interleave_levels(W);
+    std::ostringstream o;
+    o << "{\"chain\":" << (W.chain ? 1 : 0) << ",\"counters\":[";
+    for (size_t i = 0; i < W.counters.size(); ++i) o << (i ? "," : "") << W.counters[i];
+    o << "],\"tasks\":[";
+    for (size_t i = 0; i < W.tasks.size(); ++i) {
+        const tnc::PersistTask& t = W.tasks[i];
+        o << (i ? "," : "") << "[" << t.type << "," << t.idx << "," << t.item << "," << t.z << "," << t.wait[0]
+          << "," << t.wait[1] << "," << t.wait[2] << "," << t.signal << "," << t.signal2 << "," << W.level[i] << "]";
+    }
+    o << "]}";
+    const std::string js = o.str();
+    if (js.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small: need " + std::to_string(js.size() + 1));
+    std::memcpy(json, js.c_str(), js.size() + 1);
+    return TNC_OK;
+}
+
 void tnc_destroy(tnc_net_t net) {
     if (!net) return;
     many_forget(net->uid);
