@@ -80,9 +80,9 @@ def test_worklist_invariants(libtnc, spec, batch, deps):
         assert all(t[8] == -1 for t in tasks)
     else:
         assert all(t[8] >= 0 for t in tasks)
-        first = min(t[9] for t in tasks)
+        first_level = min(t[9] for t in tasks)
         for t in tasks:
-            if t[9] > first:
+            if t[9] > first_level:
                 assert any(c >= 0 and all(tasks[j][9] == t[9] - 1 for j in by[c]) for c in t[4:7])
     # ordering of data. Every task feeds the result, so the final sum's
     # predecessors (direct or through other tasks) are all other tasks.
@@ -113,9 +113,9 @@ def test_worklist_invariants(libtnc, spec, batch, deps):
 
 
 def test_worklist_deps_wait_less(libtnc):
-    """Per-entry dependencies give every task at most the waits of the level
-    chain's list, and strictly fewer transitive predecessors in total: the
-    levels of different batch entries are no longer serialised."""
+    """The same tasks with per-entry dependencies have strictly fewer
+    transitive predecessors in total than with the level chain: the levels of
+    different batch entries are no longer serialised."""
     net = _net(3, 4, 8, 1, 0, 8)
     a, b = net.worklist(8, 0, 1), net.worklist(8, 0, 0)
     assert len(a["tasks"]) == len(b["tasks"])
