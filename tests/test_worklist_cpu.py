@@ -43,26 +43,36 @@ def _signallers(tasks):
     return by
 
 
-def _closure(tasks, by, i):
-    """Every task that task i waits on, directly or through the tasks it waits on."""
-    seen, stack = set(), [i]
-    while stack:
-        for c in tasks[stack.pop()][4:7]:
+def _preds(tasks, by):
+    """Per task, the bitset of every task it waits on, directly or through the
+    tasks it waits on. List order is a topological order once the progress
+    check has passed, so each counter's set is built from finished ones."""
+    pred, per_counter = [0] * len(tasks), {}
+    for i, t in enumerate(tasks):
+        p = 0
+        for c in t[4:7]:
             if c < 0:
                 continue
-            for j in by[c]:
-                if j not in seen:
-                    seen.add(j)
-                    stack.append(j)
-    return seen
+            if c not in per_counter:
+                m = 0
+                for j in by[c]:
+                    m |= pred[j] | (1 << j)
+                per_counter[c] = m
+            p |= per_counter[c]
+        pred[i] = p
+    return pred
 
 
-@pytest.mark.parametrize("deps", [1, 0])
-@pytest.mark.parametrize("spec,batch", [((3, 4, 8, 1, 0, 8), 4), ((4, 5, 12, 3, 3, 16), 2)])
-def test_worklist_invariants(libtnc, spec, batch, deps):
-    net = _net(*spec)
-    wl = net.worklist(batch, 0, deps)
+def _mask(indices):
+    m = 0
+    for i in indices:
+        m |= 1 << i
+    return m
+
+
+def _check(wl, deps):
     tasks, counters = wl["tasks"], wl["counters"]
+    n = len(tasks)
     assert wl["chain"] == 1 - deps
     assert tasks and all(t[0] in (GEMM, ROOT, ACC, SUM) for t in tasks)
     by = _signallers(tasks)
@@ -74,42 +84,80 @@ def test_worklist_invariants(libtnc, spec, batch, deps):
         for c in t[4:7]:
             if c >= 0:
                 assert by[c] and max(by[c]) < i, (i, c)
+    pred = _preds(tasks, by)
+    level = collections.defaultdict(list)
+    for i, t in enumerate(tasks):
+        level[t[9]].append(i)
+    level = {L: _mask(v) for L, v in level.items()}
     # the chain mode: a task also counts down its level, and every task past
-    # the first level waits on the previous one; per-entry mode: no level counters
+    # the first level follows the whole previous one; per-entry mode: no
+    # level counters
     if deps:
         assert all(t[8] == -1 for t in tasks)
     else:
         assert all(t[8] >= 0 for t in tasks)
-        first_level = min(t[9] for t in tasks)
-        for t in tasks:
+        first_level = min(level)
+        for i, t in enumerate(tasks):
             if t[9] > first_level:
-                assert any(c >= 0 and all(tasks[j][9] == t[9] - 1 for j in by[c]) for c in t[4:7])
-    # ordering of data. Every task feeds the result, so the final sum's
-    # predecessors (direct or through other tasks) are all other tasks.
+                assert level[t[9] - 1] & ~pred[i] == 0, i
+    # ordering of data. Every task feeds the result, so the final sum follows
+    # all other tasks.
     final = [i for i, t in enumerate(tasks) if t[0] in (ACC, SUM)]
     assert len(final) == 1
-    assert _closure(tasks, by, final[0]) == set(range(len(tasks))) - set(final)
+    assert pred[final[0]] == ((1 << n) - 1) & ~(1 << final[0])
     # A parameter entry with tasks of several batch entries is per-slice, one
     # with entry 0 only is slice-invariant (batch >= 2 here).
     zs = collections.defaultdict(set)
     for t in tasks:
         zs[(t[0], t[1])].add(t[3])
     per_slice = {k for k, v in zs.items() if len(v) > 1}
+    ps_mask = _mask(i for i, t in enumerate(tasks) if (t[0], t[1]) in per_slice)
+    entry = collections.defaultdict(list)
+    for i, t in enumerate(tasks):
+        entry[t[3]].append(i)
+    entry = {z: _mask(v) for z, v in entry.items()}
     tiles = [i for i, t in enumerate(tasks) if t[0] == GEMM and (t[0], t[1]) in per_slice]
     first = min(tasks[i][9] for i in tiles)
     for i in tiles:
-        t, pred = tasks[i], _closure(tasks, by, i)
+        t = tasks[i]
         if deps:
             # per entry: no per-slice predecessor of another batch entry
-            assert all(tasks[j][3] == t[3] for j in pred if (tasks[j][0], tasks[j][1]) in per_slice), i
-        else:
-            # the chain: every task of the previous level
-            assert all(j in pred for j, u in enumerate(tasks) if u[9] == t[9] - 1), i
+            assert pred[i] & ps_mask & ~entry[t[3]] == 0, i
         if t[9] > first:
             # a contraction above the first per-slice level reads one from
             # the level below, of its own entry
-            assert any(tasks[j][9] == t[9] - 1 and tasks[j][3] == t[3] and (tasks[j][0], tasks[j][1]) in per_slice
-                       for j in pred), i
+            assert pred[i] & level[t[9] - 1] & entry[t[3]] & ps_mask, i
+
+
+@pytest.mark.parametrize("deps", [1, 0])
+@pytest.mark.parametrize("spec,batch", [((3, 4, 8, 1, 0, 8), 4), ((4, 5, 12, 3, 3, 16), 2)])
+def test_worklist_invariants(libtnc, spec, batch, deps):
+    _check(_net(*spec).worklist(batch, 0, deps), deps)
+
+
+@pytest.mark.parametrize("deps", [1, 0])
+def test_worklist_invariants_batched_workload(libtnc, deps):
+    """The first 24 circuits of the seeded batched workload (20-36 qubits,
+    uneven trees), planned as the batched benchmark plans them, 2 slices;
+    those whose list holds at most 2^14 tasks."""
+    from paper_2205_00393_gb300 import Network
+    from tnc_inputs.circuits import batched_workload
+    checked = 0
+    for circ, k in batched_workload(24, 1000):
+        net = Network.from_tn(circuit_to_network(circ).as_complex64())
+        net.set_path(net.greedy_path())
+        W = net.stats()["max_log2_size"]
+        t = max(min(W - k, 24), len(circ.open_qubits) + 4)
+        net.set_slices(net.find_slices(t, 7))
+        net.set_option("stem_cap_log2", 0)
+        if net.n_slices < 2:
+            continue
+        wl = net.worklist(2, 0, deps)
+        if len(wl["tasks"]) > 16384:  # bitsets of every task's predecessors stay small
+            continue
+        _check(wl, deps)
+        checked += 1
+    assert checked >= 12
 
 
 def test_worklist_deps_wait_less(libtnc):
@@ -117,10 +165,10 @@ def test_worklist_deps_wait_less(libtnc):
     transitive predecessors in total than with the level chain: the levels of
     different batch entries are no longer serialised."""
     net = _net(3, 4, 8, 1, 0, 8)
-    a, b = net.worklist(8, 0, 1), net.worklist(8, 0, 0)
-    assert len(a["tasks"]) == len(b["tasks"])
-    ca = sum(len(_closure(a["tasks"], _signallers(a["tasks"]), i)) for i in range(len(a["tasks"])))
-    cb = sum(len(_closure(b["tasks"], _signallers(b["tasks"]), i)) for i in range(len(b["tasks"])))
+    a, b = net.worklist(8, 0, 1)["tasks"], net.worklist(8, 0, 0)["tasks"]
+    assert len(a) == len(b)
+    ca = sum(bin(p).count("1") for p in _preds(a, _signallers(a)))
+    cb = sum(bin(p).count("1") for p in _preds(b, _signallers(b)))
     assert ca < cb
 
 
