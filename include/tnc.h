@@ -264,7 +264,7 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  * see the "persist_deps" option. JSON: {"chain": 0|1, "counters": [initial
  * value per counter], "tasks": [[type, parameter index, item, batch entry,
  * wait counter 0, 1, 2 (-1: none), counter signalled, second counter
- * signalled (-1: none), tree level], ...]} with the task types of the
+ * signalled (-1: none), tree level, network (0)], ...]} with the task types of the
  * executor (0 FP32 tile, 1 split blocks, 2 tensor-core tile, 3 K-split
  * reduction, 4 final-contraction chunk, 5 ordered sum of the chunks, 6 slice
  * sum of a root tensor). A task may start once every counter it waits on is
@@ -276,6 +276,16 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
  * TNC_E_STATE before tnc_set_path, with fused stem groups in use, or when a
  * contraction cannot run in the executor (row or K panels). */
 tnc_status tnc_worklist_json(tnc_net_t net, int64_t batch, int mode, int deps, char* json, size_t cap);
+
+/* The merged work list of n networks (one batch of `batch` slices each) as
+ * one persistent launch of tnc_contract_many runs it: every network's list
+ * built as by tnc_worklist_json, its parameter indices and counters offset
+ * past the earlier networks', then all tasks ordered by tree level (level L
+ * of every network before level L + 1 of any). Same JSON, with an 11th entry
+ * per task: the network's position in nets. Errors as tnc_worklist_json,
+ * and TNC_E_INVALID for n < 1 or a network given twice. */
+tnc_status tnc_worklist_many_json(int n, const tnc_net_t* nets, int64_t batch, int mode, int deps, char* json,
+                                  size_t cap);
 
 /* Tuning options of the tensor-core GEMM (no effect on results):
  *  "tc_row_bytes"  32 or 64 (default 64): bytes of K per tile row and

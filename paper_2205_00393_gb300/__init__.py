@@ -7,7 +7,7 @@ missing, importing the binding raises.
 """
 
 from ._lib import (Network, TNCError, FP32, SPLIT_TF32, SPLIT_BF16, SPLIT_BF16X2, SPLIT_FP16X2, contract_many, tune_table, lib_path,
-                   load_library, peak_probe)
+                   load_library, peak_probe, worklist_many)
 
 __all__ = ["Network", "TNCError", "contract_many", "tune_table", "FP32", "SPLIT_TF32", "SPLIT_BF16", "SPLIT_BF16X2", "SPLIT_FP16X2",
-           "lib_path", "load_library", "peak_probe"]
+           "lib_path", "load_library", "peak_probe", "worklist_many"]

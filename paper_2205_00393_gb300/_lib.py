@@ -65,6 +65,8 @@ def load_library():
         "tnc_stats": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
         "tnc_worklist_json": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
                               ctypes.c_size_t],
+        "tnc_worklist_many_json": [ctypes.c_int, P(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_char_p, ctypes.c_size_t],
         "tnc_set_timing": [ctypes.c_void_p, ctypes.c_int],
         "tnc_check_device": [ctypes.c_void_p, ctypes.c_void_p],
         "tnc_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p],
@@ -121,6 +123,17 @@ def peak_probe(kind, iters, stream=None):
     flops = ctypes.c_double(0.0)
     _check(lib, lib.tnc_peak_probe(int(kind), int(iters), ctypes.byref(flops), _stream_ptr(stream)))
     return flops.value
+
+
+def worklist_many(networks, batch, mode=FP32, deps=1):
+    """The merged persistent work list of several networks, one batch each
+    (tnc_worklist_many_json)."""
+    lib = load_library()
+    handles = (ctypes.c_void_p * len(networks))(*[n._h.value for n in networks])
+    cap = 1 << 27
+    buf = ctypes.create_string_buffer(cap)
+    _check(lib, lib.tnc_worklist_many_json(len(networks), handles, int(batch), int(mode), int(deps), buf, cap))
+    return json.loads(buf.value.decode())
 
 
 def contract_many(networks, ranges=None, mode=FP32, outs=None, use_graph=True, stream=None):

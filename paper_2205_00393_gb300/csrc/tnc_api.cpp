@@ -750,36 +750,63 @@ tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap) {
     return TNC_OK;
 }
 
-tnc_status tnc_worklist_json(tnc_net_t net, int64_t batch, int mode, int deps, char* json, size_t cap) {
-    if (!net || !json) return fail(TNC_E_INVALID, "NULL argument");
+// Work list of networks nets[0..n) for one batch each, as the persistent
+// executor would run it in one launch (one network: as tnc_contract; several:
+// merged and interleaved by level as tnc_contract_many), built against
+// stand-in workspaces, then written as JSON.
+static tnc_status worklist_json(int n, const tnc_net_t* nets, int64_t batch, int mode, int deps, char* json,
+                                size_t cap) {
+    if (n < 1 || !nets || !json) return fail(TNC_E_INVALID, "bad argument");
     if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
     if (batch < 1 || batch > 1024) return fail(TNC_E_INVALID, "batch must be in [1, 1024]");
     if (deps != 0 && deps != 1) return fail(TNC_E_INVALID, "deps must be 0 or 1");
-    tnc_status st = ensure_plan(net);
-    if (st != TNC_OK) return st;
-    if (net->plan.nodes.empty() || (stem_fusion(net) && !net->plan.stems.empty()) || net->tuning)
-        return fail(TNC_E_STATE, "the persistent executor does not run this network (fused stem groups in use?)");
-    // the list addresses an arena at a stand-in base: nothing is read or written
-    const Arena ar = plan_arena(net, batch, mode, deps == 0);
-    char* const base = reinterpret_cast<char*>(uintptr_t(1) << 40);
     WorkList W;
-    if (!wl_network(net, ar, base, (int)batch, mode, true, 0, nullptr, W))
-        return fail(TNC_E_STATE, "no work list: a contraction needs panels, or tensor maps need the CUDA driver");
+    for (int i = 0; i < n; ++i) {
+        tnc_net* net = nets[i];
+        if (!net) return fail(TNC_E_INVALID, "NULL network");
+        for (int j = 0; j < i; ++j)
+            if (nets[j] == net) return fail(TNC_E_INVALID, "a network appears twice");
+        tnc_status st = ensure_plan(net);
+        if (st != TNC_OK) return st;
+        if (net->plan.nodes.empty() || (stem_fusion(net) && !net->plan.stems.empty()) || net->tuning)
+            return fail(TNC_E_STATE, "the persistent executor does not run network " + std::to_string(i) +
+                                         " (fused stem groups in use?)");
+        // the list addresses an arena at a stand-in base: nothing is read or written
+        const Arena ar = plan_arena(net, batch, mode, deps == 0);
+        char* const base = reinterpret_cast<char*>(uintptr_t(i + 1) << 40);
+        WorkList Wi;
+        if (!wl_network(net, ar, base, (int)batch, mode, true, i, nullptr, Wi))
+            return fail(TNC_E_STATE, "no work list for network " + std::to_string(i) +
+                                         ": a contraction needs panels, or tensor maps need the CUDA driver");
+        if (n == 1) W = std::move(Wi);
+        else wl_append(W, Wi);
+    }
     wl_interleave_levels(W);
     std::ostringstream o;
-    o << "{\"chain\":" << (W.chain ? 1 : 0) << ",\"counters\":[";
+    o << "{\"chain\":" << (deps ? 0 : 1) << ",\"counters\":[";
     for (size_t i = 0; i < W.counters.size(); ++i) o << (i ? "," : "") << W.counters[i];
     o << "],\"tasks\":[";
     for (size_t i = 0; i < W.tasks.size(); ++i) {
         const tnc::PersistTask& t = W.tasks[i];
         o << (i ? "," : "") << "[" << t.type << "," << t.idx << "," << t.item << "," << t.z << "," << t.wait[0]
-          << "," << t.wait[1] << "," << t.wait[2] << "," << t.signal << "," << t.signal2 << "," << W.level[i] << "]";
+          << "," << t.wait[1] << "," << t.wait[2] << "," << t.signal << "," << t.signal2 << "," << W.level[i] << ","
+          << t.net << "]";
     }
     o << "]}";
     const std::string js = o.str();
     if (js.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small: need " + std::to_string(js.size() + 1));
     std::memcpy(json, js.c_str(), js.size() + 1);
     return TNC_OK;
+}
+
+tnc_status tnc_worklist_json(tnc_net_t net, int64_t batch, int mode, int deps, char* json, size_t cap) {
+    if (!net) return fail(TNC_E_INVALID, "NULL network");
+    return worklist_json(1, &net, batch, mode, deps, json, cap);
+}
+
+tnc_status tnc_worklist_many_json(int n, const tnc_net_t* nets, int64_t batch, int mode, int deps, char* json,
+                                  size_t cap) {
+    return worklist_json(n, nets, batch, mode, deps, json, cap);
 }
 
 void tnc_destroy(tnc_net_t net) {

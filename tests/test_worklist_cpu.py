@@ -117,7 +117,7 @@ def _check(wl, deps):
         entry[t[3]].append(i)
     entry = {z: _mask(v) for z, v in entry.items()}
     tiles = [i for i, t in enumerate(tasks) if t[0] == GEMM and (t[0], t[1]) in per_slice]
-    first = min(tasks[i][9] for i in tiles)
+    first = min((tasks[i][9] for i in tiles), default=0)
     for i in tiles:
         t = tasks[i]
         if deps:
@@ -179,3 +179,37 @@ def test_worklist_errors(libtnc):
         with pytest.raises(TNCError) as e:
             net.worklist(*args)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("deps", [1, 0])
+def test_worklist_many_merged(libtnc, deps):
+    """tnc_contract_many's merged list of four networks of different sizes:
+    the merge keeps each network's list intact (its tasks, counters and
+    initial values, offset), tasks are ordered by level across networks, no
+    task waits on another network's counters, and progress and accounting
+    hold for the merged list."""
+    from paper_2205_00393_gb300 import worklist_many
+    nets = [_net(3, 4, 8, 1, 0, 8), _net(4, 5, 12, 3, 3, 16), _net(3, 3, 7, 3, 1, 7), _net(4, 4, 10, 2, 2, 12)]
+    merged = worklist_many(nets, 2, 0, deps)
+    tasks, counters = merged["tasks"], merged["counters"]
+    by = _signallers(tasks)
+    for c, init in enumerate(counters):
+        assert init == len(by[c])
+    for i, t in enumerate(tasks):
+        for c in t[4:7]:
+            if c >= 0:
+                assert by[c] and max(by[c]) < i
+                assert all(tasks[j][10] == t[10] for j in by[c]), (i, c)
+    assert [t[9] for t in tasks] == sorted(t[9] for t in tasks)
+    # each network's share equals its own list, up to the offsets
+    for k, net in enumerate(nets):
+        own = net.worklist(2, 0, deps)
+        mine = [t for t in tasks if t[10] == k]
+        assert len(mine) == len(own["tasks"])
+        assert sorted((t[0], t[2], t[3]) for t in mine) == sorted((t[0], t[2], t[3]) for t in own["tasks"])
+        used = sorted({c for t in mine for c in (t[4], t[5], t[6], t[7], t[8]) if c >= 0})
+        assert sorted(counters[c] for c in used) == sorted(own["counters"])
+        # the network's own invariants on its share (counters renumbered)
+        ren = {c: r for r, c in enumerate(used)}
+        sub = [t[:4] + [ren.get(c, -1) for c in t[4:9]] + t[9:] for t in mine]
+        _check({"chain": merged["chain"], "counters": [counters[c] for c in used], "tasks": sub}, deps)
