@@ -256,6 +256,19 @@ tnc_status tnc_contract_many(int n, const tnc_net_t* nets, const int64_t* slice_
  * tnc_set_timing) ran on the tensor cores. */
 tnc_status tnc_stats(tnc_net_t net, char* json, size_t cap);
 
+/* The workspace plan of one batch of `batch` slices (1..1024) in `mode`, for
+ * inspection: the first-fit simulation that tnc_contract sizes and places
+ * its workspace with, tree level by level (slice-invariant levels first,
+ * then per-slice ones, then the final contraction), with reuse = 1 as for
+ * the per-level executor and the level chain, 0 without reuse (per-entry
+ * dependencies). JSON: {"peak": bytes, "events": [[op (0 allocation,
+ * 1 release), kind (0 tensor, 1 / 2 split planes of operand A / B, 3 final
+ * contraction scratch), id (tensor id; for planes and scratch the
+ * contraction's output tensor id), byte offset, bytes, level], ...]} in
+ * simulation order. Host logic, no GPU. Errors: TNC_E_INVALID for a bad
+ * argument or a too small json capacity; TNC_E_STATE before tnc_set_path. */
+tnc_status tnc_arena_json(tnc_net_t net, int64_t batch, int mode, int reuse, char* json, size_t cap);
+
 /* The persistent executor's work list for one batch of `batch` slices
  * (1..1024) in `mode`, slice-invariant contractions included, for
  * inspection: the tasks in launch order and the initial counter values. With

@@ -63,6 +63,8 @@ def load_library():
         "tnc_contract": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                          ctypes.c_void_p, ctypes.c_void_p],
         "tnc_stats": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
+        "tnc_arena_json": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
+                           ctypes.c_size_t],
         "tnc_worklist_json": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
                               ctypes.c_size_t],
         "tnc_worklist_many_json": [ctypes.c_int, P(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int, ctypes.c_int,
@@ -375,6 +377,13 @@ class Network:
         cap = 1 << 22
         buf = ctypes.create_string_buffer(cap)
         _check(self._lib, self._lib.tnc_stats(self._h, buf, cap))
+        return json.loads(buf.value.decode())
+
+    def arena(self, batch, mode=FP32, reuse=1):
+        """The workspace plan of one batch (tnc_arena_json)."""
+        cap = 1 << 26
+        buf = ctypes.create_string_buffer(cap)
+        _check(self._lib, self._lib.tnc_arena_json(self._h, int(batch), int(mode), int(reuse), buf, cap))
         return json.loads(buf.value.decode())
 
     def worklist(self, batch, mode=FP32, deps=1):

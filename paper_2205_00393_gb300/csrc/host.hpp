@@ -362,6 +362,15 @@ TcCut tc_cut(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch
 int64_t tc_bytes_a(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch);
 int64_t tc_bytes_b(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t batch);
 Arena plan_arena(const tnc_net* net, int64_t nb, int mode, bool reuse = true);
+// One allocation (op 0) or release (op 1) of plan_arena's simulation: kind 0
+// a tensor (id: its tensor id), 1 / 2 the split planes of A / B of contraction
+// id, 3 the final contraction's scratch; step: the level being simulated.
+struct ArenaEvent {
+    int op, kind, id;
+    int64_t off, len;
+    int step;
+};
+Arena plan_arena_log(const tnc_net* net, int64_t nb, int mode, bool reuse, std::vector<ArenaEvent>* log);
 std::string group_key_of(const tnc_net* net, int mode, int64_t nb, const char* ws, bool reuse);
 std::string plan_key(const tnc_net* net, int mode, int64_t nb);
 int64_t cut_batch(const Arena& ar, const NodePlan& np, int64_t b);

@@ -316,7 +316,8 @@ int64_t tc_bytes_b(const tnc_net* net, int mode, int mb, int nb, int kb, int64_t
     return tc_cut(net, mode, mb, nb, kb, batch).b_bytes;
 }
 
-static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool reuse);
+static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool reuse,
+                                 std::vector<ArenaEvent>* log = nullptr);
 
 // Everything the level groups and the arena of a batch of nb slices depend
 // on: the plan, the kernel choices and the options that shape groups and
@@ -339,7 +340,8 @@ Arena plan_arena(const tnc_net* net, int64_t nb, int mode, bool reuse) {
     return net->arena_cache[key] = plan_arena_uncached(net, nb, mode, reuse);
 }
 
-static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool reuse) {
+static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool reuse,
+                                 std::vector<ArenaEvent>* log) {
     const Plan& P = net->plan;
     const tnc::Tree& T = *net->tree;
     Arena ar;
@@ -348,7 +350,8 @@ static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool 
     ar.planes_b.assign(P.nodes.size(), -1);
     std::map<int64_t, int64_t> used;  // off -> len
     int64_t top = 0;
-    auto alloc = [&](int64_t len) {
+    int step = 0;  // level being simulated (for the optional event log)
+    auto alloc = [&](int64_t len, int kind, int id) {
         len = align_up(len);
         int64_t prev_end = 0;
         for (auto& kv : used) {
@@ -358,30 +361,36 @@ static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool 
         int64_t off = prev_end;
         used[off] = len;
         top = std::max(top, off + len);
+        if (log) log->push_back(ArenaEvent{0, kind, id, off, len, step});
         return off;
     };
     // without reuse every tensor and temporary keeps its bytes for the whole
     // launch, so tasks of different levels may run at the same time
-    auto release = [&](int64_t off) {
-        if (reuse) used.erase(off);
+    auto release = [&](int64_t off, int kind, int id) {
+        if (!reuse) return;
+        auto it = used.find(off);
+        if (it == used.end()) return;
+        if (log) log->push_back(ArenaEvent{1, kind, id, off, it->second, step});
+        used.erase(it);
     };
     auto tc_planes = [&](const NodePlan& np, int64_t b) {
         const size_t i = np.v - net->n_leaves;
-        ar.planes_a[i] = alloc(tc_bytes_a(net, mode, np.mb, np.nb, np.kb, b));
-        ar.planes_b[i] = alloc(tc_bytes_b(net, mode, np.mb, np.nb, np.kb, b));
+        ar.planes_a[i] = alloc(tc_bytes_a(net, mode, np.mb, np.nb, np.kb, b), 1, np.v);
+        ar.planes_b[i] = alloc(tc_bytes_b(net, mode, np.mb, np.nb, np.kb, b), 2, np.v);
     };
     auto tc_release = [&](const NodePlan& np) {
         const size_t i = np.v - net->n_leaves;
-        release(ar.planes_a[i]);
-        release(ar.planes_b[i]);
+        release(ar.planes_a[i], 1, np.v);
+        release(ar.planes_b[i], 2, np.v);
     };
     // Lifetimes follow the executed order: one tree level at a time; all
     // outputs of a level are live together, inputs die after their level.
     auto run_level = [&](const Group& g, int64_t b) {
-        for (int v : g.fp32) ar.off[v] = alloc(b * tensor_bytes(P, v));
-        for (int v : g.tc) ar.off[v] = alloc(b * tensor_bytes(P, v));
+        for (int v : g.fp32) ar.off[v] = alloc(b * tensor_bytes(P, v), 0, v);
+        for (int v : g.tc) ar.off[v] = alloc(b * tensor_bytes(P, v), 0, v);
         // fused stem groups: only T_n is stored; T_1 .. T_{n-1} stay on chip
-        for (int gi : g.stems) ar.off[P.stems[gi].out] = alloc(b * tensor_bytes(P, P.stems[gi].out));
+        for (int gi : g.stems)
+            ar.off[P.stems[gi].out] = alloc(b * tensor_bytes(P, P.stems[gi].out), 0, P.stems[gi].out);
         // the split planes of a level's tensor-core contractions are live
         // together: the persistent executor runs a level's contractions at
         // the same time
@@ -397,15 +406,16 @@ static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool 
             for (int v : *list) {
                 const NodePlan& np = P.nodes[v - net->n_leaves];
                 for (int c : {np.A, np.B})
-                    if (c >= net->n_leaves && P.per_slice[c] == (char)g.per_slice) release(ar.off[c]);
+                    if (c >= net->n_leaves && P.per_slice[c] == (char)g.per_slice) release(ar.off[c], 0, c);
             }
         for (int gi : g.stems) {
             const StemGroupPlan& sg = P.stems[gi];
             std::vector<int> ins{sg.in};
             for (int k : sg.steps) ins.push_back(P.nodes[k].B);
             for (int c : ins)
-                if (c >= net->n_leaves && P.per_slice[c] == (char)g.per_slice) release(ar.off[c]);
+                if (c >= net->n_leaves && P.per_slice[c] == (char)g.per_slice) release(ar.off[c], 0, c);
         }
+        ++step;
     };
     // phase 1: invariant levels (batch 1); invariant tensors consumed by
     // per-slice nodes stay live for the whole call
@@ -416,12 +426,17 @@ static Arena plan_arena_uncached(const tnc_net* net, int64_t nb, int mode, bool 
         if (!np.is_root) continue;
         int64_t bytes = np.kind == K_ROOT_F64 ? nb * np.chunks * (int64_t)16 << (np.mb + np.nb)
                                               : nb * tensor_bytes(P, np.v);
-        ar.root_scratch_off = alloc(bytes);
+        ar.root_scratch_off = alloc(bytes, 3, np.v);
     }
     ar.peak = top;
     ar.batch = nb;
     ar.reuse = reuse;
     return ar;
+}
+
+// plan_arena's simulation with its events recorded (not cached).
+Arena plan_arena_log(const tnc_net* net, int64_t nb, int mode, bool reuse, std::vector<ArenaEvent>* log) {
+    return plan_arena_uncached(net, nb, mode, reuse, log);
 }
 
 // Batch whose cut (panels, K splits, plane and partial layout) a tensor-core

@@ -799,6 +799,29 @@ static tnc_status worklist_json(int n, const tnc_net_t* nets, int64_t batch, int
     return TNC_OK;
 }
 
+tnc_status tnc_arena_json(tnc_net_t net, int64_t batch, int mode, int reuse, char* json, size_t cap) {
+    if (!net || !json) return fail(TNC_E_INVALID, "NULL argument");
+    if (mode < TNC_FP32 || mode > TNC_SPLIT_FP16X2) return fail(TNC_E_INVALID, "unknown mode");
+    if (batch < 1 || batch > 1024) return fail(TNC_E_INVALID, "batch must be in [1, 1024]");
+    if (reuse != 0 && reuse != 1) return fail(TNC_E_INVALID, "reuse must be 0 or 1");
+    tnc_status st = ensure_plan(net);
+    if (st != TNC_OK) return st;
+    std::vector<ArenaEvent> log;
+    const Arena ar = plan_arena_log(net, batch, mode, reuse == 1, &log);
+    std::ostringstream o;
+    o << "{\"peak\":" << ar.peak << ",\"events\":[";
+    for (size_t i = 0; i < log.size(); ++i) {
+        const ArenaEvent& e = log[i];
+        o << (i ? "," : "") << "[" << e.op << "," << e.kind << "," << e.id << "," << e.off << "," << e.len << ","
+          << e.step << "]";
+    }
+    o << "]}";
+    const std::string js = o.str();
+    if (js.size() + 1 > cap) return fail(TNC_E_INVALID, "json capacity too small: need " + std::to_string(js.size() + 1));
+    std::memcpy(json, js.c_str(), js.size() + 1);
+    return TNC_OK;
+}
+
 tnc_status tnc_worklist_json(tnc_net_t net, int64_t batch, int mode, int deps, char* json, size_t cap) {
     if (!net) return fail(TNC_E_INVALID, "NULL network");
     return worklist_json(1, &net, batch, mode, deps, json, cap);
