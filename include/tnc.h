@@ -371,8 +371,9 @@ tnc_status tnc_worklist_many_json(int n, const tnc_net_t* nets, int64_t batch, i
  *                  0, or when it does not fit, the workspace reuses the bytes
  *                  of dead tensors and every task also waits for the whole
  *                  previous tree level. tnc_workspace_bytes reports the
- *                  reusing layout; tnc_stats "last_workspace" gives both
- *                  sizes for the last call. tnc_contract_many does the same
+ *                  reusing layout; tnc_arena_json with reuse = 0 gives the
+ *                  size per-entry dependencies need, and tnc_stats
+ *                  "last_workspace" both sizes for the last call. tnc_contract_many does the same
  *                  per network, its own workspace capped at the larger of
  *                  256 MiB and the reusing layout.
  *  "persist_wait_ms" 0..600000 (default 0 = 10 s): bound of one dependency
